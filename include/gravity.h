@@ -1,0 +1,171 @@
+/*
+ * gravity.h - C ABI of libgravity, a GB300 (sm_103a) Barnes-Hut octree gravity library.
+ *
+ * Method: Ferrari, Lavagna, Blazquez, "A parallel-GPU code for asteroid aggregation
+ * problems with angular particles", MNRAS 2019 (arXiv:1912.04197), Sec. 2.1:
+ * N point masses, Eq. (Newton); octree clustering with the opening test of
+ * Eq. (accuracy); force rules Eqs. (Force_leaf, Force_thetaTrue) with the softened
+ * distance of Eq. (Force_rComp); node moments Eq. (COMinternal); the tree is
+ * rebuilt every step.  The library returns accelerations (force / body mass).
+ *
+ * Conventions shared by every entry point:
+ *   - Array arguments are DEVICE pointers (e.g. torch.Tensor.data_ptr()) unless the
+ *     name ends in _host.  They are contiguous, row-major, caller-owned, and not
+ *     retained after the call returns.  pos/vel/acc are (n, 3) FP64, mass is (n) FP64.
+ *   - All work is enqueued on the context's CUDA stream (the caller's stream); no
+ *     call synchronises the device except gravity_sync, gravity_debug_export and
+ *     the _host entry points.
+ *   - Return value: GRAVITY_OK (0) or a negative GRAVITY_E_* code.  Argument and
+ *     launch errors are returned immediately.  Errors found on the device (a
+ *     non-finite coordinate, an exhausted walk stack, a bounded wait that ran out)
+ *     are latched in the context and returned by the next gravity_sync.  After a
+ *     latched error the outputs of the affected call are unspecified.
+ *   - No exception crosses the ABI and nothing aborts the process.
+ *   - The context owns all scratch memory (sort buffers, tree, walk records); it
+ *     grows on demand and is freed by gravity_destroy.  One context must not be
+ *     used from two host threads at once.
+ */
+#ifndef GRAVITY_H
+#define GRAVITY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum gravity_status {
+  GRAVITY_OK = 0,
+  GRAVITY_E_ARG = -1,        /* invalid argument (n < 0, theta < 0, eps < 0, null pointer, ...) */
+  GRAVITY_E_NONFINITE = -2,  /* a position coordinate is NaN or infinite (latched) */
+  GRAVITY_E_NOMEM = -3,      /* device allocation failed */
+  GRAVITY_E_CUDA = -4,       /* a CUDA runtime call failed */
+  GRAVITY_E_TIMEOUT = -5,    /* a bounded device-side wait ran out (latched) */
+  GRAVITY_E_INTERNAL = -6,   /* walk stack exhausted or inconsistent tree (latched) */
+  GRAVITY_E_NOTREE = -7      /* gravity_forces called before gravity_tree_build */
+};
+
+typedef struct gravity_ctx gravity_ctx;
+
+/* Tunables.  Fill with gravity_params_default() and change what you need. */
+typedef struct gravity_params {
+  double G;            /* gravitational constant of Eq. (Newton); default 1.0 */
+  int32_t order;       /* 0 = monopole node terms (the paper), 2 = + traceless quadrupole */
+  int32_t leaf_max;    /* bodies per leaf cell: 1 = the paper's "zero or one body"
+                          (Sec. 2.1); 1..64 allowed */
+  int32_t accum;       /* per-body accumulation: 0 = FP32 compensated (two-sum), 1 = FP64 */
+  int32_t mac_guard;   /* 1 (default) = a cell that contains the body is always opened;
+                          0 = plain opening test for every cell */
+  int32_t scheme;      /* leapfrog_step only: 0 = kick-drift-kick leapfrog,
+                          1 = semi-implicit (symplectic) Euler (Sec. 2.3) */
+  int32_t walk_cfg;    /* -1 = default launch shape of the walk; >= 0 = index into the
+                          table of walk launch shapes (autotuner use) */
+  int32_t reserved[2];
+} gravity_params;
+
+/* Fill *p with the defaults: G = 1, order 0, leaf_max 1, accum 0, mac_guard 1,
+ * scheme 0, walk_cfg -1. */
+void gravity_params_default(gravity_params *p);
+
+/* Create a context on CUDA device `device` whose work goes to `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the handle. */
+int gravity_create(gravity_ctx **out, int device, void *cuda_stream);
+
+/* Synchronise the context's stream and free everything it owns.  NULL is a no-op. */
+int gravity_destroy(gravity_ctx *ctx);
+
+/* Change the stream later calls are enqueued on. */
+int gravity_set_stream(gravity_ctx *ctx, void *cuda_stream);
+
+/* Kernels 1-4 of the paper's five-kernel list (Sec. 2.1, "CUDA implementation"):
+ * bounding cube of all bodies (the root), octree construction (63-bit Morton keys,
+ * stable device radix sort = "sort bodies", binary radix tree collapsed to an
+ * octree), and node mass / centre of mass by Eq. (COMinternal) in FP64 (plus the
+ * traceless quadrupole when p->order == 2).  The tree stays in the context until
+ * the next build; pos and mass are read during this call only.
+ * n = 0 is a no-op that leaves an empty tree.  p = NULL means defaults. */
+int gravity_tree_build(gravity_ctx *ctx, int64_t n, const double *pos, const double *mass,
+                       const gravity_params *p);
+
+/* Kernel 5 of the list (Sec. 2.1): for every body, walk the tree from the root;
+ * a node with l < theta * D (l = cell side, D = distance to the node's centre of
+ * mass, Eq. (accuracy)) contributes its monopole (Eq. Force_thetaTrue) and, with
+ * order 2, its quadrupole; otherwise it is opened; a single-body leaf contributes a
+ * body-to-body term (Eq. Force_leaf).  Every term uses r^2 = |d|^2 + eps^2
+ * (Eq. Force_rComp); a term with r^2 = 0 contributes nothing.
+ * acc: (n, 3) FP64, caller order, overwritten with G-scaled accelerations.
+ * theta = 0 is exact (direct summation); theta < 0 or eps < 0 -> GRAVITY_E_ARG. */
+int gravity_forces(gravity_ctx *ctx, double theta, double eps, double *acc);
+
+/* As gravity_forces, and also writes per-body decision counts (caller order,
+ * int32 (n, 2): node terms accepted, body-to-body terms excluding the body
+ * itself) to the device array counts.  Slower; meant for tests. */
+int gravity_forces_counted(gravity_ctx *ctx, double theta, double eps, double *acc,
+                           int32_t *counts);
+
+/* Eq. (Newton) with the softening of Eq. (Force_rComp), all N(N-1) pairs:
+ * acc_i = G sum_{j != i} m_j (R_j - R_i) / (|R_j - R_i|^2 + eps^2)^{3/2}.
+ * FP32 pair terms on hi/lo split coordinates, compensated accumulation, FP64 out. */
+int gravity_direct(gravity_ctx *ctx, int64_t n, const double *pos, const double *mass,
+                   double eps, double G, double *acc);
+
+/* nsteps steps of a symplectic integrator (Sec. 2.3) with the tree rebuilt every
+ * step (Sec. 2.1).  p->scheme 0 (kick-drift-kick leapfrog):
+ *   v += dt/2 a;  x += dt v;  a = a(x);  v += dt/2 a
+ * p->scheme 1 (semi-implicit Euler):  v += dt a;  x += dt v;  a = a(x).
+ * pos, vel: (n, 3) FP64, updated in place.  acc_cache: (n, 3) FP64, a(x) of the
+ * incoming positions on entry (compute it once with gravity_tree_build +
+ * gravity_forces) and a(x) of the outgoing positions on exit.  theta = 0 uses the
+ * tree walk at theta = 0, i.e. the exact sum. */
+int leapfrog_step(gravity_ctx *ctx, int64_t n, double *pos, double *vel, const double *mass,
+                  double *acc_cache, double dt, int nsteps, double theta, double eps,
+                  const gravity_params *p);
+
+/* Host-buffer evaluation: copy pos_host / mass_host (ideally pinned) to the
+ * device, build the tree, walk it, copy the accelerations to acc_host, and wait
+ * for completion.  Returns any latched device error.  Same semantics as
+ * gravity_tree_build followed by gravity_forces. */
+int gravity_forces_host(gravity_ctx *ctx, int64_t n, const double *pos_host,
+                        const double *mass_host, double theta, double eps,
+                        const gravity_params *p, double *acc_host);
+
+/* Wait for the context's stream, then return (and clear) the first latched device
+ * error, or a CUDA error, or GRAVITY_OK. */
+int gravity_sync(gravity_ctx *ctx);
+
+/* Tree introspection for tests.  Synchronises.  Copies into host memory:
+ *   GRAVITY_DBG_ROOT      4 doubles: lo[3], side
+ *   GRAVITY_DBG_KEYS      n uint64: Morton keys in sorted order
+ *   GRAVITY_DBG_PERM      n int32: caller index of each sorted body
+ *   GRAVITY_DBG_NNODES    1 int32: node count
+ *   GRAVITY_DBG_TOPO      nnodes x 4 int32: first child (-1 = leaf), child count,
+ *                         body begin, body end (sorted order, end exclusive)
+ *   GRAVITY_DBG_DEPTH     nnodes int32
+ *   GRAVITY_DBG_PARENT    nnodes int32 (-1 for the root)
+ *   GRAVITY_DBG_MASS      nnodes double
+ *   GRAVITY_DBG_COM       nnodes x 3 double
+ *   GRAVITY_DBG_QUAD      nnodes x 6 double (xx, yy, zz, xy, xz, yz)
+ * bytes must be at least the size listed; otherwise GRAVITY_E_ARG. */
+enum gravity_debug_item {
+  GRAVITY_DBG_ROOT = 0,
+  GRAVITY_DBG_KEYS = 1,
+  GRAVITY_DBG_PERM = 2,
+  GRAVITY_DBG_NNODES = 3,
+  GRAVITY_DBG_TOPO = 4,
+  GRAVITY_DBG_DEPTH = 5,
+  GRAVITY_DBG_PARENT = 6,
+  GRAVITY_DBG_MASS = 7,
+  GRAVITY_DBG_COM = 8,
+  GRAVITY_DBG_QUAD = 9
+};
+int gravity_debug_export(gravity_ctx *ctx, int what, void *host_dst, size_t bytes);
+
+/* Static description of an error code. */
+const char *gravity_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRAVITY_H */

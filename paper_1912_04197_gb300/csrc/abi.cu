@@ -1,0 +1,353 @@
+// C ABI of libgravity: context, scratch management, argument checks, status
+// latching.  Declarations and their documentation are in include/gravity.h.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "internal.cuh"
+
+struct gravity_ctx {
+  grav::Ctx c;
+};
+
+namespace grav {
+
+// Largest body count: octree node indices (< 2n) must fit the walk's 25-bit fields.
+constexpr int64_t kMaxBodies = (int64_t)1 << 24;
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return GRAVITY_OK;
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return GRAVITY_E_NOMEM;
+  }
+  return GRAVITY_E_CUDA;
+}
+
+namespace {
+
+template <typename T>
+void free_ptr(T *&p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+void free_tree(Tree &t) {
+  free_ptr(t.keys); free_ptr(t.keys_alt); free_ptr(t.idx); free_ptr(t.idx_alt);
+  free_ptr(t.hist); free_ptr(t.scan_aux); free_ptr(t.bbox_part);
+  free_ptr(t.pos_s); free_ptr(t.mass_s); free_ptr(t.body_hi); free_ptr(t.body_lo);
+  free_ptr(t.bchild); free_ptr(t.bparent); free_ptr(t.bfirst); free_ptr(t.blast);
+  free_ptr(t.bplen); free_ptr(t.bnchild); free_ptr(t.bbase);
+  free_ptr(t.topo); free_ptr(t.nparent); free_ptr(t.ndepth); free_ptr(t.narrive);
+  free_ptr(t.nmass); free_ptr(t.ncom); free_ptr(t.nquad); free_ptr(t.nrec0); free_ptr(t.nrec1);
+  free_ptr(t.nquadf);
+}
+
+template <typename T>
+cudaError_t alloc(T *&p, int64_t count) {
+  return cudaMalloc(reinterpret_cast<void **>(&p), sizeof(T) * (size_t)(count > 0 ? count : 1));
+}
+
+int check_params(const gravity_params *p) {
+  if (!p) return GRAVITY_OK;
+  if (!std::isfinite(p->G)) return GRAVITY_E_ARG;
+  if (p->order != 0 && p->order != 2) return GRAVITY_E_ARG;
+  if (p->leaf_max < 1 || p->leaf_max > kMaxLeaf) return GRAVITY_E_ARG;
+  if (p->accum != 0 && p->accum != 1) return GRAVITY_E_ARG;
+  if (p->mac_guard != 0 && p->mac_guard != 1) return GRAVITY_E_ARG;
+  if (p->scheme != 0 && p->scheme != 1) return GRAVITY_E_ARG;
+  return GRAVITY_OK;
+}
+
+int set_device(const Ctx &c) { return cuda_status(cudaSetDevice(c.device)); }
+
+}  // namespace
+
+int ensure_capacity(Ctx *c, int64_t n) {
+  if (n <= c->cap) return GRAVITY_OK;
+  GRAV_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  Tree &t = c->t;
+  free_tree(t);
+  c->cap = 0;
+  int64_t cap = n + n / 8;
+  if (cap < 1024) cap = 1024;
+  if (cap > kMaxBodies) cap = kMaxBodies;
+  const int64_t ntiles = (cap + 2047) / 2048;
+  const int64_t scan_n = (256 * ntiles > cap ? 256 * ntiles : cap);
+  const int64_t nodes = 2 * cap;
+  cudaError_t e = cudaSuccess;
+#define GRAV_ALLOC(p, cnt) if (e == cudaSuccess) e = alloc(p, cnt)
+  GRAV_ALLOC(t.keys, cap); GRAV_ALLOC(t.keys_alt, cap);
+  GRAV_ALLOC(t.idx, cap); GRAV_ALLOC(t.idx_alt, cap);
+  GRAV_ALLOC(t.hist, 256 * ntiles);
+  GRAV_ALLOC(t.scan_aux, scan_n / 4096 + 64);
+  GRAV_ALLOC(t.bbox_part, 6 * 4 * (int64_t)c->num_sms);
+  GRAV_ALLOC(t.pos_s, 3 * cap); GRAV_ALLOC(t.mass_s, cap);
+  GRAV_ALLOC(t.body_hi, cap); GRAV_ALLOC(t.body_lo, cap);
+  GRAV_ALLOC(t.bchild, 2 * cap); GRAV_ALLOC(t.bparent, cap); GRAV_ALLOC(t.bfirst, cap);
+  GRAV_ALLOC(t.blast, cap); GRAV_ALLOC(t.bplen, cap); GRAV_ALLOC(t.bnchild, cap);
+  GRAV_ALLOC(t.bbase, cap);
+  GRAV_ALLOC(t.topo, nodes); GRAV_ALLOC(t.nparent, nodes); GRAV_ALLOC(t.ndepth, nodes);
+  GRAV_ALLOC(t.narrive, nodes);
+  GRAV_ALLOC(t.nmass, nodes); GRAV_ALLOC(t.ncom, 3 * nodes); GRAV_ALLOC(t.nquad, 6 * nodes);
+  GRAV_ALLOC(t.nrec0, nodes); GRAV_ALLOC(t.nrec1, nodes); GRAV_ALLOC(t.nquadf, 2 * nodes);
+#undef GRAV_ALLOC
+  if (e != cudaSuccess) {
+    free_tree(t);
+    return cuda_status(e);
+  }
+  c->cap = cap;
+  return GRAVITY_OK;
+}
+
+}  // namespace grav
+
+using grav::Ctx;
+
+extern "C" {
+
+void gravity_params_default(gravity_params *p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->G = 1.0;
+  p->order = 0;
+  p->leaf_max = 1;
+  p->accum = 0;
+  p->mac_guard = 1;
+  p->scheme = 0;
+  p->walk_cfg = -1;
+}
+
+int gravity_create(gravity_ctx **out, int device, void *cuda_stream) {
+  if (!out) return GRAVITY_E_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) { cudaGetLastError(); return GRAVITY_E_CUDA; }
+  if (device < 0 || device >= ndev) return GRAVITY_E_ARG;
+  gravity_ctx *h = new (std::nothrow) gravity_ctx();
+  if (!h) return GRAVITY_E_NOMEM;
+  Ctx &c = h->c;
+  c.device = device;
+  c.stream = static_cast<cudaStream_t>(cuda_stream);
+  gravity_params_default(&c.params);
+  int rc = grav::set_device(c);
+  if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, device));
+  if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMalloc(&c.d_status, sizeof(unsigned)));
+  if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMalloc(&c.t.geom, 8 * sizeof(double)));
+  if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMalloc(&c.t.bbox_ticket, sizeof(unsigned)));
+  if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMalloc(&c.t.nnodes, sizeof(int32_t)));
+  if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMalloc(&c.t.scalars, 16 * sizeof(uint32_t)));
+  if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMemset(c.d_status, 0, sizeof(unsigned)));
+  if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMemset(c.t.bbox_ticket, 0, sizeof(unsigned)));
+  if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMemset(c.t.nnodes, 0, sizeof(int32_t)));
+  if (rc != GRAVITY_OK) {
+    gravity_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return GRAVITY_OK;
+}
+
+int gravity_destroy(gravity_ctx *h) {
+  if (!h) return GRAVITY_OK;
+  Ctx &c = h->c;
+  cudaSetDevice(c.device);
+  cudaStreamSynchronize(c.stream);
+  grav::free_tree(c.t);
+  grav::free_ptr(c.t.geom); grav::free_ptr(c.t.bbox_ticket); grav::free_ptr(c.t.nnodes);
+  grav::free_ptr(c.t.scalars);
+  grav::free_ptr(c.d_status);
+  grav::free_ptr(c.dir_hi); grav::free_ptr(c.dir_lo);
+  grav::free_ptr(c.h2d_pos); grav::free_ptr(c.h2d_mass); grav::free_ptr(c.h2d_acc);
+  cudaGetLastError();
+  delete h;
+  return GRAVITY_OK;
+}
+
+int gravity_set_stream(gravity_ctx *h, void *cuda_stream) {
+  if (!h) return GRAVITY_E_ARG;
+  h->c.stream = static_cast<cudaStream_t>(cuda_stream);
+  return GRAVITY_OK;
+}
+
+int gravity_tree_build(gravity_ctx *h, int64_t n, const double *pos, const double *mass,
+                       const gravity_params *p) {
+  if (!h || n < 0 || n > grav::kMaxBodies) return GRAVITY_E_ARG;
+  if (n > 0 && (!pos || !mass)) return GRAVITY_E_ARG;
+  int rc = grav::check_params(p);
+  if (rc) return rc;
+  Ctx &c = h->c;
+  if (p) c.params = *p; else gravity_params_default(&c.params);
+  c.have_tree = false;
+  c.n = n;
+  if (n == 0) { c.have_tree = true; return GRAVITY_OK; }
+  if ((rc = grav::set_device(c))) return rc;
+  if ((rc = grav::ensure_capacity(&c, n))) return rc;
+  if ((rc = grav::tree_build(&c, n, pos, mass))) return rc;
+  c.have_tree = true;
+  return GRAVITY_OK;
+}
+
+static int forces_common(gravity_ctx *h, double theta, double eps, double *acc, int32_t *counts) {
+  if (!h || !(theta >= 0.0) || !(eps >= 0.0) || !std::isfinite(theta) || !std::isfinite(eps))
+    return GRAVITY_E_ARG;
+  Ctx &c = h->c;
+  if (!c.have_tree) return GRAVITY_E_NOTREE;
+  if (c.n == 0) return GRAVITY_OK;
+  if (!acc) return GRAVITY_E_ARG;
+  int rc = grav::set_device(c);
+  if (rc) return rc;
+  return grav::walk_forces(&c, theta, eps, acc, counts, nullptr, 0.0);
+}
+
+int gravity_forces(gravity_ctx *h, double theta, double eps, double *acc) {
+  return forces_common(h, theta, eps, acc, nullptr);
+}
+
+int gravity_forces_counted(gravity_ctx *h, double theta, double eps, double *acc,
+                           int32_t *counts) {
+  if (h && h->c.n > 0 && !counts) return GRAVITY_E_ARG;
+  return forces_common(h, theta, eps, acc, counts);
+}
+
+int gravity_direct(gravity_ctx *h, int64_t n, const double *pos, const double *mass, double eps,
+                   double G, double *acc) {
+  if (!h || n < 0 || !(eps >= 0.0) || !std::isfinite(eps) || !std::isfinite(G))
+    return GRAVITY_E_ARG;
+  if (n == 0) return GRAVITY_OK;
+  if (!pos || !mass || !acc) return GRAVITY_E_ARG;
+  int rc = grav::set_device(h->c);
+  if (rc) return rc;
+  return grav::direct_forces(&h->c, n, pos, mass, eps, G, acc);
+}
+
+int leapfrog_step(gravity_ctx *h, int64_t n, double *pos, double *vel, const double *mass,
+                  double *acc_cache, double dt, int nsteps, double theta, double eps,
+                  const gravity_params *p) {
+  if (!h || n < 0 || n > grav::kMaxBodies || nsteps < 0 || !std::isfinite(dt)) return GRAVITY_E_ARG;
+  if (!(theta >= 0.0) || !(eps >= 0.0) || !std::isfinite(theta) || !std::isfinite(eps))
+    return GRAVITY_E_ARG;
+  int rc = grav::check_params(p);
+  if (rc) return rc;
+  if (n == 0 || nsteps == 0) return GRAVITY_OK;
+  if (!pos || !vel || !mass || !acc_cache) return GRAVITY_E_ARG;
+  Ctx &c = h->c;
+  if (p) c.params = *p; else gravity_params_default(&c.params);
+  if ((rc = grav::set_device(c))) return rc;
+  if ((rc = grav::ensure_capacity(&c, n))) return rc;
+  const bool kdk = c.params.scheme == 0;
+  const double h_kick = kdk ? 0.5 * dt : dt;
+  for (int s = 0; s < nsteps; ++s) {
+    if ((rc = grav::launch_kick_drift(&c, n, pos, vel, acc_cache, h_kick, dt))) return rc;
+    c.n = n;
+    if ((rc = grav::tree_build(&c, n, pos, mass))) return rc;
+    c.have_tree = true;
+    if ((rc = grav::walk_forces(&c, theta, eps, acc_cache, nullptr, kdk ? vel : nullptr,
+                                kdk ? h_kick : 0.0)))
+      return rc;
+  }
+  return GRAVITY_OK;
+}
+
+int gravity_sync(gravity_ctx *h) {
+  if (!h) return GRAVITY_E_ARG;
+  Ctx &c = h->c;
+  int rc = grav::set_device(c);
+  if (rc) return rc;
+  cudaError_t e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) return grav::cuda_status(e);
+  unsigned st = 0;
+  e = cudaMemcpy(&st, c.d_status, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return grav::cuda_status(e);
+  if (st) {
+    e = cudaMemset(c.d_status, 0, sizeof(unsigned));
+    if (e != cudaSuccess) return grav::cuda_status(e);
+  }
+  if (st & grav::kErrNonFinite) return GRAVITY_E_NONFINITE;
+  if (st & grav::kErrTimeout) return GRAVITY_E_TIMEOUT;
+  if (st & (grav::kErrStack | grav::kErrTree)) return GRAVITY_E_INTERNAL;
+  return GRAVITY_OK;
+}
+
+int gravity_forces_host(gravity_ctx *h, int64_t n, const double *pos_host, const double *mass_host,
+                        double theta, double eps, const gravity_params *p, double *acc_host) {
+  if (!h || n < 0 || n > grav::kMaxBodies) return GRAVITY_E_ARG;
+  if (n > 0 && (!pos_host || !mass_host || !acc_host)) return GRAVITY_E_ARG;
+  if (!(theta >= 0.0) || !(eps >= 0.0) || !std::isfinite(theta) || !std::isfinite(eps))
+    return GRAVITY_E_ARG;
+  int rc = grav::check_params(p);
+  if (rc) return rc;
+  Ctx &c = h->c;
+  if ((rc = grav::set_device(c))) return rc;
+  if (n > c.h2d_cap) {
+    GRAV_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    grav::free_ptr(c.h2d_pos); grav::free_ptr(c.h2d_mass); grav::free_ptr(c.h2d_acc);
+    c.h2d_cap = 0;
+    GRAV_CUDA_TRY(cudaMalloc(&c.h2d_pos, sizeof(double) * 3 * n));
+    GRAV_CUDA_TRY(cudaMalloc(&c.h2d_mass, sizeof(double) * n));
+    GRAV_CUDA_TRY(cudaMalloc(&c.h2d_acc, sizeof(double) * 3 * n));
+    c.h2d_cap = n;
+  }
+  if (n > 0) {
+    GRAV_CUDA_TRY(cudaMemcpyAsync(c.h2d_pos, pos_host, sizeof(double) * 3 * n,
+                                  cudaMemcpyHostToDevice, c.stream));
+    GRAV_CUDA_TRY(cudaMemcpyAsync(c.h2d_mass, mass_host, sizeof(double) * n,
+                                  cudaMemcpyHostToDevice, c.stream));
+  }
+  if ((rc = gravity_tree_build(h, n, c.h2d_pos, c.h2d_mass, p))) return rc;
+  if ((rc = gravity_forces(h, theta, eps, c.h2d_acc))) return rc;
+  if (n > 0)
+    GRAV_CUDA_TRY(cudaMemcpyAsync(acc_host, c.h2d_acc, sizeof(double) * 3 * n,
+                                  cudaMemcpyDeviceToHost, c.stream));
+  return gravity_sync(h);
+}
+
+int gravity_debug_export(gravity_ctx *h, int what, void *dst, size_t bytes) {
+  if (!h || !dst) return GRAVITY_E_ARG;
+  Ctx &c = h->c;
+  if (!c.have_tree) return GRAVITY_E_NOTREE;
+  int rc = grav::set_device(c);
+  if (rc) return rc;
+  GRAV_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  const grav::Tree &t = c.t;
+  int32_t nn = 0;
+  if (c.n > 0) GRAV_CUDA_TRY(cudaMemcpy(&nn, t.nnodes, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  const void *src = nullptr;
+  size_t need = 0;
+  switch (what) {
+    case GRAVITY_DBG_ROOT: src = t.geom; need = 4 * sizeof(double); break;
+    case GRAVITY_DBG_KEYS: src = t.keys; need = sizeof(uint64_t) * c.n; break;
+    case GRAVITY_DBG_PERM: src = t.idx; need = sizeof(uint32_t) * c.n; break;
+    case GRAVITY_DBG_NNODES:
+      if (bytes < sizeof(int32_t)) return GRAVITY_E_ARG;
+      std::memcpy(dst, &nn, sizeof(int32_t));
+      return GRAVITY_OK;
+    case GRAVITY_DBG_TOPO: src = t.topo; need = sizeof(int4) * nn; break;
+    case GRAVITY_DBG_DEPTH: src = t.ndepth; need = sizeof(int32_t) * nn; break;
+    case GRAVITY_DBG_PARENT: src = t.nparent; need = sizeof(int32_t) * nn; break;
+    case GRAVITY_DBG_MASS: src = t.nmass; need = sizeof(double) * nn; break;
+    case GRAVITY_DBG_COM: src = t.ncom; need = 3 * sizeof(double) * nn; break;
+    case GRAVITY_DBG_QUAD: src = t.nquad; need = 6 * sizeof(double) * nn; break;
+    default: return GRAVITY_E_ARG;
+  }
+  if (bytes < need) return GRAVITY_E_ARG;
+  if (need == 0) return GRAVITY_OK;
+  GRAV_CUDA_TRY(cudaMemcpy(dst, src, need, cudaMemcpyDeviceToHost));
+  return GRAVITY_OK;
+}
+
+const char *gravity_strerror(int code) {
+  switch (code) {
+    case GRAVITY_OK: return "ok";
+    case GRAVITY_E_ARG: return "invalid argument";
+    case GRAVITY_E_NONFINITE: return "non-finite position coordinate";
+    case GRAVITY_E_NOMEM: return "device allocation failed";
+    case GRAVITY_E_CUDA: return "CUDA runtime error";
+    case GRAVITY_E_TIMEOUT: return "bounded device wait ran out";
+    case GRAVITY_E_INTERNAL: return "walk stack exhausted or inconsistent tree";
+    case GRAVITY_E_NOTREE: return "no tree built";
+    default: return "unknown error";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,40 @@
+// Symplectic steppers (Sec. 2.3: semi-implicit Euler and leapfrog) in FP64.
+// Kick-drift: v += h a; x += dt v (one fused pass); the closing kick of the
+// leapfrog is fused into the walk's output (see walk.cu).
+#include "internal.cuh"
+
+namespace grav {
+namespace {
+
+__global__ void k_kick_drift(int64_t n3, double *__restrict__ pos, double *__restrict__ vel,
+                             const double *__restrict__ acc, double h, double dt) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n3) return;
+  double v = __dadd_rn(vel[i], __dmul_rn(h, acc[i]));   // same roundings as written, no FMA
+  vel[i] = v;
+  pos[i] = __dadd_rn(pos[i], __dmul_rn(dt, v));
+}
+
+__global__ void k_kick(int64_t n3, double *__restrict__ vel, const double *__restrict__ acc,
+                       double h) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n3) return;
+  vel[i] = __dadd_rn(vel[i], __dmul_rn(h, acc[i]));
+}
+
+}  // namespace
+
+int launch_kick_drift(Ctx *c, int64_t n, double *pos, double *vel, const double *acc,
+                      double h_kick, double dt) {
+  int64_t n3 = 3 * n;
+  k_kick_drift<<<(unsigned)((n3 + 255) / 256), 256, 0, c->stream>>>(n3, pos, vel, acc, h_kick, dt);
+  return cuda_status(cudaGetLastError());
+}
+
+int launch_kick(Ctx *c, int64_t n, double *vel, const double *acc, double h_kick) {
+  int64_t n3 = 3 * n;
+  k_kick<<<(unsigned)((n3 + 255) / 256), 256, 0, c->stream>>>(n3, vel, acc, h_kick);
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace grav

@@ -1,0 +1,112 @@
+// Internal declarations of libgravity (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gravity.h"
+
+namespace grav {
+
+constexpr int kLevels = 21;          // 63-bit Morton keys: 21 levels of 3 bits
+constexpr int kMaxLeaf = 64;         // largest leaf_max accepted
+
+// Latched device error bits (combined with atomicOr into ctx->d_status).
+enum : unsigned {
+  kErrNonFinite = 1u,
+  kErrStack = 2u,
+  kErrTree = 4u,
+  kErrTimeout = 8u,
+};
+
+struct Tree {
+  // geometry: lo[3], side, scale = 2^21 / side
+  double *geom = nullptr;
+  // keys / sort
+  uint64_t *keys = nullptr, *keys_alt = nullptr;
+  uint32_t *idx = nullptr, *idx_alt = nullptr;   // after the sort: idx = perm (sorted -> caller)
+  uint32_t *hist = nullptr;                     // radix histograms, [256][tiles]
+  uint32_t *scan_aux = nullptr;                 // block sums of the scan
+  double *bbox_part = nullptr;                  // [blocks][6]
+  unsigned *bbox_ticket = nullptr;
+  // sorted bodies
+  double *pos_s = nullptr;                      // (n,3)
+  double *mass_s = nullptr;                     // (n)
+  float4 *body_hi = nullptr;                    // (x_hi, y_hi, z_hi, m)
+  float4 *body_lo = nullptr;                    // (x_lo, y_lo, z_lo, 0)
+  // binary radix tree over n-1 internal nodes; child code >= 0: internal node,
+  // < 0: body ~code
+  int32_t *bchild = nullptr;                    // [2*(n-1)]
+  int32_t *bparent = nullptr;                   // [n-1]
+  int32_t *bfirst = nullptr;                    // [n-1]
+  int32_t *blast = nullptr;                     // [n-1]
+  int32_t *bplen = nullptr;                     // [n-1] common prefix length (bits)
+  uint32_t *bnchild = nullptr;                  // [n-1] octree children (0 if not internal)
+  uint32_t *bbase = nullptr;                    // [n-1] exclusive scan of bnchild
+  uint32_t *scalars = nullptr;                  // small device scalars (scan totals)
+  // octree, capacity 2n nodes
+  int4 *topo = nullptr;                         // first child (-1 leaf), n_child, begin, end
+  int32_t *nparent = nullptr;
+  int32_t *ndepth = nullptr;
+  int32_t *narrive = nullptr;                   // arrival counters of the moment pass
+  int32_t *nnodes = nullptr;                    // device scalar
+  double *nmass = nullptr;                      // FP64 moments
+  double *ncom = nullptr;                       // (k,3)
+  double *nquad = nullptr;                      // (k,6)
+  float4 *nrec0 = nullptr;                      // (com_hi xyz, m)
+  float4 *nrec1 = nullptr;                      // (com_lo xyz, l^2)
+  float4 *nquadf = nullptr;                     // 2 per node: (xx,yy,zz,xy), (xz,yz,0,0)
+};
+
+struct Ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  int64_t cap = 0;             // body capacity of the buffers
+  int64_t n = 0;               // bodies in the current tree
+  bool have_tree = false;
+  gravity_params params{};
+  unsigned *d_status = nullptr;
+  Tree t;
+  // direct-sum staging (caller order hi/lo)
+  float4 *dir_hi = nullptr, *dir_lo = nullptr;
+  int64_t dir_cap = 0;
+  // host-buffer entry point staging
+  double *h2d_pos = nullptr, *h2d_mass = nullptr, *h2d_acc = nullptr;
+  int64_t h2d_cap = 0;
+};
+
+// ---- launchers (tree_build.cu)
+int tree_build(Ctx *c, int64_t n, const double *pos, const double *mass);
+// ---- launchers (walk.cu)
+int walk_forces(Ctx *c, double theta, double eps, double *acc, int32_t *counts,
+                double *vel, double kick);
+// ---- launchers (direct.cu)
+int direct_forces(Ctx *c, int64_t n, const double *pos, const double *mass, double eps,
+                  double G, double *acc);
+// ---- launchers (integrate.cu)
+int launch_kick_drift(Ctx *c, int64_t n, double *pos, double *vel, const double *acc,
+                      double h_kick, double dt);
+int launch_kick(Ctx *c, int64_t n, double *vel, const double *acc, double h_kick);
+
+int ensure_capacity(Ctx *c, int64_t n);
+int cuda_status(cudaError_t e);
+
+// ---- device helpers
+__device__ __forceinline__ void latch_error(unsigned *status, unsigned bit) {
+  atomicOr(status, bit);
+}
+
+// hi/lo split of an FP64 value into two FP32 values with hi + lo ~ x to ~2^-48.
+__device__ __forceinline__ void split_df(double x, float &hi, float &lo) {
+  hi = __double2float_rn(x);
+  lo = __double2float_rn(__dsub_rn(x, (double)hi));
+}
+
+}  // namespace grav
+
+#define GRAV_CUDA_TRY(expr)                         \
+  do {                                              \
+    cudaError_t _e = (expr);                        \
+    if (_e != cudaSuccess) return grav::cuda_status(_e); \
+  } while (0)

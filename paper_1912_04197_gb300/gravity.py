@@ -1,0 +1,254 @@
+"""Thin ctypes binding of libgravity (include/gravity.h): argument marshalling only.
+
+Every function keeps the name of the C entry point it calls.  Tensors are torch
+CUDA tensors (float64, contiguous); work goes to the current torch stream of the
+tensors' device.  Errors raise GravityError carrying the library's code.  There
+is no CPU fallback: if libgravity.so is missing this module fails to import.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+GRAVITY_OK = 0
+GRAVITY_E_ARG = -1
+GRAVITY_E_NONFINITE = -2
+GRAVITY_E_NOMEM = -3
+GRAVITY_E_CUDA = -4
+GRAVITY_E_TIMEOUT = -5
+GRAVITY_E_INTERNAL = -6
+GRAVITY_E_NOTREE = -7
+
+DBG_ROOT, DBG_KEYS, DBG_PERM, DBG_NNODES, DBG_TOPO, DBG_DEPTH, DBG_PARENT, DBG_MASS, DBG_COM, \
+    DBG_QUAD = range(10)
+
+
+class GravityError(RuntimeError):
+    def __init__(self, code: int, where: str = ""):
+        self.code = code
+        super().__init__(f"{where}: {gravity_strerror(code)} ({code})")
+
+
+class gravity_params(ctypes.Structure):
+    _fields_ = [("G", ctypes.c_double), ("order", ctypes.c_int32), ("leaf_max", ctypes.c_int32),
+                ("accum", ctypes.c_int32), ("mac_guard", ctypes.c_int32),
+                ("scheme", ctypes.c_int32), ("walk_cfg", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
+
+
+def _load() -> ctypes.CDLL:
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libgravity.so not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P, I64, D, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+    PP = ctypes.POINTER(gravity_params)
+    sig = {
+        "gravity_params_default": (None, [PP]),
+        "gravity_create": (I, [ctypes.POINTER(P), I, P]),
+        "gravity_destroy": (I, [P]),
+        "gravity_set_stream": (I, [P, P]),
+        "gravity_tree_build": (I, [P, I64, P, P, PP]),
+        "gravity_forces": (I, [P, D, D, P]),
+        "gravity_forces_counted": (I, [P, D, D, P, P]),
+        "gravity_direct": (I, [P, I64, P, P, D, D, P]),
+        "leapfrog_step": (I, [P, I64, P, P, P, P, D, I, D, D, PP]),
+        "gravity_forces_host": (I, [P, I64, P, P, D, D, PP, P]),
+        "gravity_sync": (I, [P]),
+        "gravity_debug_export": (I, [P, I, P, ctypes.c_size_t]),
+        "gravity_strerror": (ctypes.c_char_p, [I]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def gravity_strerror(code: int) -> str:
+    return _lib.gravity_strerror(int(code)).decode()
+
+
+def _check(rc: int, where: str):
+    if rc != GRAVITY_OK:
+        raise GravityError(rc, where)
+
+
+def params(**kw) -> gravity_params:
+    """gravity_params with the library defaults, then the given fields."""
+    p = gravity_params()
+    _lib.gravity_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _dev(t: torch.Tensor, name: str, shape_last=None) -> ctypes.c_void_p:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype not in (torch.float64, torch.int32) or not t.is_contiguous():
+        raise TypeError(f"{name} must be contiguous float64/int32")
+    if shape_last is not None and t.numel() and t.shape[-1] != shape_last:
+        raise ValueError(f"{name} must have trailing dimension {shape_last}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_of(device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+class Context:
+    """Owns a gravity_ctx (scratch memory, current tree) on one device."""
+
+    def __init__(self, device=None):
+        dev = torch.device("cuda", torch.cuda.current_device() if device is None else
+                           torch.device(device).index or 0)
+        self.device = dev
+        h = ctypes.c_void_p()
+        _check(_lib.gravity_create(ctypes.byref(h), dev.index, _stream_of(dev)), "gravity_create")
+        self._h = h
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if self._h is None:
+            raise RuntimeError("context destroyed")
+        _lib.gravity_set_stream(self._h, _stream_of(self.device))
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _lib.gravity_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gravity_create(device=None) -> Context:
+    return Context(device)
+
+
+def gravity_destroy(ctx: Context):
+    ctx.close()
+
+
+def gravity_tree_build(ctx: Context, pos: torch.Tensor, mass: torch.Tensor, p=None):
+    n = pos.shape[0] if pos.ndim else 0
+    if mass.numel() != n:
+        raise ValueError("pos and mass lengths differ")
+    _check(_lib.gravity_tree_build(ctx.handle, n, _dev(pos, "pos", 3), _dev(mass, "mass"),
+                                   None if p is None else ctypes.byref(p)), "gravity_tree_build")
+
+
+def gravity_forces(ctx: Context, theta: float, eps: float, acc: torch.Tensor) -> torch.Tensor:
+    _check(_lib.gravity_forces(ctx.handle, float(theta), float(eps), _dev(acc, "acc", 3)),
+           "gravity_forces")
+    return acc
+
+
+def gravity_forces_counted(ctx: Context, theta: float, eps: float, acc: torch.Tensor,
+                           counts: torch.Tensor) -> torch.Tensor:
+    _check(_lib.gravity_forces_counted(ctx.handle, float(theta), float(eps), _dev(acc, "acc", 3),
+                                       _dev(counts, "counts", 2)), "gravity_forces_counted")
+    return acc
+
+
+def gravity_direct(ctx: Context, pos, mass, eps: float, G: float, acc) -> torch.Tensor:
+    _check(_lib.gravity_direct(ctx.handle, pos.shape[0], _dev(pos, "pos", 3), _dev(mass, "mass"),
+                               float(eps), float(G), _dev(acc, "acc", 3)), "gravity_direct")
+    return acc
+
+
+def leapfrog_step(ctx: Context, pos, vel, mass, acc_cache, dt: float, nsteps: int, theta: float,
+                  eps: float, p=None):
+    _check(_lib.leapfrog_step(ctx.handle, pos.shape[0], _dev(pos, "pos", 3), _dev(vel, "vel", 3),
+                              _dev(mass, "mass"), _dev(acc_cache, "acc_cache", 3), float(dt),
+                              int(nsteps), float(theta), float(eps),
+                              None if p is None else ctypes.byref(p)), "leapfrog_step")
+
+
+def gravity_forces_host(ctx: Context, pos_host: torch.Tensor, mass_host: torch.Tensor,
+                        theta: float, eps: float, p, acc_host: torch.Tensor):
+    for name, t in (("pos_host", pos_host), ("mass_host", mass_host), ("acc_host", acc_host)):
+        if t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+            raise TypeError(f"{name} must be a contiguous float64 host tensor")
+    _check(_lib.gravity_forces_host(ctx.handle, pos_host.shape[0],
+                                    ctypes.c_void_p(pos_host.data_ptr()),
+                                    ctypes.c_void_p(mass_host.data_ptr()), float(theta),
+                                    float(eps), None if p is None else ctypes.byref(p),
+                                    ctypes.c_void_p(acc_host.data_ptr())), "gravity_forces_host")
+    return acc_host
+
+
+def gravity_sync(ctx: Context):
+    _check(_lib.gravity_sync(ctx.handle), "gravity_sync")
+
+
+_DBG_DTYPES = {DBG_ROOT: (np.float64, 4), DBG_KEYS: (np.uint64, 1), DBG_PERM: (np.uint32, 1),
+               DBG_TOPO: (np.int32, 4), DBG_DEPTH: (np.int32, 1), DBG_PARENT: (np.int32, 1),
+               DBG_MASS: (np.float64, 1), DBG_COM: (np.float64, 3), DBG_QUAD: (np.float64, 6)}
+
+
+def gravity_debug_export(ctx: Context, what: int, n: int) -> np.ndarray:
+    """Copy a tree array to a numpy array (n = bodies for KEYS/PERM, ignored otherwise)."""
+    if what == DBG_NNODES:
+        out = np.zeros(1, np.int32)
+        _check(_lib.gravity_debug_export(ctx.handle, what, out.ctypes.data_as(ctypes.c_void_p), 4),
+               "gravity_debug_export")
+        return out
+    dt, width = _DBG_DTYPES[what]
+    if what == DBG_ROOT:
+        count = 1
+    elif what in (DBG_KEYS, DBG_PERM):
+        count = n
+    else:
+        count = int(gravity_debug_export(ctx, DBG_NNODES, n)[0])
+    out = np.zeros((count, width) if width > 1 and what != DBG_ROOT else (count * width,), dt)
+    _check(_lib.gravity_debug_export(ctx.handle, what, out.ctypes.data_as(ctypes.c_void_p),
+                                     out.nbytes), "gravity_debug_export")
+    return out
+
+
+# ----------------------------------------------------------------- convenience
+class Gravity:
+    """Octree gravity on one device: build + forces + direct + stepping."""
+
+    def __init__(self, device=None, **param_kw):
+        self.ctx = Context(device)
+        self.p = params(**param_kw)
+
+    def tree_build(self, pos, mass):
+        gravity_tree_build(self.ctx, pos, mass, self.p)
+
+    def forces(self, theta, eps, acc=None, n=None):
+        if acc is None:
+            acc = torch.empty((n, 3), dtype=torch.float64, device=self.ctx.device)
+        return gravity_forces(self.ctx, theta, eps, acc)
+
+    def evaluate(self, pos, mass, theta, eps, acc=None):
+        self.tree_build(pos, mass)
+        return self.forces(theta, eps, acc, n=pos.shape[0])
+
+    def direct(self, pos, mass, eps, acc=None):
+        if acc is None:
+            acc = torch.empty_like(pos)
+        return gravity_direct(self.ctx, pos, mass, eps, self.p.G, acc)
+
+    def step(self, pos, vel, mass, acc_cache, dt, nsteps, theta, eps):
+        leapfrog_step(self.ctx, pos, vel, mass, acc_cache, dt, nsteps, theta, eps, self.p)
+
+    def sync(self):
+        gravity_sync(self.ctx)

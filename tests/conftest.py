@@ -14,6 +14,7 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: long-running CPU test")
     config.addinivalue_line("markers", "oracle: pins of the CPU oracle")
+    config.addinivalue_line("markers", "abi: C-ABI library build and exports")
 
 
 def load_golden(name):
