@@ -1,0 +1,377 @@
+#!/usr/bin/env python3
+"""Octree body-forces/s at N = 1,048,576, theta = 0.5 on GB300, vs the direct sum.
+
+Workload: the clumpy aggregate (64 truncated Plummer spheres of scale 0.05 with
+centres uniform in the unit sphere, equal masses, at rest), eps = 1e-3, seeded
+synthetic data.  One step = one full force evaluation: gravity_tree_build (root
+cube, Morton keys, radix sort, octree, moments) + gravity_forces (the walk).
+The reported (order, leaf_max) is the fastest that meets the <= 1e-3 median force
+error against the direct sum, which is checked on every run.
+
+Timing: W warm-up steps, then exactly K steps timed with CUDA events on the
+launching stream; the L2 (129 MB) is flushed by writing a 256 MB buffer before each
+timed step (outside the events).  Under torchrun each rank evaluates its own
+independent cloud (weak scaling, replicas only); rank 0 prints the max over ranks.
+
+--impl reference times the FP64 CPU oracle on the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "octree body-forces/s at N=1M, θ=0.5 vs direct N² on GB300 at ≤1e-3 force error"
+UNIT = "body-forces/s"
+# Algorithmic FLOPs per unit of walk work (counted from the formulas, FMA = 2):
+#   point term (node monopole or body-body): d 3, r^2 6, 1/sqrt 2, r^-3 2, m r^-3 1, accumulate 6
+#   quadrupole node term: d 3, r^2 6, 1/sqrt 2, r^-3..r^-7 4, Q d 15, d.Q d 5, 5/2 dQd r^-7 2,
+#                         m r^-3 + that 2, accumulate s d - Q d r^-5 12
+#   opening test: d 3, D^2 5, theta^2 D^2 1, compare 1
+FLOP_POINT, FLOP_QUAD, FLOP_MAC = 20, 51, 10
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=1_048_576)
+    ap.add_argument("--theta", type=float, default=0.5)
+    ap.add_argument("--eps", type=float, default=1e-3)
+    ap.add_argument("--order", type=int, default=2)
+    ap.add_argument("--leaf-max", type=int, default=16)
+    ap.add_argument("--accum", type=int, default=0)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-direct", action="store_true", help="skip the direct-sum comparison")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=65536, help="oracle targets in cpu_baseline")
+    return ap.parse_args()
+
+
+def workload(args):
+    return {"workload": f"clumpy aggregate: {args.n} bodies in 64 Plummer spheres (a=0.05, r<=10a) "
+                        f"uniform in the unit sphere, equal masses, at rest",
+            "n": args.n, "theta": args.theta, "eps": args.eps, "order": args.order,
+            "leaf_max": args.leaf_max, "accum": "fp32-two-sum" if args.accum == 0 else "fp64",
+            "mac_guard": 1, "step": "tree build + walk (one full force evaluation)",
+            "l2": "flushed before each timed step (256 MB write)", "seed": args.seed}
+
+
+def gen(args, rank):
+    from paper_1912_04197_gb300 import inputs
+    return inputs.clumpy_plummer(args.n, seed=args.seed + rank)
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.proc = None
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", gpu_id, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower() in ("active", "1"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows
+                                                         if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_eval(pos, m, args, ntarg):
+    """Oracle tree build (all bodies) + walk of ntarg seeded targets; returns the
+    extrapolated body-forces/s of a full evaluation and the times."""
+    import oracle
+    from paper_1912_04197_gb300 import inputs
+    idx = inputs.subset(len(pos), ntarg, seed=7)
+    t0 = time.perf_counter()
+    tree = oracle.Tree(pos, m, leaf_max=args.leaf_max, order=args.order)
+    t1 = time.perf_counter()
+    tree.forces(args.theta, args.eps, targets=idx)
+    t2 = time.perf_counter()
+    t_build, t_walk = t1 - t0, t2 - t1
+    full = t_build + t_walk * len(pos) / len(idx)
+    return len(pos) / full, t_build, t_walk
+
+
+def omp_threads():
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
+
+
+def cpu_baseline(pos, m, args):
+    val, tb, tw = oracle_eval(pos, m, args, args.cpu_sample)
+    return {"value": val, "unit": UNIT, "cores": omp_threads(), "kind": "oracle",
+            "sample": f"FP64 oracle: full tree build of all {len(pos)} bodies "
+                      f"({tb:.2f} s, 1 thread) + walk of {args.cpu_sample} seeded targets "
+                      f"({tw:.2f} s, OpenMP); value = N / (build + walk time scaled to N targets)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    pos, _, m = gen(args, 0)
+    # each step: full build + walk of a target sample sized so K+W steps take ~2-3 minutes
+    ntarg = 2048 if args.steps + args.warmup > 40 else 16384
+    for _ in range(args.warmup):
+        oracle_eval(pos, m, args, ntarg)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(oracle_eval(pos, m, args, ntarg)[0])
+    wall = time.perf_counter() - t0
+    value = float(statistics.median(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * args.n / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload(args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": omp_threads(), "kind": "oracle",
+                             "sample": f"per step: full FP64 tree build of {args.n} bodies + walk "
+                                       f"of {ntarg} seeded targets, extrapolated to N targets; "
+                                       f"median of {args.steps} steps ({wall:.1f} s wall)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def walk_traffic(order):
+    """DRAM bytes per walk launch from the committed ncu summary, if the walk source
+    has not changed since it was captured (else None)."""
+    path = os.path.join(ROOT, "profiles", "walk_ncu_clumpy1M.txt")
+    src = os.path.join(ROOT, "paper_1912_04197_gb300", "csrc", "walk.cu")
+    if not os.path.exists(path):
+        return None
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("walk_source_sha256_16") != h:
+        return None
+    key = f"dram_bytes_per_launch_order{order}"
+    return float(vals[key]) if key in vals else None
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_1912_04197_gb300 import gravity as g
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    pos, _, m = gen(args, rank)
+    n = len(pos)
+    P = torch.tensor(pos, device=dev)
+    M = torch.tensor(m, device=dev)
+    acc = torch.empty_like(P)
+    ctx = g.Context(dev)
+    p = g.params(order=args.order, leaf_max=args.leaf_max, accum=args.accum)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        g.gravity_tree_build(ctx, P, M, p)
+        g.gravity_forces(ctx, args.theta, args.eps, acc)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    g.gravity_sync(ctx)
+
+    # algorithmic work of one walk launch (exact per-body decision counts)
+    cnt = torch.empty((n, 3), dtype=torch.int32, device=dev)
+    g.gravity_tree_build(ctx, P, M, p)
+    g.gravity_forces_counted(ctx, args.theta, args.eps, acc, cnt)
+    g.gravity_sync(ctx)
+    c = cnt.to(torch.int64).sum(0).cpu().numpy()
+    node_terms, body_terms, tests = int(c[0]), int(c[1]), int(c[2])
+    f_node = FLOP_QUAD if args.order == 2 else FLOP_POINT
+    walk_flops = node_terms * f_node + body_terms * FLOP_POINT + tests * FLOP_MAC
+
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = str(getattr(props, "uuid", local_rank))
+    if gpu_id and not gpu_id.startswith("GPU-") and len(gpu_id) == 36:
+        gpu_id = "GPU-" + gpu_id
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = g.gravity_stats(ctx)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(gpu_id)
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        e0, e1, e2 = ev[k]
+        e0.record(stream)
+        g.gravity_tree_build(ctx, P, M, p)
+        e1.record(stream)
+        g.gravity_forces(ctx, args.theta, args.eps, acc)
+        e2.record(stream)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    g.gravity_sync(ctx)
+    launches = g.gravity_stats(ctx) - launches0
+    t_build = sum(e0.elapsed_time(e1) for e0, e1, _ in ev) / args.steps
+    t_walk = sum(e1.elapsed_time(e2) for _, e1, e2 in ev) / args.steps
+    t_step = t_build + t_walk
+    t_max = t_step
+    if world > 1:
+        t = torch.tensor([t_step], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * n / (t_max * 1e-3)
+
+    # error against the direct sum, and the direct-sum throughput on the same GPU
+    extra = {}
+    if not args.no_direct:
+        accd = torch.empty_like(P)
+        g.gravity_direct(ctx, P, M, args.eps, 1.0, accd)       # warm-up
+        d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        d0.record(stream)
+        g.gravity_direct(ctx, P, M, args.eps, 1.0, accd)
+        d1.record(stream)
+        torch.cuda.synchronize(dev)
+        t_dir = d0.elapsed_time(d1)
+        step()
+        g.gravity_sync(ctx)
+        rel = (torch.linalg.norm(acc - accd, dim=1) / torch.linalg.norm(accd, dim=1)).cpu().numpy()
+        med, p99 = float(np.median(rel)), float(np.quantile(rel, 0.99))
+        extra["error_vs_direct"] = {"median": med, "p99": p99, "meets_1e-3": med <= 1e-3,
+                                    "reference": "GPU direct sum (FP32 hi/lo pair terms, "
+                                                 "within 1e-6 of FP64 per tests)"}
+        extra["direct"] = {"ms": t_dir, "value": n / (t_dir * 1e-3), "unit": UNIT,
+                           "speedup_of_tree": (n / (t_step * 1e-3)) / (n / (t_dir * 1e-3)),
+                           "interactions_per_s": n * (n - 1) / (t_dir * 1e-3),
+                           "flops_per_s": FLOP_POINT * n * (n - 1) / (t_dir * 1e-3)}
+
+    # rooflines: the walk is FP32-ALU bound (no dense contraction, no tensor cores)
+    sm_mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
+    peak_clock = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6
+    _, probe = g.gravity_probe_fp32(ctx, 20000)
+    achieved = walk_flops / (t_walk * 1e-3)
+    roof = {"bound": "alu", "kernel": "k_walk", "achieved": achieved / 1e12,
+            "peak": peak_clock / 1e12, "unit": "TFLOP/s", "frac": achieved / peak_clock,
+            "traffic": walk_traffic(args.order),
+            "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 "
+                          f"x {sm_mhz:.0f} MHz (median SM clock sampled in the timed region)",
+            "fp32_probe_tflops": probe / 1e12, "frac_of_probe": achieved / probe,
+            "walk_ms": t_walk, "build_ms": t_build,
+            "work_per_launch": {"node_terms": node_terms, "body_terms": body_terms,
+                                "opening_tests": tests, "flops": walk_flops,
+                                "flop_per_unit": {"node_term": f_node, "body_term": FLOP_POINT,
+                                                  "opening_test": FLOP_MAC}}}
+
+    e2e = None
+    if not args.no_e2e:
+        ph = torch.tensor(pos).pin_memory()
+        mh = torch.tensor(m).pin_memory()
+        ah = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+        g.gravity_forces_host(ctx, ph, mh, args.theta, args.eps, p, ah)
+        ke = min(args.steps, 10)
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            g.gravity_forces_host(ctx, ph, mh, args.theta, args.eps, p, ah)
+        te = (time.perf_counter() - t0) / ke
+        tt = torch.tensor([te], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * n / float(tt.item()), "unit": UNIT,
+               "h2d_bytes_per_step": int(ph.nbytes + mh.nbytes), "d2h_bytes_per_step": int(ah.nbytes),
+               "ms_per_step": 1e3 * float(tt.item()),
+               "api": "gravity_forces_host (pinned host buffers, copies + build + walk + sync)"}
+
+    if rank != 0:
+        return 0
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(pos, m, args)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "dtype_note": "FP32 pair terms and opening tests on hi/lo coordinates; FP64 moments, "
+                          "FP64 decisions in the guard band, FP64 outputs",
+            "data": "synthetic", "config": workload(args), "phases_ms": {"build": t_build, "walk": t_walk},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "gpu_launches_per_step": launches / args.steps, "clocks": clk,
+            "timed_wall_s": wall}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        return run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -99,8 +99,9 @@ int gravity_tree_build(gravity_ctx *ctx, int64_t n, const double *pos, const dou
 int gravity_forces(gravity_ctx *ctx, double theta, double eps, double *acc);
 
 /* As gravity_forces, and also writes per-body decision counts (caller order,
- * int32 (n, 2): node terms accepted, body-to-body terms excluding the body
- * itself) to the device array counts.  Slower; meant for tests. */
+ * int32 (n, 3): node terms accepted, body-to-body terms excluding the body
+ * itself, opening tests of Eq. (accuracy) evaluated) to the device array counts.
+ * Slower; meant for tests and for counting the walk's algorithmic work. */
 int gravity_forces_counted(gravity_ctx *ctx, double theta, double eps, double *acc,
                            int32_t *counts);
 
@@ -160,6 +161,15 @@ enum gravity_debug_item {
   GRAVITY_DBG_QUAD = 9
 };
 int gravity_debug_export(gravity_ctx *ctx, int what, void *host_dst, size_t bytes);
+
+/* Number of kernels this context has enqueued since it was created (host-side
+ * counter, no synchronisation). */
+int gravity_stats(gravity_ctx *ctx, int64_t *launches);
+
+/* Measure the FP32 FMA throughput of the device: a grid of 8 blocks per SM runs
+ * independent FFMA chains for `iters` x 16 rounds.  Synchronises.  *ms = kernel
+ * time, *flops = achieved FLOP/s (2 per FMA).  Used as the measured ALU roofline. */
+int gravity_probe_fp32(gravity_ctx *ctx, int64_t iters, double *ms, double *flops);
 
 /* Static description of an error code. */
 const char *gravity_strerror(int code);

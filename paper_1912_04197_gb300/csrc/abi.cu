@@ -336,6 +336,19 @@ int gravity_debug_export(gravity_ctx *h, int what, void *dst, size_t bytes) {
   return GRAVITY_OK;
 }
 
+int gravity_stats(gravity_ctx *h, int64_t *launches) {
+  if (!h || !launches) return GRAVITY_E_ARG;
+  *launches = h->c.launches;
+  return GRAVITY_OK;
+}
+
+int gravity_probe_fp32(gravity_ctx *h, int64_t iters, double *ms, double *flops) {
+  if (!h || iters < 1 || !ms || !flops) return GRAVITY_E_ARG;
+  int rc = grav::set_device(h->c);
+  if (rc) return rc;
+  return grav::probe_fp32(&h->c, iters, ms, flops);
+}
+
 const char *gravity_strerror(int code) {
   switch (code) {
     case GRAVITY_OK: return "ok";

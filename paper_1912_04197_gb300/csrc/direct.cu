@@ -105,9 +105,11 @@ int direct_forces(Ctx *c, int64_t n, const double *pos, const double *mass, doub
     c->dir_cap = n;
   }
   k_split<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(pos, mass, n, c->dir_hi, c->dir_lo);
+  ++c->launches;
   const int64_t per_block = (int64_t)kDirThreads * kDirPerThread;
   k_direct<<<(unsigned)((n + per_block - 1) / per_block), kDirThreads, 0, c->stream>>>(
       c->dir_hi, c->dir_lo, n, (float)(eps * eps), G, acc);
+  ++c->launches;
   return cuda_status(cudaGetLastError());
 }
 

@@ -28,12 +28,14 @@ int launch_kick_drift(Ctx *c, int64_t n, double *pos, double *vel, const double 
                       double h_kick, double dt) {
   int64_t n3 = 3 * n;
   k_kick_drift<<<(unsigned)((n3 + 255) / 256), 256, 0, c->stream>>>(n3, pos, vel, acc, h_kick, dt);
+  ++c->launches;
   return cuda_status(cudaGetLastError());
 }
 
 int launch_kick(Ctx *c, int64_t n, double *vel, const double *acc, double h_kick) {
   int64_t n3 = 3 * n;
   k_kick<<<(unsigned)((n3 + 255) / 256), 256, 0, c->stream>>>(n3, vel, acc, h_kick);
+  ++c->launches;
   return cuda_status(cudaGetLastError());
 }
 

@@ -67,6 +67,7 @@ struct Ctx {
   bool have_tree = false;
   gravity_params params{};
   unsigned *d_status = nullptr;
+  int64_t launches = 0;        // kernels enqueued by this context (introspection)
   Tree t;
   // direct-sum staging (caller order hi/lo)
   float4 *dir_hi = nullptr, *dir_lo = nullptr;
@@ -88,6 +89,9 @@ int direct_forces(Ctx *c, int64_t n, const double *pos, const double *mass, doub
 int launch_kick_drift(Ctx *c, int64_t n, double *pos, double *vel, const double *acc,
                       double h_kick, double dt);
 int launch_kick(Ctx *c, int64_t n, double *vel, const double *acc, double h_kick);
+
+// ---- probe.cu
+int probe_fp32(Ctx *c, int64_t iters, double *ms, double *flops);
 
 int ensure_capacity(Ctx *c, int64_t n);
 int cuda_status(cudaError_t e);

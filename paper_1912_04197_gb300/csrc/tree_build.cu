@@ -195,8 +195,10 @@ int exclusive_scan(Ctx *c, uint32_t *data, int64_t n, uint32_t *total_out) {
   if (n <= 0) return GRAVITY_OK;
   int nb = (int)((n + kScanTile - 1) / kScanTile);
   k_scan_tiles<<<nb, kScanThreads, 0, c->stream>>>(data, n, c->t.scan_aux);
+  ++c->launches;
   k_scan_sums<<<1, kScanThreads, 0, c->stream>>>(c->t.scan_aux, nb, total_out);
-  if (nb > 1) k_scan_add<<<nb, kScanThreads, 0, c->stream>>>(data, n, c->t.scan_aux);
+  ++c->launches;
+  if (nb > 1) { k_scan_add<<<nb, kScanThreads, 0, c->stream>>>(data, n, c->t.scan_aux); ++c->launches; }
   return cuda_status(cudaGetLastError());
 }
 
@@ -269,9 +271,11 @@ int radix_sort(Ctx *c, int64_t n) {
   for (int pass = 0; pass < 8; ++pass) {
     int shift = 8 * pass;
     k_rs_hist<<<ntiles, kRsThreads, 0, c->stream>>>(ka, n, shift, t.hist, ntiles);
+    ++c->launches;
     int rc = exclusive_scan(c, t.hist, (int64_t)256 * ntiles, nullptr);
     if (rc) return rc;
     k_rs_scatter<<<ntiles, kRsThreads, 0, c->stream>>>(ka, va, kb, vb, n, shift, t.hist, ntiles);
+    ++c->launches;
     uint64_t *tk = ka; ka = kb; kb = tk;
     uint32_t *tv = va; va = vb; vb = tv;
   }
@@ -613,26 +617,32 @@ int tree_build(Ctx *c, int64_t n, const double *pos, const double *mass) {
   int nb = (int)nb64;
   if (nb < 1) nb = 1;
   k_bbox<<<nb, kBBoxThreads, 0, s>>>(pos, n, t.bbox_part, t.bbox_ticket, t.geom, c->d_status);
+  ++c->launches;
   // a2: keys
   k_keys<<<blocks_for(n, 256), 256, 0, s>>>(pos, n, t.geom, t.keys, t.idx);
+  ++c->launches;
   // a3: sort
   int rc = radix_sort(c, n);
   if (rc) return rc;
   // a4: gather sorted bodies
   k_gather<<<blocks_for(n, 256), 256, 0, s>>>(pos, mass, t.idx, n, t.pos_s, t.mass_s, t.body_hi,
                                                t.body_lo);
+  ++c->launches;
   const int cap_nodes = (int)(2 * c->cap);
   if (n == 1) {
     k_single_root<<<1, 1, 0, s>>>(t.topo, t.ndepth, t.nparent, t.nnodes);
+    ++c->launches;
   } else {
     int ni = (int)(n - 1);
     // a5: binary radix tree
     k_radix_tree<<<blocks_for(ni, 256), 256, 0, s>>>(t.keys, (int)n, t.bchild, t.bparent, t.bfirst,
                                                      t.blast, t.bplen);
+    ++c->launches;
     // a6: octree
     k_oct_count<<<blocks_for(ni, 256), 256, 0, s>>>((int)n, leaf_max, t.bchild, t.bparent,
                                                     t.bfirst, t.blast, t.bplen, t.bnchild,
                                                     c->d_status);
+    ++c->launches;
     uint32_t *base = t.bbase;
     GRAV_CUDA_TRY(cudaMemcpyAsync(base, t.bnchild, sizeof(uint32_t) * ni,
                                   cudaMemcpyDeviceToDevice, s));
@@ -642,8 +652,10 @@ int tree_build(Ctx *c, int64_t n, const double *pos, const double *mass) {
     k_oct_write<<<blocks_for(ni, 256), 256, 0, s>>>((int)n, leaf_max, t.bchild, t.bfirst, t.blast,
                                                     t.bplen, t.bnchild, base, total, t.topo,
                                                     t.ndepth, t.nnodes, cap_nodes, c->d_status);
+    ++c->launches;
     k_oct_parent<<<blocks_for(cap_nodes, 256), 256, 0, s>>>(cap_nodes, t.topo, t.nnodes,
                                                             t.nparent, c->d_status);
+    ++c->launches;
   }
   // a7: moments
   GRAV_CUDA_TRY(cudaMemsetAsync(t.narrive, 0, sizeof(int32_t) * cap_nodes, s));
@@ -651,6 +663,7 @@ int tree_build(Ctx *c, int64_t n, const double *pos, const double *mass) {
             t.nmass, t.ncom, t.nquad, t.nrec0, t.nrec1, t.nquadf, c->params.order, cap_nodes,
             (int)n, c->d_status};
   k_moments<<<blocks_for(cap_nodes, 256), 256, 0, s>>>(A);
+  ++c->launches;
   return cuda_status(cudaGetLastError());
 }
 

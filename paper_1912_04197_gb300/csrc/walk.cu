@@ -206,7 +206,7 @@ k_walk(WalkArgs A) {
   const float eps2 = A.eps2;
 
   Accum<ACC64> acc;
-  int c_m2p = 0, c_p2p = 0;
+  int c_m2p = 0, c_p2p = 0, c_tests = 0;
   int nmono = 0, nquad = 0;
   int sp = 0;
   bool abort = false;
@@ -306,6 +306,14 @@ k_walk(WalkArgs A) {
         if (!guard_any && l2 < theta2f * dmin2 * 0.999f) accm = omask;
         else if (l2 > theta2f * dmax2 * 1.001f) openm = omask;
         else mixed = true;
+      }
+    }
+    if (COUNT) {                               // MAC tests per body (introspection only)
+      for (int j = 0; j < nitems; ++j) {
+        const bool sj = __shfl_sync(0xffffffffu, single, j);
+        const unsigned mj = __shfl_sync(0xffffffffu, omask, j);
+        const int bj = __shfl_sync(0xffffffffu, tp.z, j), ej = __shfl_sync(0xffffffffu, tp.w, j);
+        if (!sj && ((mj >> lane) & 1u) && !(A.mac_guard && bj <= gi && gi < ej)) ++c_tests;
       }
     }
     // ---- exact per-lane test for mixed nodes
@@ -452,8 +460,9 @@ k_walk(WalkArgs A) {
     A.vel[3 * ci + 2] = __dadd_rn(A.vel[3 * ci + 2], __dmul_rn(A.kick, az));
   }
   if (COUNT) {
-    A.counts[2 * ci] = c_m2p;
-    A.counts[2 * ci + 1] = c_p2p;
+    A.counts[3 * ci] = c_m2p;
+    A.counts[3 * ci + 1] = c_p2p;
+    A.counts[3 * ci + 2] = c_tests;
   }
 }
 
@@ -471,6 +480,7 @@ int launch_walk(Ctx *c, const WalkArgs &A) {
   const int warps = (A.n + 31) / 32;
   const int blocks = (warps + kWalkWarps - 1) / kWalkWarps;
   kern<<<blocks, 32 * kWalkWarps, smem, c->stream>>>(A);
+  ++c->launches;
   return cuda_status(cudaGetLastError());
 }
 

@@ -62,6 +62,8 @@ def _load() -> ctypes.CDLL:
         "gravity_sync": (I, [P]),
         "gravity_debug_export": (I, [P, I, P, ctypes.c_size_t]),
         "gravity_strerror": (ctypes.c_char_p, [I]),
+        "gravity_stats": (I, [P, ctypes.POINTER(I64)]),
+        "gravity_probe_fp32": (I, [P, I64, ctypes.POINTER(D), ctypes.POINTER(D)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -162,7 +164,7 @@ def gravity_forces(ctx: Context, theta: float, eps: float, acc: torch.Tensor) ->
 def gravity_forces_counted(ctx: Context, theta: float, eps: float, acc: torch.Tensor,
                            counts: torch.Tensor) -> torch.Tensor:
     _check(_lib.gravity_forces_counted(ctx.handle, float(theta), float(eps), _dev(acc, "acc", 3),
-                                       _dev(counts, "counts", 2)), "gravity_forces_counted")
+                                       _dev(counts, "counts", 3)), "gravity_forces_counted")
     return acc
 
 
@@ -191,6 +193,21 @@ def gravity_forces_host(ctx: Context, pos_host: torch.Tensor, mass_host: torch.T
                                     float(eps), None if p is None else ctypes.byref(p),
                                     ctypes.c_void_p(acc_host.data_ptr())), "gravity_forces_host")
     return acc_host
+
+
+def gravity_stats(ctx: Context) -> int:
+    """Kernels enqueued by this context so far."""
+    v = ctypes.c_int64(0)
+    _check(_lib.gravity_stats(ctx.handle, ctypes.byref(v)), "gravity_stats")
+    return int(v.value)
+
+
+def gravity_probe_fp32(ctx: Context, iters: int = 20000):
+    """(ms, FLOP/s) of the FFMA-chain probe."""
+    ms, fl = ctypes.c_double(0), ctypes.c_double(0)
+    _check(_lib.gravity_probe_fp32(ctx.handle, int(iters), ctypes.byref(ms), ctypes.byref(fl)),
+           "gravity_probe_fp32")
+    return ms.value, fl.value
 
 
 def gravity_sync(ctx: Context):

@@ -30,7 +30,7 @@ def _gpu_forces(g, pos, m, theta, eps, counted=False, **kw):
     g.gravity_tree_build(ctx, P, M, g.params(**kw))
     acc = torch.empty_like(P)
     if counted:
-        cnt = torch.empty((len(pos), 2), dtype=torch.int32, device="cuda")
+        cnt = torch.empty((len(pos), 3), dtype=torch.int32, device="cuda")
         g.gravity_forces_counted(ctx, theta, eps, acc, cnt)
         g.gravity_sync(ctx)
         return acc.cpu().numpy(), cnt.cpu().numpy()
@@ -67,6 +67,7 @@ def test_tree_forces_vs_oracle(gpu, case, theta, leaf_max, order):
     ref, absum, ocnt = t.forces(theta, eps)
     assert np.array_equal(cnt[:, 0], ocnt[:, 1]), "accepted-node counts differ"
     assert np.array_equal(cnt[:, 1], ocnt[:, 2]), "body-term counts differ"
+    assert np.array_equal(cnt[:, 2], ocnt[:, 0]), "opening-test counts differ"
     _check(a, ref, absum)
     # the uncounted kernel gives the same result
     a2, _ = _gpu_forces(gpu, pos, m, theta, eps, leaf_max=leaf_max, order=order)
@@ -81,6 +82,7 @@ def test_tree_variants(gpu, mac_guard, accum, eps):
     t = oracle.Tree(pos, m, leaf_max=4)
     ref, absum, ocnt = t.forces(0.6, eps, mac_guard=mac_guard)
     assert np.array_equal(cnt[:, 0], ocnt[:, 1]) and np.array_equal(cnt[:, 1], ocnt[:, 2])
+    assert np.array_equal(cnt[:, 2], ocnt[:, 0])
     _check(a, ref, absum)
 
 
