@@ -111,6 +111,27 @@ int gravity_forces_counted(gravity_ctx *ctx, double theta, double eps, double *a
 int gravity_direct(gravity_ctx *ctx, int64_t n, const double *pos, const double *mass,
                    double eps, double G, double *acc);
 
+/* Allocation-free direct sum (the paper has no counterpart: this is a library
+ * service).  For callers that cannot call cudaMalloc - an application that owns
+ * all device memory (fixed-budget pool, plugin host forbidding allocations after
+ * start-up), or a latency-critical loop that cannot afford the implicit device
+ * synchronisation of cudaMalloc/cudaFree.  Same result as gravity_direct (same
+ * kernels), but needs no context and allocates nothing: the hi/lo staging of the
+ * bodies lives in a file-scope __device__ array of 2 MiB, sized for at most
+ * 65536 bodies, which every GPU that loads the library holds until the process
+ * exits.
+ *   n      number of bodies, 0 <= n <= 65536; larger n -> GRAVITY_E_ARG (nothing runs)
+ *   pos, mass, acc  device pointers as for gravity_direct, on the CURRENT device
+ *   cuda_stream     stream the two kernels are enqueued on (NULL = legacy default)
+ * The first call on a device (with that device current) resolves the array's
+ * device address with cudaGetSymbolAddress; make that first call before any stream
+ * capture.  All calls on a device share the one array, which keeps the last call's
+ * contents (every entry a call reads is written by that call first): calls that
+ * overlap on the GPU (different streams, or different host threads) race and give
+ * wrong results - serialise them. */
+int gravity_direct_noalloc(int64_t n, const double *pos, const double *mass, double eps,
+                           double G, double *acc, void *cuda_stream);
+
 /* nsteps steps of a symplectic integrator (Sec. 2.3) with the tree rebuilt every
  * step (Sec. 2.1).  p->scheme 0 (kick-drift-kick leapfrog):
  *   v += dt/2 a;  x += dt v;  a = a(x);  v += dt/2 a

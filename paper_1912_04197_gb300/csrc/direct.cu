@@ -114,3 +114,66 @@ int direct_forces(Ctx *c, int64_t n, const double *pos, const double *mass, doub
 }
 
 }  // namespace grav
+
+// ---------------------------------------------------------------------------
+// Allocation-free direct sum.
+//
+// Some callers cannot call cudaMalloc: code embedded in a host application that
+// owns every byte of device memory (a fixed-budget pool, or a plugin host that
+// forbids allocations once it has started), and latency-critical loops where the
+// implicit device-wide synchronisation of cudaMalloc/cudaFree is not acceptable.
+// gravity_direct_noalloc serves them: it runs the same two kernels as
+// gravity_direct, but its hi/lo staging lives in the file-scope array below
+// instead of context-owned scratch, and it needs no context at all.
+#include <mutex>
+
+namespace grav {
+namespace {
+
+constexpr int64_t kNoAllocMaxBodies = 65536;     // 2 x 65536 x 16 B = 2 MiB per device
+constexpr int kNoAllocMaxDevices = 64;
+
+// hi/lo staging of gravity_direct_noalloc: [0, max) = (x_hi, y_hi, z_hi, m),
+// [max, 2 max) = (x_lo, y_lo, z_lo, 0).  Every GPU that loads this library holds it
+// until the process exits.  Host code must not pass this name to a kernel: on the
+// host it is only a stand-in for the symbol; the device address comes from
+// cudaGetSymbolAddress, once per device.
+static __device__ __align__(256) float4 g_direct_scratch[2 * kNoAllocMaxBodies];
+
+std::mutex g_noalloc_mu;
+float4 *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+}  // namespace
+}  // namespace grav
+
+extern "C" int gravity_direct_noalloc(int64_t n, const double *pos, const double *mass,
+                                      double eps, double G, double *acc, void *cuda_stream) {
+  using namespace grav;
+  if (n < 0 || n > kNoAllocMaxBodies || !(eps >= 0.0) || !isfinite(eps) || !isfinite(G))
+    return GRAVITY_E_ARG;
+  if (n == 0) return GRAVITY_OK;
+  if (!pos || !mass || !acc) return GRAVITY_E_ARG;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return GRAVITY_E_ARG;
+  float4 *base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {               // first call on this device: resolve the address
+      void *p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_direct_scratch);
+      if (e != cudaSuccess) return cuda_status(e);
+      g_noalloc_ptr[dev] = static_cast<float4 *>(p);
+    }
+    base = g_noalloc_ptr[dev];
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  float4 *hi = base, *lo = base + kNoAllocMaxBodies;
+  // every staging entry the sum reads (j < n) is written first by k_split in this call
+  k_split<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pos, mass, n, hi, lo);
+  const int64_t per_block = (int64_t)kDirThreads * kDirPerThread;
+  k_direct<<<(unsigned)((n + per_block - 1) / per_block), kDirThreads, 0, s>>>(
+      hi, lo, n, (float)(eps * eps), G, acc);
+  return cuda_status(cudaGetLastError());
+}

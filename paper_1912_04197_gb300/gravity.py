@@ -64,6 +64,7 @@ def _load() -> ctypes.CDLL:
         "gravity_strerror": (ctypes.c_char_p, [I]),
         "gravity_stats": (I, [P, ctypes.POINTER(I64)]),
         "gravity_probe_fp32": (I, [P, I64, ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "gravity_direct_noalloc": (I, [I64, P, P, D, D, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -171,6 +172,14 @@ def gravity_forces_counted(ctx: Context, theta: float, eps: float, acc: torch.Te
 def gravity_direct(ctx: Context, pos, mass, eps: float, G: float, acc) -> torch.Tensor:
     _check(_lib.gravity_direct(ctx.handle, pos.shape[0], _dev(pos, "pos", 3), _dev(mass, "mass"),
                                float(eps), float(G), _dev(acc, "acc", 3)), "gravity_direct")
+    return acc
+
+
+def gravity_direct_noalloc(pos, mass, eps: float, G: float, acc) -> torch.Tensor:
+    """Direct sum with no context and no allocation (n <= 65536); see gravity.h."""
+    _check(_lib.gravity_direct_noalloc(pos.shape[0], _dev(pos, "pos", 3), _dev(mass, "mass"),
+                                       float(eps), float(G), _dev(acc, "acc", 3),
+                                       _stream_of(pos.device)), "gravity_direct_noalloc")
     return acc
 
 
