@@ -109,11 +109,20 @@ int64_t build_rec(Tree &t, int depth, int64_t b, int64_t e, int64_t parent) {
 
 // Eq. (COMinternal): node mass = sum of child masses, node centre of mass =
 // (sum of child COM * child mass) / node mass, children in octant order.
-// A leaf sums its bodies in sorted order.  The traceless quadrupole (not in the
-// paper) is Q = sum m (3 y y^T - |y|^2 I) about the COM, shifted to the parent
-// with the parallel-axis rule; a single-body leaf has Q = 0.
+// A leaf of several bodies sums them in sorted order; a one-body leaf is the body.
+// The traceless quadrupole (not in the paper) is Q = sum m (3 y y^T - |y|^2 I)
+// about the COM, shifted to the parent with the parallel-axis rule; a one-body
+// leaf has Q = 0.
 void moments_rec(Tree &t, int64_t k) {
   Node &nd = t.nodes[k];
+  if (nd.leaf && nd.end - nd.begin == 1) {
+    // a one-body leaf is the body itself (leaves are bodies, Sec. 2.1): its mass
+    // and position, no sum and no division
+    nd.m = t.m[nd.begin];
+    for (int a = 0; a < 3; ++a) nd.com[a] = t.x[3 * nd.begin + a];
+    for (double &v : nd.q) v = 0.0;
+    return;
+  }
   if (nd.leaf) {
     double msum = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
     for (int64_t i = nd.begin; i < nd.end; ++i) {
