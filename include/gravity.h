@@ -168,6 +168,9 @@ int gravity_sync(gravity_ctx *ctx);
  *   GRAVITY_DBG_MASS      nnodes double
  *   GRAVITY_DBG_COM       nnodes x 3 double
  *   GRAVITY_DBG_QUAD      nnodes x 6 double (xx, yy, zz, xy, xz, yz)
+ *   GRAVITY_DBG_WALKSTATS 8 uint64 from the last gravity_forces_counted: batches, items,
+ *                         mixed nodes, FP64 decisions, point-list entries, quadrupole-list
+ *                         entries, deepest stack, terms evaluated by active lanes
  * bytes must be at least the size listed; otherwise GRAVITY_E_ARG. */
 enum gravity_debug_item {
   GRAVITY_DBG_ROOT = 0,
@@ -179,7 +182,8 @@ enum gravity_debug_item {
   GRAVITY_DBG_PARENT = 6,
   GRAVITY_DBG_MASS = 7,
   GRAVITY_DBG_COM = 8,
-  GRAVITY_DBG_QUAD = 9
+  GRAVITY_DBG_QUAD = 9,
+  GRAVITY_DBG_WALKSTATS = 10
 };
 int gravity_debug_export(gravity_ctx *ctx, int what, void *host_dst, size_t bytes);
 

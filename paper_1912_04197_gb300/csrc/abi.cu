@@ -38,7 +38,7 @@ void free_tree(Tree &t) {
   free_ptr(t.pos_s); free_ptr(t.mass_s); free_ptr(t.body_hi); free_ptr(t.body_lo);
   free_ptr(t.bchild); free_ptr(t.bparent); free_ptr(t.bfirst); free_ptr(t.blast);
   free_ptr(t.bplen); free_ptr(t.bnchild); free_ptr(t.bbase);
-  free_ptr(t.topo); free_ptr(t.nparent); free_ptr(t.ndepth); free_ptr(t.narrive);
+  free_ptr(t.topo); free_ptr(t.nparent); free_ptr(t.ndepth); free_ptr(t.nlist);
   free_ptr(t.nmass); free_ptr(t.ncom); free_ptr(t.nquad); free_ptr(t.nrec0); free_ptr(t.nrec1);
   free_ptr(t.nquadf);
 }
@@ -81,14 +81,14 @@ int ensure_capacity(Ctx *c, int64_t n) {
   GRAV_ALLOC(t.idx, cap); GRAV_ALLOC(t.idx_alt, cap);
   GRAV_ALLOC(t.hist, 256 * ntiles);
   GRAV_ALLOC(t.scan_aux, scan_n / 4096 + 64);
-  GRAV_ALLOC(t.bbox_part, 6 * 4 * (int64_t)c->num_sms);
+  GRAV_ALLOC(t.bbox_part, 6 * (4 * (int64_t)c->num_sms + 3));
   GRAV_ALLOC(t.pos_s, 3 * cap); GRAV_ALLOC(t.mass_s, cap);
   GRAV_ALLOC(t.body_hi, cap); GRAV_ALLOC(t.body_lo, cap);
   GRAV_ALLOC(t.bchild, 2 * cap); GRAV_ALLOC(t.bparent, cap); GRAV_ALLOC(t.bfirst, cap);
   GRAV_ALLOC(t.blast, cap); GRAV_ALLOC(t.bplen, cap); GRAV_ALLOC(t.bnchild, cap);
   GRAV_ALLOC(t.bbase, cap);
   GRAV_ALLOC(t.topo, nodes); GRAV_ALLOC(t.nparent, nodes); GRAV_ALLOC(t.ndepth, nodes);
-  GRAV_ALLOC(t.narrive, nodes);
+  GRAV_ALLOC(t.nlist, nodes);
   GRAV_ALLOC(t.nmass, nodes); GRAV_ALLOC(t.ncom, 3 * nodes); GRAV_ALLOC(t.nquad, 6 * nodes);
   GRAV_ALLOC(t.nrec0, nodes); GRAV_ALLOC(t.nrec1, nodes); GRAV_ALLOC(t.nquadf, 2 * nodes);
 #undef GRAV_ALLOC
@@ -136,7 +136,9 @@ int gravity_create(gravity_ctx **out, int device, void *cuda_stream) {
   if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMalloc(&c.t.geom, 8 * sizeof(double)));
   if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMalloc(&c.t.bbox_ticket, sizeof(unsigned)));
   if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMalloc(&c.t.nnodes, sizeof(int32_t)));
-  if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMalloc(&c.t.scalars, 16 * sizeof(uint32_t)));
+  if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMalloc(&c.t.scalars, 128 * sizeof(uint32_t)));
+  if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMalloc(&c.walk_stats, 8 * sizeof(unsigned long long)));
+  if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMemset(c.walk_stats, 0, 8 * sizeof(unsigned long long)));
   if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMemset(c.d_status, 0, sizeof(unsigned)));
   if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMemset(c.t.bbox_ticket, 0, sizeof(unsigned)));
   if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMemset(c.t.nnodes, 0, sizeof(int32_t)));
@@ -156,6 +158,7 @@ int gravity_destroy(gravity_ctx *h) {
   grav::free_tree(c.t);
   grav::free_ptr(c.t.geom); grav::free_ptr(c.t.bbox_ticket); grav::free_ptr(c.t.nnodes);
   grav::free_ptr(c.t.scalars);
+  grav::free_ptr(c.walk_stats);
   grav::free_ptr(c.d_status);
   grav::free_ptr(c.dir_hi); grav::free_ptr(c.dir_lo);
   grav::free_ptr(c.h2d_pos); grav::free_ptr(c.h2d_mass); grav::free_ptr(c.h2d_acc);
@@ -328,11 +331,21 @@ int gravity_debug_export(gravity_ctx *h, int what, void *dst, size_t bytes) {
     case GRAVITY_DBG_MASS: src = t.nmass; need = sizeof(double) * nn; break;
     case GRAVITY_DBG_COM: src = t.ncom; need = 3 * sizeof(double) * nn; break;
     case GRAVITY_DBG_QUAD: src = t.nquad; need = 6 * sizeof(double) * nn; break;
+    case GRAVITY_DBG_WALKSTATS: src = c.walk_stats; need = 8 * sizeof(unsigned long long); break;
     default: return GRAVITY_E_ARG;
   }
   if (bytes < need) return GRAVITY_E_ARG;
   if (need == 0) return GRAVITY_OK;
   GRAV_CUDA_TRY(cudaMemcpy(dst, src, need, cudaMemcpyDeviceToHost));
+  if (what == GRAVITY_DBG_QUAD) {             // stored as T = sum m y y^T; export Q = 3T - tr(T) I
+    double *q = static_cast<double *>(dst);
+    for (int32_t k = 0; k < nn; ++k) {
+      double *T = q + 6 * k;
+      const double tr = T[0] + T[1] + T[2];
+      for (int a = 0; a < 3; ++a) T[a] = 3.0 * T[a] - tr;
+      for (int a = 3; a < 6; ++a) T[a] = 3.0 * T[a];
+    }
+  }
   return GRAVITY_OK;
 }
 

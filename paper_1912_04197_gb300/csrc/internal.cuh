@@ -43,16 +43,16 @@ struct Tree {
   int32_t *bplen = nullptr;                     // [n-1] common prefix length (bits)
   uint32_t *bnchild = nullptr;                  // [n-1] octree children (0 if not internal)
   uint32_t *bbase = nullptr;                    // [n-1] exclusive scan of bnchild
-  uint32_t *scalars = nullptr;                  // small device scalars (scan totals)
+  uint32_t *scalars = nullptr;                  // small device scalars (scan totals, buckets)
   // octree, capacity 2n nodes
   int4 *topo = nullptr;                         // first child (-1 leaf), n_child, begin, end
   int32_t *nparent = nullptr;
   int32_t *ndepth = nullptr;
-  int32_t *narrive = nullptr;                   // arrival counters of the moment pass
+  int32_t *nlist = nullptr;                     // node ids bucketed for the moment pass
   int32_t *nnodes = nullptr;                    // device scalar
   double *nmass = nullptr;                      // FP64 moments
   double *ncom = nullptr;                       // (k,3)
-  double *nquad = nullptr;                      // (k,6)
+  double *nquad = nullptr;                      // (k,6) second moments T about the COM
   float4 *nrec0 = nullptr;                      // (com_hi xyz, m)
   float4 *nrec1 = nullptr;                      // (com_lo xyz, l^2)
   float4 *nquadf = nullptr;                     // 2 per node: (xx,yy,zz,xy), (xz,yz,0,0)
@@ -68,6 +68,7 @@ struct Ctx {
   gravity_params params{};
   unsigned *d_status = nullptr;
   int64_t launches = 0;        // kernels enqueued by this context (introspection)
+  unsigned long long *walk_stats = nullptr;   // 8 counters filled by the counted walk
   Tree t;
   // direct-sum staging (caller order hi/lo)
   float4 *dir_hi = nullptr, *dir_lo = nullptr;

@@ -28,59 +28,90 @@ __device__ __forceinline__ int cap_depth(int plen) {
 // ------------------------------------------------------------------ a1: root cube
 // Kernel 1 (Sec. 2.1): bounding box of all bodies.  Root cube: corner at the
 // per-axis minimum, side = largest extent (1 if that is 0 or n <= 1).  Any
-// non-finite coordinate latches kErrNonFinite.  Last-block reduction, no spin.
-__global__ void __launch_bounds__(kBBoxThreads)
-k_bbox(const double *__restrict__ pos, int64_t n, double *__restrict__ part,
-       unsigned *__restrict__ ticket, double *__restrict__ geom, unsigned *status) {
-  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-  bool bad = false;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    for (int a = 0; a < 3; ++a) {
-      double v = pos[3 * i + a];
-      bad |= !isfinite(v);
-      lo[a] = fmin(lo[a], v);
-      hi[a] = fmax(hi[a], v);
-    }
-  }
+// non-finite coordinate latches kErrNonFinite.  Min/max run on order-preserving
+// 64-bit integer images of the doubles (exact, and off the slow FP64 pipe); the
+// last block to finish reduces the per-block partials.  No spin-wait.
+__device__ __forceinline__ unsigned long long ord_of(double v) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double of_ord(unsigned long long k) {
+  unsigned long long b = (k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
+  return __longlong_as_double((long long)b);
+}
+__device__ __forceinline__ unsigned long long umin64(unsigned long long a, unsigned long long b) {
+  return a < b ? a : b;
+}
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+  return a > b ? a : b;
+}
+
+// Block-wide min (lo[3]) / max (hi[3]) of ordered keys; result valid in thread 0.
+__device__ __forceinline__ void block_minmax(unsigned long long lo[3], unsigned long long hi[3]) {
+  __shared__ unsigned long long s[kBBoxThreads / 32][6];
   for (int o = 16; o > 0; o >>= 1)
     for (int a = 0; a < 3; ++a) {
-      lo[a] = fmin(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
-      hi[a] = fmax(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+      lo[a] = umin64(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+      hi[a] = umax64(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
     }
-  bad = __any_sync(0xffffffffu, bad);
-  __shared__ double s[kBBoxThreads / 32][6];
-  __shared__ int s_bad;
-  __shared__ bool s_last;
-  if (threadIdx.x == 0) s_bad = 0;
-  __syncthreads();
-  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0)
     for (int a = 0; a < 3; ++a) { s[w][a] = lo[a]; s[w][3 + a] = hi[a]; }
-    if (bad) s_bad = 1;
-  }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0)
     for (int ww = 1; ww < kBBoxThreads / 32; ++ww)
       for (int a = 0; a < 3; ++a) {
-        s[0][a] = fmin(s[0][a], s[ww][a]);
-        s[0][3 + a] = fmax(s[0][3 + a], s[ww][3 + a]);
+        lo[a] = umin64(lo[a], s[ww][a]);
+        hi[a] = umax64(hi[a], s[ww][3 + a]);
       }
-    for (int a = 0; a < 6; ++a) part[6 * blockIdx.x + a] = s[0][a];
-    if (s_bad) latch_error(status, kErrNonFinite);
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kBBoxThreads)
+k_bbox(const double *__restrict__ pos, int64_t n, unsigned long long *__restrict__ part,
+       unsigned *__restrict__ ticket, double *__restrict__ geom, unsigned *status) {
+  unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
+  unsigned long long klo = ~0ull, khi = 0ull;
+  bool bad = false;
+  const unsigned long long *p64 = reinterpret_cast<const unsigned long long *>(pos);
+  // coalesced over the flat (n,3) array; the grid stride is a multiple of 3 (the
+  // launcher makes gridDim a multiple of 3), so each thread keeps one axis
+  const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = i0; i < 3 * n; i += stride) {
+    unsigned long long b = p64[i];
+    bad |= ((b >> 52) & 0x7FFull) == 0x7FFull;
+    unsigned long long k = (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+    klo = umin64(klo, k);
+    khi = umax64(khi, k);
+  }
+  const int axis = (int)(i0 % 3);
+  lo[0] = axis == 0 ? klo : lo[0]; hi[0] = axis == 0 ? khi : hi[0];
+  lo[1] = axis == 1 ? klo : lo[1]; hi[1] = axis == 1 ? khi : hi[1];
+  lo[2] = axis == 2 ? klo : lo[2]; hi[2] = axis == 2 ? khi : hi[2];
+  bad = __syncthreads_or(bad);
+  block_minmax(lo, hi);
+  __shared__ bool s_last;
+  if (threadIdx.x == 0) {
+    for (int a = 0; a < 3; ++a) { part[6 * blockIdx.x + a] = lo[a]; part[6 * blockIdx.x + 3 + a] = hi[a]; }
+    if (bad) latch_error(status, kErrNonFinite);
     __threadfence();
     unsigned t = atomicAdd(ticket, 1u);
     s_last = (t == gridDim.x - 1);
   }
   __syncthreads();
-  if (!s_last || threadIdx.x != 0) return;
+  if (!s_last) return;
   __threadfence();
-  double glo[3] = {INFINITY, INFINITY, INFINITY}, ghi[3] = {-INFINITY, -INFINITY, -INFINITY};
-  for (unsigned b = 0; b < gridDim.x; ++b)
+  for (int a = 0; a < 3; ++a) { lo[a] = ~0ull; hi[a] = 0ull; }
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
     for (int a = 0; a < 3; ++a) {
-      glo[a] = fmin(glo[a], __ldcg(&part[6 * b + a]));
-      ghi[a] = fmax(ghi[a], __ldcg(&part[6 * b + 3 + a]));
+      lo[a] = umin64(lo[a], __ldcg(&part[6 * b + a]));
+      hi[a] = umax64(hi[a], __ldcg(&part[6 * b + 3 + a]));
     }
+  block_minmax(lo, hi);
+  if (threadIdx.x != 0) return;
+  double glo[3], ghi[3];
+  for (int a = 0; a < 3; ++a) { glo[a] = of_ord(lo[a]); ghi[a] = of_ord(hi[a]); }
   double side = 0.0;
   for (int a = 0; a < 3; ++a) side = fmax(side, __dsub_rn(ghi[a], glo[a]));
   if (n <= 1 || !(side > 0.0) || !isfinite(side)) side = 1.0;
@@ -102,11 +133,10 @@ __device__ __forceinline__ uint64_t spread3(uint32_t v) {
 }
 
 __device__ __forceinline__ uint32_t grid_coord(double x, double lo, double scale) {
-  // q = clamp(floor((x - lo) * scale), 0, 2^21 - 1): separate IEEE sub and mul
-  double f = floor(__dmul_rn(__dsub_rn(x, lo), scale));
-  if (!(f >= 0.0)) f = 0.0;
-  if (f > 2097151.0) f = 2097151.0;
-  return (uint32_t)f;
+  // q = clamp(floor((x - lo) * scale), 0, 2^21 - 1): separate IEEE sub and mul, then
+  // one floor-converting conversion (saturating; NaN gives 0) and an integer clamp
+  const int q = __double2int_rd(__dmul_rn(__dsub_rn(x, lo), scale));
+  return (uint32_t)min(max(q, 0), 2097151);
 }
 
 __global__ void k_keys(const double *__restrict__ pos, int64_t n, const double *__restrict__ geom,
@@ -460,23 +490,33 @@ __global__ void k_oct_parent(int cap_nodes, const int4 *__restrict__ topo,
 
 // ------------------------------------------------------------------ a7: moments
 // Eq. (COMinternal): m = sum of child masses; COM = (sum of child COM * child mass)
-// / m, children in octant order; a leaf sums its bodies in sorted order.  FP64
-// with explicit IEEE roundings (no contraction) so the result is reproducible.
-// Quadrupole (order 2): Q = sum m (3 y y^T - |y|^2 I) about the COM, shifted to the
-// parent by the parallel-axis rule; a single-body leaf has Q = 0.
-// Bottom-up by arrival counters: the last child to arrive computes the parent.
+// / m, children in octant order; a leaf of several bodies sums them in sorted
+// order; a one-body leaf is the body (its mass and position).  FP64 with explicit
+// IEEE roundings (no contraction) so m and COM are reproducible bit for bit.
+// Quadrupole (order 2): the second moment T = sum m y y^T about the node's COM is
+// carried up with the parallel-axis rule T_p = sum_c (T_c + m_c d_c d_c^T),
+// d_c = COM_c - COM_p (FP64, fused multiply-adds); the walk uses the traceless
+// Q = 3 T - tr(T) I, identical in exact arithmetic to sum m (3 y y^T - |y|^2 I).
+//
+// GB300's FP64 pipe costs the same per warp instruction however many lanes are
+// active, so the pass runs on full warps: nodes are counting-sorted into buckets
+// (all leaves; then internal nodes by depth, deepest first), leaves are done in
+// one launch and each depth level in one launch after the deeper levels.
+constexpr int kBuckets = kLevels + 2;      // 0 = leaves, 1 + (21 - depth) = internal
+constexpr int kSlotCnt = 0, kSlotFill = 32, kSlotOff = 64;   // offsets into t.scalars
+
 struct MomArgs {
   const int4 *topo;
-  const int32_t *nparent;
   const int32_t *ndepth;
   const int32_t *nnodes;
-  int32_t *narrive;
+  const int32_t *nlist;
+  const uint32_t *boff;
   const double *pos_s;
   const double *mass_s;
   const double *geom;
   double *nmass;
   double *ncom;
-  double *nquad;
+  double *nsec;                // second moments T (xx, yy, zz, xy, xz, yz)
   float4 *rec0;
   float4 *rec1;
   float4 *quadf;
@@ -490,106 +530,150 @@ __device__ __forceinline__ double dm(double a, double b) { return __dmul_rn(a, b
 __device__ __forceinline__ double da(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double ds(double a, double b) { return __dsub_rn(a, b); }
 
-// Walk records: (COM hi, m) and (COM lo, l^2).  A one-body leaf is always a
-// body-to-body term, so its record holds the body position itself and l^2 = -1
-// marks it as a point term.
+__device__ __forceinline__ int bucket_of(int4 t, int depth) {
+  return t.x < 0 ? 0 : 1 + (kLevels - depth);
+}
+
+__global__ void k_bucket_count(const int4 *__restrict__ topo, const int32_t *__restrict__ ndepth,
+                               const int32_t *__restrict__ nnodes, int cap_nodes,
+                               uint32_t *__restrict__ slots) {
+  __shared__ uint32_t cnt[kBuckets];
+  if (threadIdx.x < kBuckets) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nn = min(*nnodes, cap_nodes);
+  if (id < nn) atomicAdd(&cnt[bucket_of(topo[id], ndepth[id])], 1u);
+  __syncthreads();
+  if (threadIdx.x < kBuckets && cnt[threadIdx.x])
+    atomicAdd(&slots[kSlotCnt + threadIdx.x], cnt[threadIdx.x]);
+}
+
+// Scatter node ids into their buckets (order inside a bucket is irrelevant: every
+// node is computed from its children only).
+__global__ void k_bucket_fill(const int4 *__restrict__ topo, const int32_t *__restrict__ ndepth,
+                              const int32_t *__restrict__ nnodes, int cap_nodes,
+                              uint32_t *__restrict__ slots, int32_t *__restrict__ nlist) {
+  __shared__ uint32_t cnt[kBuckets], base[kBuckets], off[kBuckets + 1];
+  if (threadIdx.x < kBuckets) cnt[threadIdx.x] = 0;
+  if (threadIdx.x == 0) {
+    off[0] = 0;
+    for (int b = 0; b < kBuckets; ++b) off[b + 1] = off[b] + slots[kSlotCnt + b];
+    if (blockIdx.x == 0)
+      for (int b = 0; b <= kBuckets; ++b) slots[kSlotOff + b] = off[b];
+  }
+  __syncthreads();
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nn = min(*nnodes, cap_nodes);
+  int b = 0;
+  uint32_t local = 0;
+  if (id < nn) {
+    b = bucket_of(topo[id], ndepth[id]);
+    local = atomicAdd(&cnt[b], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x < kBuckets && cnt[threadIdx.x])
+    base[threadIdx.x] = atomicAdd(&slots[kSlotFill + threadIdx.x], cnt[threadIdx.x]);
+  __syncthreads();
+  if (id < nn) nlist[off[b] + base[b] + local] = id;
+}
+
+// Walk records: (COM hi, m) and (COM lo, l^2); l^2 = -1 marks a one-body leaf
+// (always a body-to-body term).  Quadrupole record: Q = 3T - tr(T) I as FP32.
 __device__ void write_records(const MomArgs &A, int id, double m, const double *com,
-                              const double *q, int single_body) {
+                              const double *T, bool single_body) {
   float h[3], lo[3];
-  const double *x = single_body >= 0 ? &A.pos_s[3 * single_body] : com;
-  for (int a = 0; a < 3; ++a) split_df(x[a], h[a], lo[a]);
+  for (int a = 0; a < 3; ++a) split_df(com[a], h[a], lo[a]);
   double l = ldexp(A.geom[3], -A.ndepth[id]);
-  float l2 = single_body >= 0 ? -1.0f : __double2float_rn(dm(l, l));
+  float l2 = single_body ? -1.0f : __double2float_rn(dm(l, l));
   A.rec0[id] = make_float4(h[0], h[1], h[2], __double2float_rn(m));
   A.rec1[id] = make_float4(lo[0], lo[1], lo[2], l2);
   if (A.order >= 2) {
-    A.quadf[2 * id] = make_float4(__double2float_rn(q[0]), __double2float_rn(q[1]),
-                                  __double2float_rn(q[2]), __double2float_rn(q[3]));
-    A.quadf[2 * id + 1] = make_float4(__double2float_rn(q[4]), __double2float_rn(q[5]), 0.f, 0.f);
+    double tr = T[0] + T[1] + T[2];
+    A.quadf[2 * id] = make_float4(__double2float_rn(fma(3.0, T[0], -tr)),
+                                  __double2float_rn(fma(3.0, T[1], -tr)),
+                                  __double2float_rn(fma(3.0, T[2], -tr)),
+                                  __double2float_rn(3.0 * T[3]));
+    A.quadf[2 * id + 1] = make_float4(__double2float_rn(3.0 * T[4]),
+                                      __double2float_rn(3.0 * T[5]), 0.f, 0.f);
   }
 }
 
-__global__ void k_moments(MomArgs A) {
-  int id = blockIdx.x * blockDim.x + threadIdx.x;
-  int nn = *A.nnodes;
-  if (id >= nn || id >= A.cap_nodes) return;
-  int4 t = A.topo[id];
-  if (t.x >= 0) return;                       // internal nodes are done by their last child
-  if (t.z < 0 || t.w > A.n || t.z >= t.w) { latch_error(A.status, kErrTree); return; }
-  // leaf: bodies [t.z, t.w) in sorted order
-  double msum = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
-  for (int i = t.z; i < t.w; ++i) {
-    double mi = A.mass_s[i];
-    msum = da(msum, mi);
-    sx = da(sx, dm(mi, A.pos_s[3 * i]));
-    sy = da(sy, dm(mi, A.pos_s[3 * i + 1]));
-    sz = da(sz, dm(mi, A.pos_s[3 * i + 2]));
-  }
-  double com[3] = {__ddiv_rn(sx, msum), __ddiv_rn(sy, msum), __ddiv_rn(sz, msum)};
-  double q[6] = {0, 0, 0, 0, 0, 0};
-  if (A.order >= 2 && t.w - t.z > 1) {
-    for (int i = t.z; i < t.w; ++i) {
-      double mi = A.mass_s[i];
-      double y0 = ds(A.pos_s[3 * i], com[0]), y1 = ds(A.pos_s[3 * i + 1], com[1]),
-             y2 = ds(A.pos_s[3 * i + 2], com[2]);
-      double r2 = da(da(dm(y0, y0), dm(y1, y1)), dm(y2, y2));
-      q[0] = da(q[0], dm(mi, ds(dm(dm(3.0, y0), y0), r2)));
-      q[1] = da(q[1], dm(mi, ds(dm(dm(3.0, y1), y1), r2)));
-      q[2] = da(q[2], dm(mi, ds(dm(dm(3.0, y2), y2), r2)));
-      q[3] = da(q[3], dm(mi, dm(dm(3.0, y0), y1)));
-      q[4] = da(q[4], dm(mi, dm(dm(3.0, y0), y2)));
-      q[5] = da(q[5], dm(mi, dm(dm(3.0, y1), y2)));
-    }
-  }
-  A.nmass[id] = msum;
-  for (int a = 0; a < 3; ++a) A.ncom[3 * id + a] = com[a];
-  if (A.order >= 2)
-    for (int a = 0; a < 6; ++a) A.nquad[6 * id + a] = q[a];
-  write_records(A, id, msum, com, q, t.w - t.z == 1 ? t.z : -1);
-
-  int node = id;
-  for (int guard = 0;; ++guard) {
-    int p = A.nparent[node];
-    if (p < 0) return;
-    if (guard > 64 || p >= nn) { latch_error(A.status, kErrTree); return; }
-    int4 tp = A.topo[p];
-    if (tp.x <= 0 || tp.x + tp.y > nn) { latch_error(A.status, kErrTree); return; }
-    __threadfence();
-    int old = atomicAdd(&A.narrive[p], 1);
-    if (old != tp.y - 1) return;             // not the last child
-    __threadfence();
-    double pm = 0.0, px = 0.0, py = 0.0, pz = 0.0;
-    for (int c = tp.x; c < tp.x + tp.y; ++c) {
-      double mc = __ldcg(&A.nmass[c]);
-      pm = da(pm, mc);
-      px = da(px, dm(__ldcg(&A.ncom[3 * c]), mc));
-      py = da(py, dm(__ldcg(&A.ncom[3 * c + 1]), mc));
-      pz = da(pz, dm(__ldcg(&A.ncom[3 * c + 2]), mc));
-    }
-    double pc[3] = {__ddiv_rn(px, pm), __ddiv_rn(py, pm), __ddiv_rn(pz, pm)};
-    double pq[6] = {0, 0, 0, 0, 0, 0};
-    if (A.order >= 2) {
-      for (int c = tp.x; c < tp.x + tp.y; ++c) {
-        double mc = __ldcg(&A.nmass[c]);
-        double d0 = ds(__ldcg(&A.ncom[3 * c]), pc[0]);
-        double d1 = ds(__ldcg(&A.ncom[3 * c + 1]), pc[1]);
-        double d2 = ds(__ldcg(&A.ncom[3 * c + 2]), pc[2]);
-        double r2 = da(da(dm(d0, d0), dm(d1, d1)), dm(d2, d2));
-        const double *cq = &A.nquad[6 * c];
-        pq[0] = da(pq[0], da(__ldcg(cq + 0), dm(mc, ds(dm(dm(3.0, d0), d0), r2))));
-        pq[1] = da(pq[1], da(__ldcg(cq + 1), dm(mc, ds(dm(dm(3.0, d1), d1), r2))));
-        pq[2] = da(pq[2], da(__ldcg(cq + 2), dm(mc, ds(dm(dm(3.0, d2), d2), r2))));
-        pq[3] = da(pq[3], da(__ldcg(cq + 3), dm(mc, dm(dm(3.0, d0), d1))));
-        pq[4] = da(pq[4], da(__ldcg(cq + 4), dm(mc, dm(dm(3.0, d0), d2))));
-        pq[5] = da(pq[5], da(__ldcg(cq + 5), dm(mc, dm(dm(3.0, d1), d2))));
+__global__ void k_leaf_moments(MomArgs A) {
+  const uint32_t b0 = A.boff[0], b1 = A.boff[1];
+  for (uint32_t k = b0 + blockIdx.x * blockDim.x + threadIdx.x; k < b1;
+       k += gridDim.x * blockDim.x) {
+    const int id = A.nlist[k];
+    const int4 t = A.topo[id];
+    if (t.z < 0 || t.w > A.n || t.z >= t.w) { latch_error(A.status, kErrTree); continue; }
+    double msum, com[3], T[6] = {0, 0, 0, 0, 0, 0};
+    if (t.w - t.z == 1) {
+      msum = A.mass_s[t.z];
+      for (int a = 0; a < 3; ++a) com[a] = A.pos_s[3 * t.z + a];
+    } else {
+      double sx = 0.0, sy = 0.0, sz = 0.0;
+      msum = 0.0;
+      for (int i = t.z; i < t.w; ++i) {
+        const double mi = A.mass_s[i];
+        msum = da(msum, mi);
+        sx = da(sx, dm(mi, A.pos_s[3 * i]));
+        sy = da(sy, dm(mi, A.pos_s[3 * i + 1]));
+        sz = da(sz, dm(mi, A.pos_s[3 * i + 2]));
+      }
+      com[0] = __ddiv_rn(sx, msum); com[1] = __ddiv_rn(sy, msum); com[2] = __ddiv_rn(sz, msum);
+      if (A.order >= 2) {
+        for (int i = t.z; i < t.w; ++i) {
+          const double mi = A.mass_s[i];
+          const double y0 = A.pos_s[3 * i] - com[0], y1 = A.pos_s[3 * i + 1] - com[1],
+                       y2 = A.pos_s[3 * i + 2] - com[2];
+          const double m0 = mi * y0, m1 = mi * y1, m2 = mi * y2;
+          T[0] = fma(m0, y0, T[0]); T[1] = fma(m1, y1, T[1]); T[2] = fma(m2, y2, T[2]);
+          T[3] = fma(m0, y1, T[3]); T[4] = fma(m0, y2, T[4]); T[5] = fma(m1, y2, T[5]);
+        }
       }
     }
-    A.nmass[p] = pm;
-    for (int a = 0; a < 3; ++a) A.ncom[3 * p + a] = pc[a];
+    A.nmass[id] = msum;
+    for (int a = 0; a < 3; ++a) A.ncom[3 * id + a] = com[a];
     if (A.order >= 2)
-      for (int a = 0; a < 6; ++a) A.nquad[6 * p + a] = pq[a];
-    write_records(A, p, pm, pc, pq, -1);
-    node = p;
+      for (int a = 0; a < 6; ++a) A.nsec[6 * id + a] = T[a];
+    write_records(A, id, msum, com, T, t.w - t.z == 1);
+  }
+}
+
+// Internal nodes of one depth (bucket); their children are deeper, hence done.
+__global__ void k_level_moments(MomArgs A, int bucket) {
+  const uint32_t b0 = A.boff[bucket], b1 = A.boff[bucket + 1];
+  const int nn = min(*A.nnodes, A.cap_nodes);
+  for (uint32_t k = b0 + blockIdx.x * blockDim.x + threadIdx.x; k < b1;
+       k += gridDim.x * blockDim.x) {
+    const int id = A.nlist[k];
+    const int4 tp = A.topo[id];
+    if (tp.x <= 0 || tp.x + tp.y > nn) { latch_error(A.status, kErrTree); continue; }
+    double pm = 0.0, px = 0.0, py = 0.0, pz = 0.0;
+    for (int c = tp.x; c < tp.x + tp.y; ++c) {
+      const double mc = A.nmass[c];
+      pm = da(pm, mc);
+      px = da(px, dm(A.ncom[3 * c], mc));
+      py = da(py, dm(A.ncom[3 * c + 1], mc));
+      pz = da(pz, dm(A.ncom[3 * c + 2], mc));
+    }
+    const double pc[3] = {__ddiv_rn(px, pm), __ddiv_rn(py, pm), __ddiv_rn(pz, pm)};
+    double T[6] = {0, 0, 0, 0, 0, 0};
+    if (A.order >= 2) {
+      for (int c = tp.x; c < tp.x + tp.y; ++c) {
+        const double mc = A.nmass[c];
+        const double d0 = A.ncom[3 * c] - pc[0], d1 = A.ncom[3 * c + 1] - pc[1],
+                     d2 = A.ncom[3 * c + 2] - pc[2];
+        const double m0 = mc * d0, m1 = mc * d1, m2 = mc * d2;
+        const double *Tc = &A.nsec[6 * c];
+        T[0] += fma(m0, d0, Tc[0]); T[1] += fma(m1, d1, Tc[1]); T[2] += fma(m2, d2, Tc[2]);
+        T[3] += fma(m0, d1, Tc[3]); T[4] += fma(m0, d2, Tc[4]); T[5] += fma(m1, d2, Tc[5]);
+      }
+    }
+    A.nmass[id] = pm;
+    for (int a = 0; a < 3; ++a) A.ncom[3 * id + a] = pc[a];
+    if (A.order >= 2)
+      for (int a = 0; a < 6; ++a) A.nsec[6 * id + a] = T[a];
+    write_records(A, id, pm, pc, T, false);
   }
 }
 
@@ -612,11 +696,13 @@ int tree_build(Ctx *c, int64_t n, const double *pos, const double *mass) {
   cudaStream_t s = c->stream;
   const int leaf_max = c->params.leaf_max;
   // a1: root cube (also validates the coordinates)
-  int64_t nb64 = (n + kBBoxThreads - 1) / kBBoxThreads;
+  int64_t nb64 = (3 * n + 4 * kBBoxThreads - 1) / (4 * kBBoxThreads);
   if (nb64 > 4 * (int64_t)c->num_sms) nb64 = 4 * (int64_t)c->num_sms;
+  nb64 = (nb64 + 2) / 3 * 3;                 // stride multiple of 3 (see k_bbox)
   int nb = (int)nb64;
   if (nb < 1) nb = 1;
-  k_bbox<<<nb, kBBoxThreads, 0, s>>>(pos, n, t.bbox_part, t.bbox_ticket, t.geom, c->d_status);
+  k_bbox<<<nb, kBBoxThreads, 0, s>>>(pos, n, reinterpret_cast<unsigned long long *>(t.bbox_part),
+                                     t.bbox_ticket, t.geom, c->d_status);
   ++c->launches;
   // a2: keys
   k_keys<<<blocks_for(n, 256), 256, 0, s>>>(pos, n, t.geom, t.keys, t.idx);
@@ -657,13 +743,24 @@ int tree_build(Ctx *c, int64_t n, const double *pos, const double *mass) {
                                                             t.nparent, c->d_status);
     ++c->launches;
   }
-  // a7: moments
-  GRAV_CUDA_TRY(cudaMemsetAsync(t.narrive, 0, sizeof(int32_t) * cap_nodes, s));
-  MomArgs A{t.topo, t.nparent, t.ndepth, t.nnodes, t.narrive, t.pos_s, t.mass_s, t.geom,
-            t.nmass, t.ncom, t.nquad, t.nrec0, t.nrec1, t.nquadf, c->params.order, cap_nodes,
-            (int)n, c->d_status};
-  k_moments<<<blocks_for(cap_nodes, 256), 256, 0, s>>>(A);
+  // a7: moments (bucketed by depth, full warps)
+  GRAV_CUDA_TRY(cudaMemsetAsync(t.scalars + kSlotCnt, 0, sizeof(uint32_t) * 64, s));
+  const unsigned nb_nodes = blocks_for(cap_nodes, 256);
+  k_bucket_count<<<nb_nodes, 256, 0, s>>>(t.topo, t.ndepth, t.nnodes, cap_nodes, t.scalars);
   ++c->launches;
+  k_bucket_fill<<<nb_nodes, 256, 0, s>>>(t.topo, t.ndepth, t.nnodes, cap_nodes, t.scalars,
+                                         t.nlist);
+  ++c->launches;
+  MomArgs A{t.topo, t.ndepth, t.nnodes, t.nlist, t.scalars + kSlotOff, t.pos_s, t.mass_s,
+            t.geom, t.nmass, t.ncom, t.nquad, t.nrec0, t.nrec1, t.nquadf, c->params.order,
+            cap_nodes, (int)n, c->d_status};
+  const unsigned grid = (unsigned)(4 * c->num_sms);
+  k_leaf_moments<<<grid, 128, 0, s>>>(A);
+  ++c->launches;
+  for (int d = kLevels - 1; d >= 0; --d) {
+    k_level_moments<<<grid, 128, 0, s>>>(A, 1 + (kLevels - d));
+    ++c->launches;
+  }
   return cuda_status(cudaGetLastError());
 }
 

@@ -33,6 +33,12 @@ constexpr uint32_t kKindBody = 0x80000000u;
 constexpr uint32_t kFirstMask = 0x01FFFFFFu;   // 25-bit first index
 constexpr int kCntShift = 25;                  // 6-bit (count - 1)
 
+// Walk statistics accumulated by the counted variant (introspection, not used on the
+// timed path): batches, items, mixed nodes, FP64 decisions, point-list entries,
+// quadrupole-list entries, deepest stack, lane-terms evaluated by active lanes.
+enum { kStatBatches, kStatItems, kStatMixed, kStatFp64, kStatMono, kStatQuad, kStatMaxSp,
+       kStatLaneTerms, kStatCount };
+
 struct WarpSmemMono {
   uint32_t st_a[kStackCap];       // first | (count-1) << 25 | kind
   uint32_t st_m[kStackCap];       // lane mask
@@ -68,6 +74,7 @@ struct WalkArgs {
   double kick;
   unsigned *status;
   int max_iter;
+  unsigned long long *stats;     // counted variant only: walk statistics (see kStat*)
 };
 
 __device__ __forceinline__ int warp_incl_scan_i(int v, int lane) {
@@ -207,6 +214,8 @@ k_walk(WalkArgs A) {
 
   Accum<ACC64> acc;
   int c_m2p = 0, c_p2p = 0, c_tests = 0;
+  unsigned long long w_batches = 0, w_items = 0, w_mixed = 0, w_fp64 = 0, w_mono = 0, w_quad = 0;
+  int w_maxsp = 0;
   int nmono = 0, nquad = 0;
   int sp = 0;
   bool abort = false;
@@ -253,6 +262,7 @@ k_walk(WalkArgs A) {
     const uint32_t oa = __shfl_sync(0xffffffffu, ea, owner);
     const uint32_t omask = __shfl_sync(0xffffffffu, em, owner);
     const bool have = lane < nitems;
+    if (COUNT) { ++w_batches; w_items += nitems; }
     const bool kbody = (oa & kKindBody) != 0;
     const int item = (int)(oa & kFirstMask) + (lane - stpos);
 
@@ -318,6 +328,7 @@ k_walk(WalkArgs A) {
     }
     // ---- exact per-lane test for mixed nodes
     unsigned mixed_bits = __ballot_sync(0xffffffffu, mixed);
+    if (COUNT) w_mixed += __popc(mixed_bits);
     while (mixed_bits) {
       const int j = __ffs(mixed_bits) - 1;
       mixed_bits &= mixed_bits - 1;
@@ -350,6 +361,7 @@ k_walk(WalkArgs A) {
                                          __dmul_rn(ddz, ddz));
             const double l = ldexp(side, -A.ndepth[node]);
             a_i = __dmul_rn(l, l) < __dmul_rn(A.theta2d, D2d);
+            if (COUNT) atomicAdd(&A.stats[kStatFp64], 1ull);
           } else {
             a_i = diff < 0.f;
           }
@@ -411,10 +423,12 @@ k_walk(WalkArgs A) {
       }
     }
     sp += ptotal;
+    if (COUNT) w_maxsp = max(w_maxsp, sp);
     __syncwarp();
 
     // ---- evaluate full lists
     if (nmono >= kFlushAt) {
+      if (COUNT) w_mono += nmono;
       float px, py, pz;
       flush_mono<COUNT>(M, nmono, lane, xh, yh, zh, xl, yl, zl, eps2, px, py, pz, gi, c_m2p, c_p2p);
       acc.add(px, py, pz);
@@ -423,6 +437,7 @@ k_walk(WalkArgs A) {
     }
     if constexpr (ORDER == 2) {
       if (nquad >= kFlushAt) {
+        if (COUNT) w_quad += nquad;
         float px, py, pz;
         flush_quad<COUNT>(S, nquad, lane, xh, yh, zh, xl, yl, zl,
                           eps2, px, py, pz, c_m2p);
@@ -432,6 +447,7 @@ k_walk(WalkArgs A) {
       }
     }
   }
+  if (COUNT) { w_mono += nmono; w_quad += nquad; }
   if (!abort) {
     if (nmono > 0) {
       float px, py, pz;
@@ -444,6 +460,19 @@ k_walk(WalkArgs A) {
         flush_quad<COUNT>(S, nquad, lane, xh, yh, zh, xl, yl, zl, eps2, px, py, pz, c_m2p);
         acc.add(px, py, pz);
       }
+    }
+  }
+  if (COUNT) {
+    const unsigned long long lt =
+        __reduce_add_sync(0xffffffffu, (unsigned)(valid ? c_m2p + c_p2p : 0));
+    if (lane == 0) {
+      atomicAdd(&A.stats[kStatBatches], w_batches);
+      atomicAdd(&A.stats[kStatItems], w_items);
+      atomicAdd(&A.stats[kStatMixed], w_mixed);
+      atomicAdd(&A.stats[kStatMono], w_mono);
+      atomicAdd(&A.stats[kStatQuad], w_quad);
+      atomicMax(&A.stats[kStatMaxSp], (unsigned long long)w_maxsp);
+      atomicAdd(&A.stats[kStatLaneTerms], lt);
     }
   }
   if (!valid) return;
@@ -503,6 +532,10 @@ int walk_forces(Ctx *c, double theta, double eps, double *acc, int32_t *counts, 
   A.acc = acc; A.counts = counts; A.vel = vel; A.kick = kick;
   A.status = c->d_status;
   A.max_iter = (int)(8 * c->n + 64);
+  A.stats = c->walk_stats;
+  if (counts) {
+    GRAV_CUDA_TRY(cudaMemsetAsync(c->walk_stats, 0, sizeof(unsigned long long) * 8, c->stream));
+  }
   const bool q = c->params.order == 2;
   const bool d64 = c->params.accum == 1;
   if (counts) {

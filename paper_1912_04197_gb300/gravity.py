@@ -25,7 +25,7 @@ GRAVITY_E_INTERNAL = -6
 GRAVITY_E_NOTREE = -7
 
 DBG_ROOT, DBG_KEYS, DBG_PERM, DBG_NNODES, DBG_TOPO, DBG_DEPTH, DBG_PARENT, DBG_MASS, DBG_COM, \
-    DBG_QUAD = range(10)
+    DBG_QUAD, DBG_WALKSTATS = range(11)
 
 
 class GravityError(RuntimeError):
@@ -225,7 +225,8 @@ def gravity_sync(ctx: Context):
 
 _DBG_DTYPES = {DBG_ROOT: (np.float64, 4), DBG_KEYS: (np.uint64, 1), DBG_PERM: (np.uint32, 1),
                DBG_TOPO: (np.int32, 4), DBG_DEPTH: (np.int32, 1), DBG_PARENT: (np.int32, 1),
-               DBG_MASS: (np.float64, 1), DBG_COM: (np.float64, 3), DBG_QUAD: (np.float64, 6)}
+               DBG_MASS: (np.float64, 1), DBG_COM: (np.float64, 3), DBG_QUAD: (np.float64, 6),
+               DBG_WALKSTATS: (np.uint64, 8)}
 
 
 def gravity_debug_export(ctx: Context, what: int, n: int) -> np.ndarray:
@@ -236,13 +237,14 @@ def gravity_debug_export(ctx: Context, what: int, n: int) -> np.ndarray:
                "gravity_debug_export")
         return out
     dt, width = _DBG_DTYPES[what]
-    if what == DBG_ROOT:
+    if what in (DBG_ROOT, DBG_WALKSTATS):
         count = 1
     elif what in (DBG_KEYS, DBG_PERM):
         count = n
     else:
         count = int(gravity_debug_export(ctx, DBG_NNODES, n)[0])
-    out = np.zeros((count, width) if width > 1 and what != DBG_ROOT else (count * width,), dt)
+    flat = what in (DBG_ROOT, DBG_WALKSTATS) or width == 1
+    out = np.zeros((count * width,) if flat else (count, width), dt)
     _check(_lib.gravity_debug_export(ctx.handle, what, out.ctypes.data_as(ctypes.c_void_p),
                                      out.nbytes), "gravity_debug_export")
     return out

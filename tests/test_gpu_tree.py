@@ -92,9 +92,13 @@ def test_moments_bitexact(gpu, case, leaf_max, order):
     assert np.array_equal(gm[order_ids], om)
     assert np.array_equal(gc[order_ids], oc)
     if order == 2:
+        # the GPU carries T = sum m y y^T up the tree (same value in exact arithmetic,
+        # other roundings): compare on the node's natural scale m l^2
         gq = gpu.gravity_debug_export(ctx, gpu.DBG_QUAD, n)[order_ids]
-        scale = np.abs(oq).max(axis=1, keepdims=True) + 1e-300
-        assert np.all(np.abs(gq - oq) <= 1e-13 * scale)
+        depth = gpu.gravity_debug_export(ctx, gpu.DBG_DEPTH, n)[order_ids]
+        side = gpu.gravity_debug_export(ctx, gpu.DBG_ROOT, n)[3]
+        scale = (om * (side * 2.0 ** -depth.astype(np.float64)) ** 2)[:, None]
+        assert np.all(np.abs(gq - oq) <= 1e-12 * scale)
 
 
 def test_single_and_coincident(gpu):
