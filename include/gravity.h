@@ -168,9 +168,11 @@ int gravity_sync(gravity_ctx *ctx);
  *   GRAVITY_DBG_MASS      nnodes double
  *   GRAVITY_DBG_COM       nnodes x 3 double
  *   GRAVITY_DBG_QUAD      nnodes x 6 double (xx, yy, zz, xy, xz, yz)
- *   GRAVITY_DBG_WALKSTATS 8 uint64 from the last gravity_forces_counted: batches, items,
+ *   GRAVITY_DBG_WALKSTATS 16 uint64 from the last gravity_forces_counted: batches, items,
  *                         mixed nodes, FP64 decisions, point-list entries, quadrupole-list
- *                         entries, deepest stack, terms evaluated by active lanes
+ *                         entries, deepest stack, terms evaluated by active lanes, lockstep
+ *                         iterations of lists split by 16 / 8 / 1 lanes, full-mask entries,
+ *                         4 reserved
  * bytes must be at least the size listed; otherwise GRAVITY_E_ARG. */
 enum gravity_debug_item {
   GRAVITY_DBG_ROOT = 0,

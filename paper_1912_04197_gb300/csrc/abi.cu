@@ -137,8 +137,8 @@ int gravity_create(gravity_ctx **out, int device, void *cuda_stream) {
   if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMalloc(&c.t.bbox_ticket, sizeof(unsigned)));
   if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMalloc(&c.t.nnodes, sizeof(int32_t)));
   if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMalloc(&c.t.scalars, 128 * sizeof(uint32_t)));
-  if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMalloc(&c.walk_stats, 8 * sizeof(unsigned long long)));
-  if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMemset(c.walk_stats, 0, 8 * sizeof(unsigned long long)));
+  if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMalloc(&c.walk_stats, 16 * sizeof(unsigned long long)));
+  if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMemset(c.walk_stats, 0, 16 * sizeof(unsigned long long)));
   if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMemset(c.d_status, 0, sizeof(unsigned)));
   if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMemset(c.t.bbox_ticket, 0, sizeof(unsigned)));
   if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMemset(c.t.nnodes, 0, sizeof(int32_t)));
@@ -159,6 +159,7 @@ int gravity_destroy(gravity_ctx *h) {
   grav::free_ptr(c.t.geom); grav::free_ptr(c.t.bbox_ticket); grav::free_ptr(c.t.nnodes);
   grav::free_ptr(c.t.scalars);
   grav::free_ptr(c.walk_stats);
+  grav::free_ptr(c.walk_gstack);
   grav::free_ptr(c.d_status);
   grav::free_ptr(c.dir_hi); grav::free_ptr(c.dir_lo);
   grav::free_ptr(c.h2d_pos); grav::free_ptr(c.h2d_mass); grav::free_ptr(c.h2d_acc);
@@ -331,7 +332,7 @@ int gravity_debug_export(gravity_ctx *h, int what, void *dst, size_t bytes) {
     case GRAVITY_DBG_MASS: src = t.nmass; need = sizeof(double) * nn; break;
     case GRAVITY_DBG_COM: src = t.ncom; need = 3 * sizeof(double) * nn; break;
     case GRAVITY_DBG_QUAD: src = t.nquad; need = 6 * sizeof(double) * nn; break;
-    case GRAVITY_DBG_WALKSTATS: src = c.walk_stats; need = 8 * sizeof(unsigned long long); break;
+    case GRAVITY_DBG_WALKSTATS: src = c.walk_stats; need = 16 * sizeof(unsigned long long); break;
     default: return GRAVITY_E_ARG;
   }
   if (bytes < need) return GRAVITY_E_ARG;

@@ -4,7 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/gravity.h"
+#include "gravity.h"
 
 namespace grav {
 
@@ -68,7 +68,9 @@ struct Ctx {
   gravity_params params{};
   unsigned *d_status = nullptr;
   int64_t launches = 0;        // kernels enqueued by this context (introspection)
-  unsigned long long *walk_stats = nullptr;   // 8 counters filled by the counted walk
+  unsigned long long *walk_stats = nullptr;   // 16 counters filled by the counted walk
+  void *walk_gstack = nullptr;                // walk stack overflow, per persistent warp
+  size_t walk_gstack_cap = 0;                 // in 8-byte entries
   Tree t;
   // direct-sum staging (caller order hi/lo)
   float4 *dir_hi = nullptr, *dir_lo = nullptr;

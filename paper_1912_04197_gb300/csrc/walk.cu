@@ -13,11 +13,19 @@
 //     Eq. (accuracy): l^2 < theta^2 D^2 in FP32 on hi/lo coordinates; a result
 //     within a relative 2^-16 of the boundary is recomputed in FP64 exactly as
 //     the oracle does, so every decision equals the FP64 one;
-//   * accepted nodes (Eq. Force_thetaTrue; + quadrupole) and body-to-body terms
-//     (Eq. Force_leaf) go to a shared-memory list that all lanes evaluate with
-//     the softened r of Eq. (Force_rComp); inactive lanes add zero.
-// Pair terms are FP32 with d = (c_hi - x_hi) + (c_lo - x_lo); each flushed list's
-// partial sum enters a (hi, lo) two-sum accumulator (or an FP64 one).
+//   * accepted terms go to shared-memory lists that all lanes evaluate with the
+//     softened r of Eq. (Force_rComp); inactive lanes add zero.  Three lists:
+//       point  - body-to-body terms (Eq. Force_leaf), d = (c_hi - x_hi) + (c_lo - x_lo);
+//       far    - node terms (Eq. Force_thetaTrue; + quadrupole) of cells at least
+//                theta R_w / 2 wide (R_w = extent of the warp's bodies), on FP32
+//                coordinates relative to the warp's first body: every accepting
+//                body is then more than R_w / 2 away, which bounds the error of
+//                d = c_rel - x_rel by 5.5 * 2^-23 |d| (2^-23 (1.5 |d| + 2 R_w));
+//       near   - the other node terms, on hi/lo coordinates as the point list;
+//   * each flushed list's partial sum enters a (hi, lo) two-sum accumulator (or an
+//     FP64 one).
+// The kernel is persistent: each warp takes 32-body tasks from an atomic counter,
+// and owns an overflow area in global memory for the deep part of its stack.
 #include <type_traits>
 
 #include "internal.cuh"
@@ -26,30 +34,37 @@ namespace grav {
 namespace {
 
 constexpr int kWalkWarps = 4;
-constexpr int kStackCap = 512;
+constexpr int kSmemStack = 224;                // stack entries in shared memory
+constexpr int kGlobStack = 1024;               // further entries in global memory, per warp
+constexpr int kStackCap = kSmemStack + kGlobStack;
 constexpr int kListCap = 64;
 constexpr int kFlushAt = 32;
 constexpr uint32_t kKindBody = 0x80000000u;
 constexpr uint32_t kFirstMask = 0x01FFFFFFu;   // 25-bit first index
 constexpr int kCntShift = 25;                  // 6-bit (count - 1)
 
-// Walk statistics accumulated by the counted variant (introspection, not used on the
-// timed path): batches, items, mixed nodes, FP64 decisions, point-list entries,
-// quadrupole-list entries, deepest stack, lane-terms evaluated by active lanes.
+// Walk statistics accumulated by the counted variant (introspection, not used on
+// the timed path): batches, items, mixed nodes, FP64 decisions, point-list entries,
+// node-term entries, deepest stack, lane-terms evaluated by active lanes, lockstep
+// iterations of lists split by 16 / 8 / 1 lanes, full-mask entries, far entries.
 enum { kStatBatches, kStatItems, kStatMixed, kStatFp64, kStatMono, kStatQuad, kStatMaxSp,
-       kStatLaneTerms, kStatCount };
+       kStatLaneTerms, kStatSplit2, kStatSplit4, kStatSplit32, kStatFull, kStatFar,
+       kStatCount = 16 };
 
-struct WarpSmemMono {
-  uint32_t st_a[kStackCap];       // first | (count-1) << 25 | kind
-  uint32_t st_m[kStackCap];       // lane mask
-  float4 la[kListCap];            // (x_hi, y_hi, z_hi, m)
-  float4 lb[kListCap];            // (x_lo, y_lo, z_lo, lane mask bits)
+struct WarpSmem {
+  uint32_t st_a[kSmemStack];      // first | (count-1) << 25 | kind
+  uint32_t st_m[kSmemStack];      // lane mask
+  float4 la[kListCap];            // point list: (x_hi, y_hi, z_hi, m)
+  float4 lb[kListCap];            //             (x_lo, y_lo, z_lo, lane mask bits)
+  float4 fa[kListCap];            // far list:   (c_rel xyz, m)
+  float4 fc[kListCap];            //             (q_xz, q_yz, lane mask bits, 0)
   int32_t ltag[kListCap];         // counting: -1 node term, else sorted body index
 };
 
-struct WarpSmemQuad {
-  WarpSmemMono mono;
-  float4 qa[kListCap], qb[kListCap], qc[kListCap], qd[kListCap];
+struct WarpSmemQ {
+  WarpSmem base;
+  float4 fb[kListCap];            // far list:   (q_xx, q_yy, q_zz, q_xy)
+  float4 qa[kListCap], qb[kListCap], qc[kListCap], qd[kListCap];   // near node terms
 };
 
 struct WalkArgs {
@@ -63,18 +78,22 @@ struct WalkArgs {
   const uint32_t *perm;
   const int32_t *nnodes;
   int n;
+  int ntasks;
   float theta2f;
   double theta2d;
   float eps2;
   double G;
   int mac_guard;
+  int acc64;
   double *acc;
   int32_t *counts;
   double *vel;
   double kick;
   unsigned *status;
   int max_iter;
-  unsigned long long *stats;     // counted variant only: walk statistics (see kStat*)
+  unsigned *task_counter;
+  uint2 *gstack;                  // [persistent warps][kGlobStack] (first|cnt|kind, mask)
+  unsigned long long *stats;      // counted variant only
 };
 
 __device__ __forceinline__ int warp_incl_scan_i(int v, int lane) {
@@ -93,39 +112,46 @@ __device__ __forceinline__ void two_sum_add(float &hi, float &lo, float p) {
   lo += err;
 }
 
-template <bool ACC64>
 struct Accum {
   float hx = 0, hy = 0, hz = 0, lx = 0, ly = 0, lz = 0;
   double dx = 0, dy = 0, dz = 0;
-  __device__ __forceinline__ void add(float px, float py, float pz) {
-    if (ACC64) { dx += (double)px; dy += (double)py; dz += (double)pz; }
+  __device__ __forceinline__ void add(bool acc64, float px, float py, float pz) {
+    if (acc64) { dx += (double)px; dy += (double)py; dz += (double)pz; }
     else { two_sum_add(hx, lx, px); two_sum_add(hy, ly, py); two_sum_add(hz, lz, pz); }
   }
-  __device__ __forceinline__ void get(double &x, double &y, double &z) const {
-    if (ACC64) { x = dx; y = dy; z = dz; }
+  __device__ __forceinline__ void get(bool acc64, double &x, double &y, double &z) const {
+    if (acc64) { x = dx; y = dy; z = dz; }
     else { x = (double)hx + (double)lx; y = (double)hy + (double)ly; z = (double)hz + (double)lz; }
   }
 };
 
-// Monopole / body terms: a += m d / (|d|^2 + eps^2)^{3/2}, d = source - body.
-template <bool COUNT>
-__device__ __forceinline__ void flush_mono(const WarpSmemMono &S, int cnt, int lane, float xh,
-                                           float yh, float zh, float xl, float yl, float zl,
-                                           float eps2, float &px, float &py, float &pz,
-                                           int gi, int &c_m2p, int &c_p2p) {
+// 1/sqrt(r2) for an active lane, 0 otherwise.  With eps > 0, r2 >= eps^2 > 0;
+// with eps = 0 a term with r2 = 0 (coincident bodies) contributes nothing.
+template <bool EPS0>
+__device__ __forceinline__ float inv_r(float r2, bool act) {
+  const float inv = rsqrtf(r2);
+  if (EPS0) return (act && r2 > 0.f) ? inv : 0.f;
+  return act ? inv : 0.f;
+}
+
+// Point terms: a += m d / (|d|^2 + eps^2)^{3/2}, d = source - body (hi/lo).
+template <bool EPS0, bool COUNT>
+__device__ __forceinline__ void flush_point(const WarpSmem &S, int cnt, int lane, float xh,
+                                            float yh, float zh, float xl, float yl, float zl,
+                                            float eps2, float &px, float &py, float &pz,
+                                            int gi, int &c_m2p, int &c_p2p) {
   px = py = pz = 0.f;
 #pragma unroll 4
   for (int k = 0; k < cnt; ++k) {
-    float4 a = S.la[k];
-    float4 b = S.lb[k];
-    bool act = (__float_as_uint(b.w) >> lane) & 1u;
-    float dx = (a.x - xh) + (b.x - xl);
-    float dy = (a.y - yh) + (b.y - yl);
-    float dz = (a.z - zh) + (b.z - zl);
-    float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
-    float inv = rsqrtf(r2);
-    inv = (act && r2 > 0.f) ? inv : 0.f;
-    float s = a.w * (inv * inv * inv);
+    const float4 a = S.la[k];
+    const float4 b = S.lb[k];
+    const bool act = (__float_as_uint(b.w) >> lane) & 1u;
+    const float dx = (a.x - xh) + (b.x - xl);
+    const float dy = (a.y - yh) + (b.y - yl);
+    const float dz = (a.z - zh) + (b.z - zl);
+    const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+    const float inv = inv_r<EPS0>(r2, act);
+    const float s = a.w * (inv * inv * inv);
     px = fmaf(s, dx, px);
     py = fmaf(s, dy, py);
     pz = fmaf(s, dz, pz);
@@ -137,377 +163,531 @@ __device__ __forceinline__ void flush_mono(const WarpSmemMono &S, int cnt, int l
   }
 }
 
-// Quadrupole node terms: a += m d r^-3 - Q d r^-5 + (5/2) (d.Q d) d r^-7 with
-// r^2 = |d|^2 + eps^2 (the negative gradient of -m/r - y.Q y/(2 r^5), y = -d).
-template <bool COUNT>
-__device__ __forceinline__ void flush_quad(const WarpSmemQuad &S, int cnt, int lane, float xh,
+// Quadrupole node term with d = source - body:
+//   a += m d r^-3 - Q d r^-5 + (5/2) (d.Q d) d r^-7,  r^2 = |d|^2 + eps^2
+// (the negative gradient of -m/r - y.Q y/(2 r^5), y = -d).
+__device__ __forceinline__ void quad_term(float dx, float dy, float dz, float m, float4 q0,
+                                          float qxz, float qyz, float inv, float &px,
+                                          float &py, float &pz) {
+  const float inv2 = inv * inv;
+  const float inv3 = inv2 * inv;
+  const float inv5 = inv3 * inv2;
+  const float inv7 = inv5 * inv2;
+  const float qx = fmaf(q0.x, dx, fmaf(q0.w, dy, qxz * dz));
+  const float qy = fmaf(q0.w, dx, fmaf(q0.y, dy, qyz * dz));
+  const float qz = fmaf(qxz, dx, fmaf(qyz, dy, q0.z * dz));
+  const float dqd = fmaf(dx, qx, fmaf(dy, qy, dz * qz));
+  const float s = fmaf(m, inv3, 2.5f * (dqd * inv7));
+  px = fmaf(s, dx, fmaf(-qx, inv5, px));
+  py = fmaf(s, dy, fmaf(-qy, inv5, py));
+  pz = fmaf(s, dz, fmaf(-qz, inv5, pz));
+}
+
+// Far node terms on warp-relative coordinates (monopole, or + quadrupole).
+template <int ORDER, bool EPS0, bool COUNT>
+__device__ __forceinline__ void flush_far(const void *Sv, int cnt, int lane, float xr, float yr,
+                                          float zr, float eps2, float &px, float &py, float &pz,
+                                          int &c_m2p) {
+  const WarpSmem &S = *reinterpret_cast<const WarpSmem *>(Sv);
+  px = py = pz = 0.f;
+#pragma unroll 2
+  for (int k = 0; k < cnt; ++k) {
+    const float4 a = S.fa[k];
+    const float4 c = S.fc[k];
+    const bool act = (__float_as_uint(c.z) >> lane) & 1u;
+    const float dx = a.x - xr, dy = a.y - yr, dz = a.z - zr;
+    const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+    const float inv = inv_r<EPS0>(r2, act);
+    if constexpr (ORDER == 2) {
+      const float4 q0 = reinterpret_cast<const WarpSmemQ *>(Sv)->fb[k];
+      quad_term(dx, dy, dz, a.w, q0, c.x, c.y, inv, px, py, pz);
+    } else {
+      const float s = a.w * (inv * inv * inv);
+      px = fmaf(s, dx, px);
+      py = fmaf(s, dy, py);
+      pz = fmaf(s, dz, pz);
+    }
+    if (COUNT && act) ++c_m2p;
+  }
+}
+
+// Near quadrupole node terms on hi/lo coordinates.
+template <bool EPS0, bool COUNT>
+__device__ __forceinline__ void flush_near(const WarpSmemQ &S, int cnt, int lane, float xh,
                                            float yh, float zh, float xl, float yl, float zl,
                                            float eps2, float &px, float &py, float &pz,
                                            int &c_m2p) {
   px = py = pz = 0.f;
 #pragma unroll 2
   for (int k = 0; k < cnt; ++k) {
-    float4 a = S.qa[k], b = S.qb[k], q0 = S.qc[k], q1 = S.qd[k];
-    bool act = (__float_as_uint(b.w) >> lane) & 1u;
-    float dx = (a.x - xh) + (b.x - xl);
-    float dy = (a.y - yh) + (b.y - yl);
-    float dz = (a.z - zh) + (b.z - zl);
-    float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
-    float inv = rsqrtf(r2);
-    inv = (act && r2 > 0.f) ? inv : 0.f;
-    float inv2 = inv * inv;
-    float inv3 = inv2 * inv;
-    float inv5 = inv3 * inv2;
-    float inv7 = inv5 * inv2;
-    float qx = fmaf(q0.x, dx, fmaf(q0.w, dy, q1.x * dz));
-    float qy = fmaf(q0.w, dx, fmaf(q0.y, dy, q1.y * dz));
-    float qz = fmaf(q1.x, dx, fmaf(q1.y, dy, q0.z * dz));
-    float dqd = fmaf(dx, qx, fmaf(dy, qy, dz * qz));
-    float s = fmaf(a.w, inv3, 2.5f * dqd * inv7);
-    px = fmaf(s, dx, fmaf(-qx, inv5, px));
-    py = fmaf(s, dy, fmaf(-qy, inv5, py));
-    pz = fmaf(s, dz, fmaf(-qz, inv5, pz));
+    const float4 a = S.qa[k], b = S.qb[k], q0 = S.qc[k], q1 = S.qd[k];
+    const bool act = (__float_as_uint(b.w) >> lane) & 1u;
+    const float dx = (a.x - xh) + (b.x - xl);
+    const float dy = (a.y - yh) + (b.y - yl);
+    const float dz = (a.z - zh) + (b.z - zl);
+    const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+    const float inv = inv_r<EPS0>(r2, act);
+    quad_term(dx, dy, dz, a.w, q0, q1.x, q1.y, inv, px, py, pz);
     if (COUNT && act) ++c_m2p;
   }
 }
 
-template <int ORDER, bool ACC64, bool COUNT>
+// Counted variant only: lockstep iteration counts of lane-group-split lists.
+__device__ __forceinline__ void split_costs(const float4 *m4, int comp, int cnt, int lane,
+                                            unsigned long long *st) {
+  int c2 = 0, c4 = 0, c32 = 0, full = 0;
+  const unsigned h = 0xFFFFu << (16 * (lane >> 4)), q = 0xFFu << (8 * (lane >> 3));
+  for (int k = 0; k < cnt; ++k) {
+    const float4 v = m4[k];
+    const unsigned m = __float_as_uint(comp == 3 ? v.w : v.z);
+    c2 += (m & h) != 0;
+    c4 += (m & q) != 0;
+    c32 += (m >> lane) & 1u;
+    full += m == 0xFFFFFFFFu;
+  }
+  c2 = __reduce_max_sync(0xffffffffu, c2);
+  c4 = __reduce_max_sync(0xffffffffu, c4);
+  c32 = __reduce_max_sync(0xffffffffu, c32);
+  if (lane == 0) {
+    st[0] += c2; st[1] += c4; st[2] += c32; st[3] += full;
+  }
+}
+
+// Stack slot access: [0, kSmemStack) in shared memory, the rest in the warp's
+// global overflow area.
+struct Stack {
+  uint32_t *sa, *sm;
+  uint2 *g;
+  __device__ __forceinline__ void get(int i, uint32_t &a, uint32_t &m) const {
+    if (i < kSmemStack) { a = sa[i]; m = sm[i]; }
+    else { uint2 v = g[i - kSmemStack]; a = v.x; m = v.y; }
+  }
+  __device__ __forceinline__ void set(int i, uint32_t a, uint32_t m) const {
+    if (i < kSmemStack) { sa[i] = a; sm[i] = m; }
+    else g[i - kSmemStack] = make_uint2(a, m);
+  }
+  __device__ __forceinline__ void set_a(int i, uint32_t a) const {
+    if (i < kSmemStack) sa[i] = a;
+    else g[i - kSmemStack].x = a;
+  }
+};
+
+template <int ORDER, bool EPS0, bool COUNT>
 __global__ void __launch_bounds__(32 * kWalkWarps)
 k_walk(WalkArgs A) {
-  using Smem = typename std::conditional<ORDER == 2, WarpSmemQuad, WarpSmemMono>::type;
+  using Smem = typename std::conditional<ORDER == 2, WarpSmemQ, WarpSmem>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   Smem &S = reinterpret_cast<Smem *>(smem_raw)[wib];
-  WarpSmemMono &M = *reinterpret_cast<WarpSmemMono *>(&S);
+  WarpSmem &M = *reinterpret_cast<WarpSmem *>(&S);
+  const Stack st{M.st_a, M.st_m, A.gstack + (size_t)(blockIdx.x * kWalkWarps + wib) * kGlobStack};
 
   const int n = A.n;
-  const int wbeg = (blockIdx.x * kWalkWarps + wib) * 32;
-  if (wbeg >= n) return;                       // warp-uniform
-  const int wend = min(n, wbeg + 32);
-  const int gi = wbeg + lane;
-  const bool valid = gi < n;
   const int nn = *A.nnodes;
-
-  float xh = 0, yh = 0, zh = 0, xl = 0, yl = 0, zl = 0;
-  if (valid) {
-    float4 h = A.bhi[gi], l = A.blo[gi];
-    xh = h.x; yh = h.y; zh = h.z; xl = l.x; yl = l.y; zl = l.z;
-  }
-  // warp bounding box of the bodies (hi parts), and its magnitude
-  float bminx = valid ? xh : INFINITY, bminy = valid ? yh : INFINITY, bminz = valid ? zh : INFINITY;
-  float bmaxx = valid ? xh : -INFINITY, bmaxy = valid ? yh : -INFINITY, bmaxz = valid ? zh : -INFINITY;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    bminx = fminf(bminx, __shfl_xor_sync(0xffffffffu, bminx, o));
-    bminy = fminf(bminy, __shfl_xor_sync(0xffffffffu, bminy, o));
-    bminz = fminf(bminz, __shfl_xor_sync(0xffffffffu, bminz, o));
-    bmaxx = fmaxf(bmaxx, __shfl_xor_sync(0xffffffffu, bmaxx, o));
-    bmaxy = fmaxf(bmaxy, __shfl_xor_sync(0xffffffffu, bmaxy, o));
-    bmaxz = fmaxf(bmaxz, __shfl_xor_sync(0xffffffffu, bmaxz, o));
-  }
-  const float bR = fmaxf(fmaxf(fmaxf(fabsf(bminx), fabsf(bmaxx)), fmaxf(fabsf(bminy), fabsf(bmaxy))),
-                         fmaxf(fabsf(bminz), fabsf(bmaxz)));
   const double side = A.geom[3];
   const float theta2f = A.theta2f;
   const float eps2 = A.eps2;
+  const bool acc64 = A.acc64 != 0;
 
-  Accum<ACC64> acc;
-  int c_m2p = 0, c_p2p = 0, c_tests = 0;
-  unsigned long long w_batches = 0, w_items = 0, w_mixed = 0, w_fp64 = 0, w_mono = 0, w_quad = 0;
-  int w_maxsp = 0;
-  int nmono = 0, nquad = 0;
-  int sp = 0;
-  bool abort = false;
-  if (lane == 0) {
-    M.st_a[0] = 0u;                            // root node, count 1, kind node
-    M.st_m[0] = __ballot_sync(0xffffffffu, valid);
-  } else {
-    __ballot_sync(0xffffffffu, valid);
-  }
-  sp = 1;
-  __syncwarp();
+  for (;;) {
+    int task = 0;
+    if (lane == 0) task = (int)atomicAdd(A.task_counter, 1u);
+    task = __shfl_sync(0xffffffffu, task, 0);
+    if (task >= A.ntasks) break;
 
-  for (int iter = 0; sp > 0; ++iter) {
-    if (iter > A.max_iter) {                    // cannot happen on a well-formed tree
-      if (lane == 0) latch_error(A.status, kErrTree);
-      abort = true;
-      break;
-    }
-    // ---- pop up to 32 items from the top entries (lane 0 = top of stack)
-    const int ke = sp - 1 - lane;
-    uint32_t ea = 0, em = 0;
-    int ecnt = 0;
-    if (ke >= 0) {
-      ea = M.st_a[ke];
-      em = M.st_m[ke];
-      ecnt = (int)((ea >> kCntShift) & 63u) + 1;
-    }
-    const int incl = warp_incl_scan_i(ecnt, lane);
-    const int excl = incl - ecnt;
-    const int take = max(0, min(ecnt, 32 - excl));
-    const unsigned full = __ballot_sync(0xffffffffu, ecnt > 0 && take == ecnt);
-    const int nfull = __popc(full);
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    const int nitems = min(total, 32);
-    __syncwarp();
-    if (take > 0 && take < ecnt) {             // the one partially consumed entry stays
-      M.st_a[ke] = (((ea & kFirstMask) + take) & kFirstMask) |
-                   ((uint32_t)(ecnt - take - 1) << kCntShift) | (ea & kKindBody);
-    }
-    sp -= nfull;
-    const unsigned starts = __reduce_or_sync(0xffffffffu, take > 0 ? (1u << excl) : 0u);
-    const int stpos = 31 - __clz(starts & (0xffffffffu >> (31 - lane)));
-    const int owner = __popc(starts & ((1u << stpos) - 1u));
-    const uint32_t oa = __shfl_sync(0xffffffffu, ea, owner);
-    const uint32_t omask = __shfl_sync(0xffffffffu, em, owner);
-    const bool have = lane < nitems;
-    if (COUNT) { ++w_batches; w_items += nitems; }
-    const bool kbody = (oa & kKindBody) != 0;
-    const int item = (int)(oa & kFirstMask) + (lane - stpos);
+    const int wbeg = task * 32;
+    const int wend = min(n, wbeg + 32);
+    const int gi = wbeg + lane;
+    const bool valid = gi < n;
 
-    // ---- load and classify (lane = item)
-    float4 r0 = make_float4(0, 0, 0, 0), r1 = make_float4(0, 0, 0, 0);
-    int4 tp = make_int4(-1, 0, 0, 0);
-    bool single = false;                       // a point term (body or one-body leaf)
-    bool bad = false;
-    if (have) {
-      if (kbody) {
-        bad = item >= n;
-        if (!bad) { r0 = A.bhi[item]; r1 = A.blo[item]; }
-        tp = make_int4(-1, 0, item, item + 1);
-        single = true;
-      } else {
-        bad = item >= nn;
-        if (!bad) {
-          tp = A.topo[item];
-          r0 = A.rec0[item];
-          r1 = A.rec1[item];
-          single = r1.w < 0.f;                 // one-body leaf: record holds the body itself
-          bad = (tp.x >= 0 && (tp.x <= 0 || tp.x + tp.y > nn)) || tp.z < 0 || tp.w > n ||
-                tp.z >= tp.w;
-        }
-      }
+    float xh = 0, yh = 0, zh = 0, xl = 0, yl = 0, zl = 0;
+    if (valid) {
+      const float4 h = A.bhi[gi], l = A.blo[gi];
+      xh = h.x; yh = h.y; zh = h.z; xl = l.x; yl = l.y; zl = l.z;
     }
-    if (__any_sync(0xffffffffu, bad)) {
-      if (lane == 0) latch_error(A.status, kErrTree);
-      abort = true;
-      break;
+    // warp origin = lane 0's body (always valid); warp-relative FP32 coordinates
+    const float ohx = __shfl_sync(0xffffffffu, xh, 0), ohy = __shfl_sync(0xffffffffu, yh, 0),
+                ohz = __shfl_sync(0xffffffffu, zh, 0), olx = __shfl_sync(0xffffffffu, xl, 0),
+                oly = __shfl_sync(0xffffffffu, yl, 0), olz = __shfl_sync(0xffffffffu, zl, 0);
+    const float xr = valid ? (xh - ohx) + (xl - olx) : 0.f;
+    const float yr = valid ? (yh - ohy) + (yl - oly) : 0.f;
+    const float zr = valid ? (zh - ohz) + (zl - olz) : 0.f;
+    // bounding box of the bodies (hi parts) and extent around the origin
+    float bminx = valid ? xh : INFINITY, bminy = valid ? yh : INFINITY, bminz = valid ? zh : INFINITY;
+    float bmaxx = valid ? xh : -INFINITY, bmaxy = valid ? yh : -INFINITY, bmaxz = valid ? zh : -INFINITY;
+    float rw2 = fmaf(xr, xr, fmaf(yr, yr, zr * zr));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      bminx = fminf(bminx, __shfl_xor_sync(0xffffffffu, bminx, o));
+      bminy = fminf(bminy, __shfl_xor_sync(0xffffffffu, bminy, o));
+      bminz = fminf(bminz, __shfl_xor_sync(0xffffffffu, bminz, o));
+      bmaxx = fmaxf(bmaxx, __shfl_xor_sync(0xffffffffu, bmaxx, o));
+      bmaxy = fmaxf(bmaxy, __shfl_xor_sync(0xffffffffu, bmaxy, o));
+      bmaxz = fmaxf(bmaxz, __shfl_xor_sync(0xffffffffu, bmaxz, o));
+      rw2 = fmaxf(rw2, __shfl_xor_sync(0xffffffffu, rw2, o));
     }
-    unsigned accm = 0, openm = 0;
-    bool mixed = false;
-    if (have) {
-      if (single) {
-        accm = omask;
-      } else {
-        const float cx = r0.x, cy = r0.y, cz = r0.z, l2 = r1.w;
-        const float C = fmaxf(fabsf(cx), fmaxf(fabsf(cy), fabsf(cz)));
-        const float del = (bR + C) * 1.9073486e-6f;      // 2^-19 (R + C): bound on hi/lo + rounding
-        float gx = fmaxf(fmaxf(bminx - cx, cx - bmaxx), 0.f);
-        float gy = fmaxf(fmaxf(bminy - cy, cy - bmaxy), 0.f);
-        float gz = fmaxf(fmaxf(bminz - cz, cz - bmaxz), 0.f);
-        gx = fmaxf(gx - del, 0.f); gy = fmaxf(gy - del, 0.f); gz = fmaxf(gz - del, 0.f);
-        float fx = fmaxf(fabsf(cx - bminx), fabsf(cx - bmaxx)) + del;
-        float fy = fmaxf(fabsf(cy - bminy), fabsf(cy - bmaxy)) + del;
-        float fz = fmaxf(fabsf(cz - bminz), fabsf(cz - bmaxz)) + del;
-        float dmin2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
-        float dmax2 = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
-        bool guard_any = A.mac_guard && tp.z < wend && tp.w > wbeg;
-        if (!guard_any && l2 < theta2f * dmin2 * 0.999f) accm = omask;
-        else if (l2 > theta2f * dmax2 * 1.001f) openm = omask;
-        else mixed = true;
-      }
-    }
-    if (COUNT) {                               // MAC tests per body (introspection only)
-      for (int j = 0; j < nitems; ++j) {
-        const bool sj = __shfl_sync(0xffffffffu, single, j);
-        const unsigned mj = __shfl_sync(0xffffffffu, omask, j);
-        const int bj = __shfl_sync(0xffffffffu, tp.z, j), ej = __shfl_sync(0xffffffffu, tp.w, j);
-        if (!sj && ((mj >> lane) & 1u) && !(A.mac_guard && bj <= gi && gi < ej)) ++c_tests;
-      }
-    }
-    // ---- exact per-lane test for mixed nodes
-    unsigned mixed_bits = __ballot_sync(0xffffffffu, mixed);
-    if (COUNT) w_mixed += __popc(mixed_bits);
-    while (mixed_bits) {
-      const int j = __ffs(mixed_bits) - 1;
-      mixed_bits &= mixed_bits - 1;
-      const float cx = __shfl_sync(0xffffffffu, r0.x, j);
-      const float cy = __shfl_sync(0xffffffffu, r0.y, j);
-      const float cz = __shfl_sync(0xffffffffu, r0.z, j);
-      const float clx = __shfl_sync(0xffffffffu, r1.x, j);
-      const float cly = __shfl_sync(0xffffffffu, r1.y, j);
-      const float clz = __shfl_sync(0xffffffffu, r1.z, j);
-      const float l2 = __shfl_sync(0xffffffffu, r1.w, j);
-      const unsigned mk = __shfl_sync(0xffffffffu, omask, j);
-      const int nb = __shfl_sync(0xffffffffu, tp.z, j);
-      const int ne = __shfl_sync(0xffffffffu, tp.w, j);
-      const int node = __shfl_sync(0xffffffffu, item, j);
-      bool a_i = false, o_i = false;
-      if ((mk >> lane) & 1u) {
-        if (A.mac_guard && nb <= gi && gi < ne) {
-          o_i = true;
-        } else {
-          float dx = (cx - xh) + (clx - xl);
-          float dy = (cy - yh) + (cly - yl);
-          float dz = (cz - zh) + (clz - zl);
-          float D2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          float diff = l2 - theta2f * D2;
-          if (fabsf(diff) <= 1.52587890625e-5f * l2) {     // 2^-16 band: decide in FP64
-            const double X = A.ncom[3 * node], Y = A.ncom[3 * node + 1], Z = A.ncom[3 * node + 2];
-            const double x = A.pos_s[3 * gi], y = A.pos_s[3 * gi + 1], z = A.pos_s[3 * gi + 2];
-            const double ddx = __dsub_rn(X, x), ddy = __dsub_rn(Y, y), ddz = __dsub_rn(Z, z);
-            const double D2d = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)),
-                                         __dmul_rn(ddz, ddz));
-            const double l = ldexp(side, -A.ndepth[node]);
-            a_i = __dmul_rn(l, l) < __dmul_rn(A.theta2d, D2d);
-            if (COUNT) atomicAdd(&A.stats[kStatFp64], 1ull);
-          } else {
-            a_i = diff < 0.f;
-          }
-          o_i = !a_i;
-        }
-      }
-      const unsigned am = __ballot_sync(0xffffffffu, a_i);
-      const unsigned om = __ballot_sync(0xffffffffu, o_i);
-      if (lane == j) { accm = am; openm = om; }
-    }
+    const float bR = fmaxf(fmaxf(fmaxf(fabsf(bminx), fabsf(bmaxx)), fmaxf(fabsf(bminy), fabsf(bmaxy))),
+                           fmaxf(fabsf(bminz), fabsf(bmaxz)));
+    // a node with l^2 >= farl2 is at least R_w / 2 from every body that accepts it
+    // (D > l / theta), which bounds the far-path error of d by 5.5 * 2^-23 |d|
+    const float farl2 = 0.25f * theta2f * rw2 * 1.01f;
 
-    // ---- append accepted terms to the lists
-    const bool to_quad = (ORDER == 2) && accm != 0 && !single;
-    const bool to_mono = accm != 0 && !to_quad;
+    Accum acc;
+    int c_m2p = 0, c_p2p = 0, c_tests = 0;
+    unsigned long long w_batches = 0, w_items = 0, w_mixed = 0, w_mono = 0, w_quad = 0, w_far = 0;
+    unsigned long long w_split[4] = {0, 0, 0, 0};
+    int w_maxsp = 0;
+    int npt = 0, nfar = 0, nnear = 0;
+    int sp = 1;
+    bool abort = false;
     {
-      const unsigned bm = __ballot_sync(0xffffffffu, to_mono);
-      if (to_mono) {
-        int p = nmono + __popc(bm & ((1u << lane) - 1u));
-        M.la[p] = r0;
-        M.lb[p] = make_float4(r1.x, r1.y, r1.z, __uint_as_float(accm));
-        if (COUNT) M.ltag[p] = single ? tp.z : -1;
-      }
-      nmono += __popc(bm);
+      const unsigned vm = __ballot_sync(0xffffffffu, valid);
+      if (lane == 0) st.set(0, 0u, vm);        // root node, count 1, kind node
     }
-    if constexpr (ORDER == 2) {
-      const unsigned bq = __ballot_sync(0xffffffffu, to_quad);
-      if (to_quad) {
-        int p = nquad + __popc(bq & ((1u << lane) - 1u));
-        WarpSmemQuad &QS = S;
-        QS.qa[p] = r0;
-        QS.qb[p] = make_float4(r1.x, r1.y, r1.z, __uint_as_float(accm));
-        QS.qc[p] = A.quadf[2 * item];
-        QS.qd[p] = A.quadf[2 * item + 1];
-      }
-      nquad += __popc(bq);
-    }
-
-    // ---- push opened nodes (children range) or bucket bodies (chunks of <= 32)
-    int npush = 0;
-    if (openm != 0) npush = (tp.x >= 0) ? 1 : (tp.w - tp.z + 31) / 32;
-    const int pincl = warp_incl_scan_i(npush, lane);
-    const int ptotal = __shfl_sync(0xffffffffu, pincl, 31);
-    if (sp + ptotal > kStackCap) {
-      if (lane == 0) latch_error(A.status, kErrStack);
-      abort = true;
-      break;
-    }
-    if (npush > 0) {
-      int p = sp + pincl - npush;
-      if (tp.x >= 0) {
-        M.st_a[p] = (uint32_t)tp.x | ((uint32_t)(tp.y - 1) << kCntShift);
-        M.st_m[p] = openm;
-      } else {
-        for (int b = tp.z; b < tp.w; b += 32, ++p) {
-          int c = min(32, tp.w - b);
-          M.st_a[p] = (uint32_t)b | ((uint32_t)(c - 1) << kCntShift) | kKindBody;
-          M.st_m[p] = openm;
-        }
-      }
-    }
-    sp += ptotal;
-    if (COUNT) w_maxsp = max(w_maxsp, sp);
     __syncwarp();
 
-    // ---- evaluate full lists
-    if (nmono >= kFlushAt) {
-      if (COUNT) w_mono += nmono;
-      float px, py, pz;
-      flush_mono<COUNT>(M, nmono, lane, xh, yh, zh, xl, yl, zl, eps2, px, py, pz, gi, c_m2p, c_p2p);
-      acc.add(px, py, pz);
-      nmono = 0;
+    for (int iter = 0; sp > 0; ++iter) {
+      if (iter > A.max_iter) {                  // cannot happen on a well-formed tree
+        if (lane == 0) latch_error(A.status, kErrTree);
+        abort = true;
+        break;
+      }
+      // ---- pop up to 32 items from the top entries (lane 0 = top of stack)
+      const int ke = sp - 1 - lane;
+      uint32_t ea = 0, em = 0;
+      int ecnt = 0;
+      if (ke >= 0) {
+        st.get(ke, ea, em);
+        ecnt = (int)((ea >> kCntShift) & 63u) + 1;
+      }
+      const int incl = warp_incl_scan_i(ecnt, lane);
+      const int excl = incl - ecnt;
+      const int take = max(0, min(ecnt, 32 - excl));
+      const unsigned fullm = __ballot_sync(0xffffffffu, ecnt > 0 && take == ecnt);
+      const int nfull = __popc(fullm);
+      const int total = __shfl_sync(0xffffffffu, incl, 31);
+      const int nitems = min(total, 32);
       __syncwarp();
-    }
-    if constexpr (ORDER == 2) {
-      if (nquad >= kFlushAt) {
-        if (COUNT) w_quad += nquad;
+      if (take > 0 && take < ecnt) {           // the one partially consumed entry stays
+        st.set_a(ke, (((ea & kFirstMask) + take) & kFirstMask) |
+                         ((uint32_t)(ecnt - take - 1) << kCntShift) | (ea & kKindBody));
+      }
+      sp -= nfull;
+      const unsigned starts = __reduce_or_sync(0xffffffffu, take > 0 ? (1u << excl) : 0u);
+      const int stpos = 31 - __clz(starts & (0xffffffffu >> (31 - lane)));
+      const int owner = __popc(starts & ((1u << stpos) - 1u));
+      const uint32_t oa = __shfl_sync(0xffffffffu, ea, owner);
+      const uint32_t omask = __shfl_sync(0xffffffffu, em, owner);
+      const bool have = lane < nitems;
+      if (COUNT) { ++w_batches; w_items += nitems; }
+      const bool kbody = (oa & kKindBody) != 0;
+      const int item = (int)(oa & kFirstMask) + (lane - stpos);
+
+      // ---- load and classify (lane = item)
+      float4 r0 = make_float4(0, 0, 0, 0), r1 = make_float4(0, 0, 0, 0);
+      float4 q0 = make_float4(0, 0, 0, 0), q1 = make_float4(0, 0, 0, 0);
+      int4 tp = make_int4(-1, 0, 0, 0);
+      bool single = false;                     // a point term (body or one-body leaf)
+      bool bad = false;
+      if (have) {
+        if (kbody) {
+          bad = item >= n;
+          if (!bad) { r0 = A.bhi[item]; r1 = A.blo[item]; }
+          tp = make_int4(-1, 0, item, item + 1);
+          single = true;
+        } else {
+          bad = item >= nn;
+          if (!bad) {
+            tp = A.topo[item];
+            r0 = A.rec0[item];
+            r1 = A.rec1[item];
+            if constexpr (ORDER == 2) {        // in flight during classification
+              q0 = A.quadf[2 * item];
+              q1 = A.quadf[2 * item + 1];
+            }
+            single = r1.w < 0.f;               // one-body leaf: record holds the body itself
+            bad = (tp.x >= 0 && (tp.x <= 0 || tp.x + tp.y > nn)) || tp.z < 0 || tp.w > n ||
+                  tp.z >= tp.w;
+          }
+        }
+      }
+      if (__any_sync(0xffffffffu, bad)) {
+        if (lane == 0) latch_error(A.status, kErrTree);
+        abort = true;
+        break;
+      }
+      unsigned accm = 0, openm = 0;
+      bool mixed = false;
+      if (have) {
+        if (single) {
+          accm = omask;
+        } else {
+          const float cx = r0.x, cy = r0.y, cz = r0.z, l2 = r1.w;
+          const float C = fmaxf(fabsf(cx), fmaxf(fabsf(cy), fabsf(cz)));
+          const float del = (bR + C) * 1.9073486e-6f;    // 2^-19 (R + C): bound on hi/lo + rounding
+          float gx = fmaxf(fmaxf(bminx - cx, cx - bmaxx), 0.f);
+          float gy = fmaxf(fmaxf(bminy - cy, cy - bmaxy), 0.f);
+          float gz = fmaxf(fmaxf(bminz - cz, cz - bmaxz), 0.f);
+          gx = fmaxf(gx - del, 0.f); gy = fmaxf(gy - del, 0.f); gz = fmaxf(gz - del, 0.f);
+          const float fx = fmaxf(fabsf(cx - bminx), fabsf(cx - bmaxx)) + del;
+          const float fy = fmaxf(fabsf(cy - bminy), fabsf(cy - bmaxy)) + del;
+          const float fz = fmaxf(fabsf(cz - bminz), fabsf(cz - bmaxz)) + del;
+          const float dmin2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
+          const float dmax2 = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+          const bool guard_any = A.mac_guard && tp.z < wend && tp.w > wbeg;
+          if (!guard_any && l2 < theta2f * dmin2 * 0.999f) accm = omask;
+          else if (l2 > theta2f * dmax2 * 1.001f) openm = omask;
+          else mixed = true;
+        }
+      }
+      if (COUNT) {                             // MAC tests per body (introspection only)
+        for (int j = 0; j < nitems; ++j) {
+          const bool sj = __shfl_sync(0xffffffffu, single, j);
+          const unsigned mj = __shfl_sync(0xffffffffu, omask, j);
+          const int bj = __shfl_sync(0xffffffffu, tp.z, j), ej = __shfl_sync(0xffffffffu, tp.w, j);
+          if (!sj && ((mj >> lane) & 1u) && !(A.mac_guard && bj <= gi && gi < ej)) ++c_tests;
+        }
+      }
+      // ---- exact per-lane test for mixed nodes (node record re-read from L1 by all lanes)
+      unsigned mixed_bits = __ballot_sync(0xffffffffu, mixed);
+      if (COUNT) w_mixed += __popc(mixed_bits);
+      while (mixed_bits) {
+        const int j = __ffs(mixed_bits) - 1;
+        mixed_bits &= mixed_bits - 1;
+        const int node = __shfl_sync(0xffffffffu, item, j);
+        const unsigned mk = __shfl_sync(0xffffffffu, omask, j);
+        bool a_i = false, o_i = false;
+        if ((mk >> lane) & 1u) {
+          const int4 tj = A.topo[node];
+          if (A.mac_guard && tj.z <= gi && gi < tj.w) {
+            o_i = true;
+          } else {
+            const float4 c0 = A.rec0[node], c1 = A.rec1[node];
+            const float dx = (c0.x - xh) + (c1.x - xl);
+            const float dy = (c0.y - yh) + (c1.y - yl);
+            const float dz = (c0.z - zh) + (c1.z - zl);
+            const float D2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float diff = c1.w - theta2f * D2;
+            if (fabsf(diff) <= 1.52587890625e-5f * c1.w) {    // 2^-16 band: decide in FP64
+              const double X = A.ncom[3 * node], Y = A.ncom[3 * node + 1], Z = A.ncom[3 * node + 2];
+              const double x = A.pos_s[3 * gi], y = A.pos_s[3 * gi + 1], z = A.pos_s[3 * gi + 2];
+              const double ddx = __dsub_rn(X, x), ddy = __dsub_rn(Y, y), ddz = __dsub_rn(Z, z);
+              const double D2d = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)),
+                                           __dmul_rn(ddz, ddz));
+              const double l = ldexp(side, -A.ndepth[node]);
+              a_i = __dmul_rn(l, l) < __dmul_rn(A.theta2d, D2d);
+              if (COUNT) atomicAdd(&A.stats[kStatFp64], 1ull);
+            } else {
+              a_i = diff < 0.f;
+            }
+            o_i = !a_i;
+          }
+        }
+        const unsigned am = __ballot_sync(0xffffffffu, a_i);
+        const unsigned om = __ballot_sync(0xffffffffu, o_i);
+        if (lane == j) { accm = am; openm = om; }
+      }
+
+      // ---- append accepted terms: point / far / near
+      const bool node_term = accm != 0 && !single;
+      const bool to_far = node_term && r1.w >= farl2;
+      const bool to_near = (ORDER == 2) && node_term && !to_far;
+      const bool to_pt = accm != 0 && !to_far && !to_near;
+      {
+        const unsigned bm = __ballot_sync(0xffffffffu, to_pt);
+        if (to_pt) {
+          const int p = npt + __popc(bm & ((1u << lane) - 1u));
+          M.la[p] = r0;
+          M.lb[p] = make_float4(r1.x, r1.y, r1.z, __uint_as_float(accm));
+          if (COUNT) M.ltag[p] = single ? tp.z : -1;
+        }
+        npt += __popc(bm);
+      }
+      {
+        const unsigned bf = __ballot_sync(0xffffffffu, to_far);
+        if (to_far) {
+          const int p = nfar + __popc(bf & ((1u << lane) - 1u));
+          const float cx = (r0.x - ohx) + (r1.x - olx);
+          const float cy = (r0.y - ohy) + (r1.y - oly);
+          const float cz = (r0.z - ohz) + (r1.z - olz);
+          M.fa[p] = make_float4(cx, cy, cz, r0.w);
+          if constexpr (ORDER == 2) {
+            S.fb[p] = q0;
+            M.fc[p] = make_float4(q1.x, q1.y, __uint_as_float(accm), 0.f);
+          } else {
+            M.fc[p] = make_float4(0.f, 0.f, __uint_as_float(accm), 0.f);
+          }
+        }
+        nfar += __popc(bf);
+        if (COUNT) w_far += __popc(bf);
+      }
+      if constexpr (ORDER == 2) {
+        const unsigned bq = __ballot_sync(0xffffffffu, to_near);
+        if (to_near) {
+          const int p = nnear + __popc(bq & ((1u << lane) - 1u));
+          S.qa[p] = r0;
+          S.qb[p] = make_float4(r1.x, r1.y, r1.z, __uint_as_float(accm));
+          S.qc[p] = q0;
+          S.qd[p] = q1;
+        }
+        nnear += __popc(bq);
+      }
+
+      // ---- push opened nodes (children range) or bucket bodies (chunks of <= 32)
+      int npush = 0;
+      if (openm != 0) npush = (tp.x >= 0) ? 1 : (tp.w - tp.z + 31) / 32;
+      int pincl, ptotal;
+      if (__all_sync(0xffffffffu, npush <= 1)) {
+        const unsigned pb = __ballot_sync(0xffffffffu, npush == 1);
+        pincl = __popc(pb & (0xffffffffu >> (31 - lane)));
+        ptotal = __popc(pb);
+      } else {
+        pincl = warp_incl_scan_i(npush, lane);
+        ptotal = __shfl_sync(0xffffffffu, pincl, 31);
+      }
+      if (sp + ptotal > kStackCap) {
+        if (lane == 0) latch_error(A.status, kErrStack);
+        abort = true;
+        break;
+      }
+      if (npush > 0) {
+        int p = sp + pincl - npush;
+        if (tp.x >= 0) {
+          st.set(p, (uint32_t)tp.x | ((uint32_t)(tp.y - 1) << kCntShift), openm);
+        } else {
+          for (int b = tp.z; b < tp.w; b += 32, ++p) {
+            const int c = min(32, tp.w - b);
+            st.set(p, (uint32_t)b | ((uint32_t)(c - 1) << kCntShift) | kKindBody, openm);
+          }
+        }
+      }
+      sp += ptotal;
+      if (COUNT) w_maxsp = max(w_maxsp, sp);
+      __syncwarp();
+
+      // ---- evaluate full lists
+      if (npt >= kFlushAt) {
+        if (COUNT) { w_mono += npt; split_costs(M.lb, 3, npt, lane, w_split); }
         float px, py, pz;
-        flush_quad<COUNT>(S, nquad, lane, xh, yh, zh, xl, yl, zl,
-                          eps2, px, py, pz, c_m2p);
-        acc.add(px, py, pz);
-        nquad = 0;
+        flush_point<EPS0, COUNT>(M, npt, lane, xh, yh, zh, xl, yl, zl, eps2, px, py, pz, gi,
+                                 c_m2p, c_p2p);
+        acc.add(acc64, px, py, pz);
+        npt = 0;
         __syncwarp();
       }
-    }
-  }
-  if (COUNT) { w_mono += nmono; w_quad += nquad; }
-  if (!abort) {
-    if (nmono > 0) {
-      float px, py, pz;
-      flush_mono<COUNT>(M, nmono, lane, xh, yh, zh, xl, yl, zl, eps2, px, py, pz, gi, c_m2p, c_p2p);
-      acc.add(px, py, pz);
-    }
-    if constexpr (ORDER == 2) {
-      if (nquad > 0) {
+      if (nfar >= kFlushAt) {
+        if (COUNT) { w_quad += nfar; split_costs(M.fc, 2, nfar, lane, w_split); }
         float px, py, pz;
-        flush_quad<COUNT>(S, nquad, lane, xh, yh, zh, xl, yl, zl, eps2, px, py, pz, c_m2p);
-        acc.add(px, py, pz);
+        flush_far<ORDER, EPS0, COUNT>(&S, nfar, lane, xr, yr, zr, eps2, px, py, pz, c_m2p);
+        acc.add(acc64, px, py, pz);
+        nfar = 0;
+        __syncwarp();
+      }
+      if constexpr (ORDER == 2) {
+        if (nnear >= kFlushAt) {
+          if (COUNT) { w_quad += nnear; split_costs(S.qb, 3, nnear, lane, w_split); }
+          float px, py, pz;
+          flush_near<EPS0, COUNT>(S, nnear, lane, xh, yh, zh, xl, yl, zl, eps2, px, py, pz,
+                                  c_m2p);
+          acc.add(acc64, px, py, pz);
+          nnear = 0;
+          __syncwarp();
+        }
       }
     }
-  }
-  if (COUNT) {
-    const unsigned long long lt =
-        __reduce_add_sync(0xffffffffu, (unsigned)(valid ? c_m2p + c_p2p : 0));
-    if (lane == 0) {
-      atomicAdd(&A.stats[kStatBatches], w_batches);
-      atomicAdd(&A.stats[kStatItems], w_items);
-      atomicAdd(&A.stats[kStatMixed], w_mixed);
-      atomicAdd(&A.stats[kStatMono], w_mono);
-      atomicAdd(&A.stats[kStatQuad], w_quad);
-      atomicMax(&A.stats[kStatMaxSp], (unsigned long long)w_maxsp);
-      atomicAdd(&A.stats[kStatLaneTerms], lt);
+    if (!abort) {
+      if (COUNT) {
+        w_mono += npt; w_quad += nfar + nnear;
+        if (npt > 0) split_costs(M.lb, 3, npt, lane, w_split);
+        if (nfar > 0) split_costs(M.fc, 2, nfar, lane, w_split);
+        if constexpr (ORDER == 2) { if (nnear > 0) split_costs(S.qb, 3, nnear, lane, w_split); }
+      }
+      float px, py, pz;
+      if (npt > 0) {
+        flush_point<EPS0, COUNT>(M, npt, lane, xh, yh, zh, xl, yl, zl, eps2, px, py, pz, gi,
+                                 c_m2p, c_p2p);
+        acc.add(acc64, px, py, pz);
+      }
+      if (nfar > 0) {
+        flush_far<ORDER, EPS0, COUNT>(&S, nfar, lane, xr, yr, zr, eps2, px, py, pz, c_m2p);
+        acc.add(acc64, px, py, pz);
+      }
+      if constexpr (ORDER == 2) {
+        if (nnear > 0) {
+          flush_near<EPS0, COUNT>(S, nnear, lane, xh, yh, zh, xl, yl, zl, eps2, px, py, pz, c_m2p);
+          acc.add(acc64, px, py, pz);
+        }
+      }
     }
-  }
-  if (!valid) return;
-  double ax, ay, az;
-  acc.get(ax, ay, az);
-  ax *= A.G; ay *= A.G; az *= A.G;
-  const int64_t ci = A.perm[gi];
-  A.acc[3 * ci] = ax;
-  A.acc[3 * ci + 1] = ay;
-  A.acc[3 * ci + 2] = az;
-  if (A.vel) {                                // fused closing kick of the leapfrog
-    A.vel[3 * ci] = __dadd_rn(A.vel[3 * ci], __dmul_rn(A.kick, ax));
-    A.vel[3 * ci + 1] = __dadd_rn(A.vel[3 * ci + 1], __dmul_rn(A.kick, ay));
-    A.vel[3 * ci + 2] = __dadd_rn(A.vel[3 * ci + 2], __dmul_rn(A.kick, az));
-  }
-  if (COUNT) {
-    A.counts[3 * ci] = c_m2p;
-    A.counts[3 * ci + 1] = c_p2p;
-    A.counts[3 * ci + 2] = c_tests;
+    __syncwarp();
+    if (COUNT) {
+      const unsigned long long lt =
+          __reduce_add_sync(0xffffffffu, (unsigned)(valid ? c_m2p + c_p2p : 0));
+      if (lane == 0) {
+        atomicAdd(&A.stats[kStatBatches], w_batches);
+        atomicAdd(&A.stats[kStatItems], w_items);
+        atomicAdd(&A.stats[kStatMixed], w_mixed);
+        atomicAdd(&A.stats[kStatMono], w_mono);
+        atomicAdd(&A.stats[kStatQuad], w_quad);
+        atomicMax(&A.stats[kStatMaxSp], (unsigned long long)w_maxsp);
+        atomicAdd(&A.stats[kStatLaneTerms], lt);
+        atomicAdd(&A.stats[kStatSplit2], w_split[0]);
+        atomicAdd(&A.stats[kStatSplit4], w_split[1]);
+        atomicAdd(&A.stats[kStatSplit32], w_split[2]);
+        atomicAdd(&A.stats[kStatFull], w_split[3]);
+        atomicAdd(&A.stats[kStatFar], w_far);
+      }
+    }
+    if (valid) {
+      double ax, ay, az;
+      acc.get(acc64, ax, ay, az);
+      ax *= A.G; ay *= A.G; az *= A.G;
+      const int64_t ci = A.perm[gi];
+      A.acc[3 * ci] = ax;
+      A.acc[3 * ci + 1] = ay;
+      A.acc[3 * ci + 2] = az;
+      if (A.vel) {                              // fused closing kick of the leapfrog
+        A.vel[3 * ci] = __dadd_rn(A.vel[3 * ci], __dmul_rn(A.kick, ax));
+        A.vel[3 * ci + 1] = __dadd_rn(A.vel[3 * ci + 1], __dmul_rn(A.kick, ay));
+        A.vel[3 * ci + 2] = __dadd_rn(A.vel[3 * ci + 2], __dmul_rn(A.kick, az));
+      }
+      if (COUNT) {
+        A.counts[3 * ci] = c_m2p;
+        A.counts[3 * ci + 1] = c_p2p;
+        A.counts[3 * ci + 2] = c_tests;
+      }
+    }
   }
 }
 
-template <int ORDER, bool ACC64, bool COUNT>
-int launch_walk(Ctx *c, const WalkArgs &A) {
-  using Smem = typename std::conditional<ORDER == 2, WarpSmemQuad, WarpSmemMono>::type;
+template <int ORDER, bool EPS0, bool COUNT>
+int launch_walk(Ctx *c, WalkArgs A) {
+  using Smem = typename std::conditional<ORDER == 2, WarpSmemQ, WarpSmem>::type;
   const size_t smem = sizeof(Smem) * kWalkWarps;
-  auto kern = k_walk<ORDER, ACC64, COUNT>;
-  static bool configured[64] = {false};
-  int dev = c->device < 64 ? c->device : 63;
-  if (!configured[dev]) {
+  auto kern = k_walk<ORDER, EPS0, COUNT>;
+  static int blocks_per_sm[64] = {0};
+  const int dev = c->device < 64 ? c->device : 63;
+  if (blocks_per_sm[dev] == 0) {
     GRAV_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    configured[dev] = true;
+    int b = 0;
+    GRAV_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, 32 * kWalkWarps, smem));
+    blocks_per_sm[dev] = b > 0 ? b : 1;
   }
-  const int warps = (A.n + 31) / 32;
-  const int blocks = (warps + kWalkWarps - 1) / kWalkWarps;
+  int blocks = blocks_per_sm[dev] * c->num_sms;
+  const int need = (A.ntasks + kWalkWarps - 1) / kWalkWarps;
+  if (blocks > need) blocks = need;
+  if (blocks < 1) blocks = 1;
+  const size_t gneed = (size_t)blocks * kWalkWarps * kGlobStack;
+  if (gneed > c->walk_gstack_cap) {
+    if (c->walk_gstack) cudaFree(c->walk_gstack);
+    c->walk_gstack = nullptr;
+    c->walk_gstack_cap = 0;
+    GRAV_CUDA_TRY(cudaMalloc(&c->walk_gstack, gneed * sizeof(uint2)));
+    c->walk_gstack_cap = gneed;
+  }
+  A.gstack = reinterpret_cast<uint2 *>(c->walk_gstack);
+  GRAV_CUDA_TRY(cudaMemsetAsync(A.task_counter, 0, sizeof(unsigned), c->stream));
   kern<<<blocks, 32 * kWalkWarps, smem, c->stream>>>(A);
   ++c->launches;
   return cuda_status(cudaGetLastError());
@@ -518,32 +698,35 @@ int launch_walk(Ctx *c, const WalkArgs &A) {
 int walk_forces(Ctx *c, double theta, double eps, double *acc, int32_t *counts, double *vel,
                 double kick) {
   Tree &t = c->t;
-  WalkArgs A;
+  WalkArgs A{};
   A.bhi = t.body_hi; A.blo = t.body_lo; A.pos_s = t.pos_s;
   A.rec0 = t.nrec0; A.rec1 = t.nrec1; A.quadf = t.nquadf;
   A.topo = t.topo; A.ndepth = t.ndepth; A.ncom = t.ncom; A.geom = t.geom;
   A.perm = t.idx; A.nnodes = t.nnodes;
   A.n = (int)c->n;
+  A.ntasks = (int)((c->n + 31) / 32);
   A.theta2d = theta * theta;
   A.theta2f = (float)(theta * theta);
   A.eps2 = (float)(eps * eps);
   A.G = c->params.G;
   A.mac_guard = c->params.mac_guard;
+  A.acc64 = c->params.accum == 1;
   A.acc = acc; A.counts = counts; A.vel = vel; A.kick = kick;
   A.status = c->d_status;
   A.max_iter = (int)(8 * c->n + 64);
+  A.task_counter = t.scalars + 120;
   A.stats = c->walk_stats;
   if (counts) {
-    GRAV_CUDA_TRY(cudaMemsetAsync(c->walk_stats, 0, sizeof(unsigned long long) * 8, c->stream));
+    GRAV_CUDA_TRY(cudaMemsetAsync(c->walk_stats, 0, sizeof(unsigned long long) * 16, c->stream));
   }
   const bool q = c->params.order == 2;
-  const bool d64 = c->params.accum == 1;
+  const bool e0 = !(A.eps2 > 0.f);
   if (counts) {
-    if (q) return d64 ? launch_walk<2, true, true>(c, A) : launch_walk<2, false, true>(c, A);
-    return d64 ? launch_walk<0, true, true>(c, A) : launch_walk<0, false, true>(c, A);
+    if (q) return e0 ? launch_walk<2, true, true>(c, A) : launch_walk<2, false, true>(c, A);
+    return e0 ? launch_walk<0, true, true>(c, A) : launch_walk<0, false, true>(c, A);
   }
-  if (q) return d64 ? launch_walk<2, true, false>(c, A) : launch_walk<2, false, false>(c, A);
-  return d64 ? launch_walk<0, true, false>(c, A) : launch_walk<0, false, false>(c, A);
+  if (q) return e0 ? launch_walk<2, true, false>(c, A) : launch_walk<2, false, false>(c, A);
+  return e0 ? launch_walk<0, true, false>(c, A) : launch_walk<0, false, false>(c, A);
 }
 
 }  // namespace grav

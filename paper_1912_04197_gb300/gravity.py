@@ -226,7 +226,7 @@ def gravity_sync(ctx: Context):
 _DBG_DTYPES = {DBG_ROOT: (np.float64, 4), DBG_KEYS: (np.uint64, 1), DBG_PERM: (np.uint32, 1),
                DBG_TOPO: (np.int32, 4), DBG_DEPTH: (np.int32, 1), DBG_PARENT: (np.int32, 1),
                DBG_MASS: (np.float64, 1), DBG_COM: (np.float64, 3), DBG_QUAD: (np.float64, 6),
-               DBG_WALKSTATS: (np.uint64, 8)}
+               DBG_WALKSTATS: (np.uint64, 16)}
 
 
 def gravity_debug_export(ctx: Context, what: int, n: int) -> np.ndarray:
