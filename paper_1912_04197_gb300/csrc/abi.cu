@@ -138,6 +138,7 @@ int gravity_create(gravity_ctx **out, int device, void *cuda_stream) {
   if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMalloc(&c.t.nnodes, sizeof(int32_t)));
   if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMalloc(&c.t.scalars, 128 * sizeof(uint32_t)));
   if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMalloc(&c.walk_stats, 16 * sizeof(unsigned long long)));
+  if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMalloc(&c.walk_queues, sizeof(unsigned) * (c.num_sms + 1)));
   if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMemset(c.walk_stats, 0, 16 * sizeof(unsigned long long)));
   if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMemset(c.d_status, 0, sizeof(unsigned)));
   if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMemset(c.t.bbox_ticket, 0, sizeof(unsigned)));
@@ -160,6 +161,7 @@ int gravity_destroy(gravity_ctx *h) {
   grav::free_ptr(c.t.scalars);
   grav::free_ptr(c.walk_stats);
   grav::free_ptr(c.walk_gstack);
+  grav::free_ptr(c.walk_queues);
   grav::free_ptr(c.d_status);
   grav::free_ptr(c.dir_hi); grav::free_ptr(c.dir_lo);
   grav::free_ptr(c.h2d_pos); grav::free_ptr(c.h2d_mass); grav::free_ptr(c.h2d_acc);

@@ -70,6 +70,7 @@ struct Ctx {
   int64_t launches = 0;        // kernels enqueued by this context (introspection)
   unsigned long long *walk_stats = nullptr;   // 16 counters filled by the counted walk
   void *walk_gstack = nullptr;                // walk stack overflow, per persistent warp
+  unsigned *walk_queues = nullptr;            // walk task-queue counters, one per SM
   size_t walk_gstack_cap = 0;                 // in 8-byte entries
   Tree t;
   // direct-sum staging (caller order hi/lo)

@@ -34,11 +34,11 @@ namespace grav {
 namespace {
 
 constexpr int kWalkWarps = 4;
-constexpr int kSmemStack = 224;                // stack entries in shared memory
-constexpr int kGlobStack = 1024;               // further entries in global memory, per warp
+constexpr int kSmemStack = 128;                // stack entries in shared memory
+constexpr int kGlobStack = 1152;               // further entries in global memory, per warp
 constexpr int kStackCap = kSmemStack + kGlobStack;
-constexpr int kListCap = 64;
-constexpr int kFlushAt = 32;
+constexpr int kFlushAt = 16;                   // evaluate a list once it holds this many terms
+constexpr int kListCap = kFlushAt + 32;        // a batch appends at most 32 terms per list
 constexpr uint32_t kKindBody = 0x80000000u;
 constexpr uint32_t kFirstMask = 0x01FFFFFFu;   // 25-bit first index
 constexpr int kCntShift = 25;                  // 6-bit (count - 1)
@@ -91,7 +91,8 @@ struct WalkArgs {
   double kick;
   unsigned *status;
   int max_iter;
-  unsigned *task_counter;
+  unsigned *task_counter;         // [nqueues] per-queue counters, zeroed before the launch
+  int nqueues;
   uint2 *gstack;                  // [persistent warps][kGlobStack] (first|cnt|kind, mask)
   unsigned long long *stats;      // counted variant only
 };
@@ -290,11 +291,28 @@ k_walk(WalkArgs A) {
   const float eps2 = A.eps2;
   const bool acc64 = A.acc64 != 0;
 
+  // Tasks (32 consecutive bodies) are split into one contiguous queue per SM, so
+  // that the warps resident on an SM walk neighbouring bodies and share node
+  // records in L1; a warp whose queue is empty takes tasks from the next queues.
+  unsigned smid;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+  const int nq = A.nqueues;
+  int q = (int)(smid % (unsigned)nq);
+  int visited = 0;
   for (;;) {
-    int task = 0;
-    if (lane == 0) task = (int)atomicAdd(A.task_counter, 1u);
+    int task = -1;
+    if (lane == 0) {
+      while (visited < nq) {
+        const int qbeg = (int)(((long long)A.ntasks * q) / nq);
+        const int qend = (int)(((long long)A.ntasks * (q + 1)) / nq);
+        const int t = qbeg + (int)atomicAdd(&A.task_counter[q], 1u);
+        if (t < qend) { task = t; break; }
+        q = (q + 1 == nq) ? 0 : q + 1;
+        ++visited;
+      }
+    }
     task = __shfl_sync(0xffffffffu, task, 0);
-    if (task >= A.ntasks) break;
+    if (task < 0) break;
 
     const int wbeg = task * 32;
     const int wend = min(n, wbeg + 32);
@@ -670,6 +688,16 @@ int launch_walk(Ctx *c, WalkArgs A) {
   const int dev = c->device < 64 ? c->device : 63;
   if (blocks_per_sm[dev] == 0) {
     GRAV_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    cudaFuncAttributes fa{};
+    GRAV_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+    int regs_blocks = 65536 / (fa.numRegs * 32 * kWalkWarps);
+    if (regs_blocks < 1) regs_blocks = 1;
+    int smem_sm = 0;
+    GRAV_CUDA_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, c->device));
+    const double need = (double)regs_blocks * (smem + 1024);
+    int pct = (int)(100.0 * need / smem_sm) + 1;
+    if (pct > 100) pct = 100;
+    GRAV_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
     int b = 0;
     GRAV_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, 32 * kWalkWarps, smem));
     blocks_per_sm[dev] = b > 0 ? b : 1;
@@ -687,7 +715,8 @@ int launch_walk(Ctx *c, WalkArgs A) {
     c->walk_gstack_cap = gneed;
   }
   A.gstack = reinterpret_cast<uint2 *>(c->walk_gstack);
-  GRAV_CUDA_TRY(cudaMemsetAsync(A.task_counter, 0, sizeof(unsigned), c->stream));
+  A.nqueues = c->num_sms;
+  GRAV_CUDA_TRY(cudaMemsetAsync(A.task_counter, 0, sizeof(unsigned) * A.nqueues, c->stream));
   kern<<<blocks, 32 * kWalkWarps, smem, c->stream>>>(A);
   ++c->launches;
   return cuda_status(cudaGetLastError());
@@ -714,7 +743,7 @@ int walk_forces(Ctx *c, double theta, double eps, double *acc, int32_t *counts, 
   A.acc = acc; A.counts = counts; A.vel = vel; A.kick = kick;
   A.status = c->d_status;
   A.max_iter = (int)(8 * c->n + 64);
-  A.task_counter = t.scalars + 120;
+  A.task_counter = c->walk_queues;
   A.stats = c->walk_stats;
   if (counts) {
     GRAV_CUDA_TRY(cudaMemsetAsync(c->walk_stats, 0, sizeof(unsigned long long) * 16, c->stream));
