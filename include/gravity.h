@@ -61,11 +61,14 @@ typedef struct gravity_params {
                           1 = semi-implicit (symplectic) Euler (Sec. 2.3) */
   int32_t walk_cfg;    /* -1 = default launch shape of the walk; >= 0 = index into the
                           table of walk launch shapes (autotuner use) */
-  int32_t reserved[2];
+  int32_t use_graph;   /* leapfrog_step with nsteps > 2 on a non-default stream: 1 (default)
+                          = capture one step as a CUDA graph and replay it, 0 = launch
+                          every kernel of every step */
+  int32_t reserved;
 } gravity_params;
 
 /* Fill *p with the defaults: G = 1, order 0, leaf_max 1, accum 0, mac_guard 1,
- * scheme 0, walk_cfg -1. */
+ * scheme 0, walk_cfg -1, use_graph 1. */
 void gravity_params_default(gravity_params *p);
 
 /* Create a context on CUDA device `device` whose work goes to `cuda_stream`
@@ -104,6 +107,21 @@ int gravity_forces(gravity_ctx *ctx, double theta, double eps, double *acc);
  * Slower; meant for tests and for counting the walk's algorithmic work. */
 int gravity_forces_counted(gravity_ctx *ctx, double theta, double eps, double *acc,
                            int32_t *counts);
+
+/* Independent clouds ("batched ensemble"): many separate N-body problems handled
+ * by one tree build and one walk launch.  offsets_host (host memory, nclouds + 1
+ * int64) gives cloud k as bodies [offsets[k], offsets[k+1]) of the arrays passed
+ * to later calls (offsets[0] = 0, strictly increasing; at most 65536 clouds).
+ * Each cloud gets its own root cube and octree, exactly as if it were built alone,
+ * and bodies feel only the bodies of their own cloud.  The segmentation stays in
+ * effect for gravity_tree_build / gravity_forces / leapfrog_step (whose n must then
+ * equal offsets[nclouds]) until changed; nclouds <= 1 returns to a single cloud.
+ * Synchronises the context's stream. */
+int gravity_set_clouds(gravity_ctx *ctx, int32_t nclouds, const int64_t *offsets_host);
+
+/* gravity_set_clouds followed by gravity_tree_build of all clouds. */
+int gravity_batch_tree_build(gravity_ctx *ctx, int32_t nclouds, const int64_t *offsets_host,
+                             const double *pos, const double *mass, const gravity_params *p);
 
 /* Eq. (Newton) with the softening of Eq. (Force_rComp), all N(N-1) pairs:
  * acc_i = G sum_{j != i} m_j (R_j - R_i) / (|R_j - R_i|^2 + eps^2)^{3/2}.
@@ -157,12 +175,13 @@ int gravity_forces_host(gravity_ctx *ctx, int64_t n, const double *pos_host,
 int gravity_sync(gravity_ctx *ctx);
 
 /* Tree introspection for tests.  Synchronises.  Copies into host memory:
- *   GRAVITY_DBG_ROOT      4 doubles: lo[3], side
+ *   GRAVITY_DBG_ROOT      4 doubles per cloud: lo[3], side
  *   GRAVITY_DBG_KEYS      n uint64: Morton keys in sorted order
  *   GRAVITY_DBG_PERM      n int32: caller index of each sorted body
  *   GRAVITY_DBG_NNODES    1 int32: node count
  *   GRAVITY_DBG_TOPO      nnodes x 4 int32: first child (-1 = leaf), child count,
- *                         body begin, body end (sorted order, end exclusive)
+ *                         body begin, body end (sorted order, end exclusive); node k
+ *                         (k < number of clouds) is the root of cloud k
  *   GRAVITY_DBG_DEPTH     nnodes int32
  *   GRAVITY_DBG_PARENT    nnodes int32 (-1 for the root)
  *   GRAVITY_DBG_MASS      nnodes double

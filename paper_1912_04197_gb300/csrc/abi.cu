@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -56,6 +57,7 @@ int check_params(const gravity_params *p) {
   if (p->accum != 0 && p->accum != 1) return GRAVITY_E_ARG;
   if (p->mac_guard != 0 && p->mac_guard != 1) return GRAVITY_E_ARG;
   if (p->scheme != 0 && p->scheme != 1) return GRAVITY_E_ARG;
+  if (p->use_graph != 0 && p->use_graph != 1) return GRAVITY_E_ARG;
   return GRAVITY_OK;
 }
 
@@ -100,6 +102,61 @@ int ensure_capacity(Ctx *c, int64_t n) {
   return GRAVITY_OK;
 }
 
+namespace {
+void free_segments(Segs &sg) {
+  free_ptr(sg.off); free_ptr(sg.seg_of); free_ptr(sg.seg_sorted);
+  free_ptr(sg.task_begin); free_ptr(sg.task_end); free_ptr(sg.task_seg);
+  sg = Segs{};
+}
+}  // namespace
+
+// Clouds given by host offsets off[0..nseg] (off[0] = 0, strictly increasing).
+// nseg <= 1 returns to a single cloud.  Builds the per-body cloud ids, the walk
+// task list (32 consecutive bodies of one cloud per task) and the geometry array.
+int set_segments(Ctx *c, int nseg, const int64_t *off) {
+  GRAV_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  free_segments(c->seg);
+  if (nseg <= 1) return GRAVITY_OK;
+  if (!off || off[0] != 0 || nseg > 65536) return GRAVITY_E_ARG;
+  for (int k = 0; k < nseg; ++k)
+    if (off[k + 1] <= off[k]) return GRAVITY_E_ARG;
+  const int64_t n = off[nseg];
+  if (n > kMaxBodies) return GRAVITY_E_ARG;
+  Segs sg;
+  sg.nseg = nseg;
+  sg.cbits = 0;
+  while ((1 << sg.cbits) < nseg) ++sg.cbits;
+  sg.n = n;
+  std::vector<int32_t> tb, te, ts;
+  for (int k = 0; k < nseg; ++k)
+    for (int64_t b = off[k]; b < off[k + 1]; b += 32) {
+      tb.push_back((int32_t)b);
+      te.push_back((int32_t)off[k + 1]);
+      ts.push_back(k);
+    }
+  sg.ntasks = (int)tb.size();
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = alloc(sg.off, nseg + 1);
+  if (e == cudaSuccess) e = alloc(sg.seg_of, n);
+  if (e == cudaSuccess) e = alloc(sg.seg_sorted, n);
+  if (e == cudaSuccess) e = alloc(sg.task_begin, sg.ntasks);
+  if (e == cudaSuccess) e = alloc(sg.task_end, sg.ntasks);
+  if (e == cudaSuccess) e = alloc(sg.task_seg, sg.ntasks);
+  if (e == cudaSuccess) e = cudaMemcpy(sg.off, off, sizeof(int64_t) * (nseg + 1), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(sg.task_begin, tb.data(), sizeof(int32_t) * sg.ntasks, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(sg.task_end, te.data(), sizeof(int32_t) * sg.ntasks, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(sg.task_seg, ts.data(), sizeof(int32_t) * sg.ntasks, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && c->t.geom_cap < nseg) {
+    free_ptr(c->t.geom);
+    c->t.geom_cap = 0;
+    e = alloc(c->t.geom, 8 * (int64_t)nseg);
+    if (e == cudaSuccess) c->t.geom_cap = nseg;
+  }
+  c->seg = sg;
+  if (e != cudaSuccess) { free_segments(c->seg); return cuda_status(e); }
+  return fill_segment_ids(c);
+}
+
 }  // namespace grav
 
 using grav::Ctx;
@@ -116,6 +173,7 @@ void gravity_params_default(gravity_params *p) {
   p->mac_guard = 1;
   p->scheme = 0;
   p->walk_cfg = -1;
+  p->use_graph = 1;
 }
 
 int gravity_create(gravity_ctx **out, int device, void *cuda_stream) {
@@ -134,6 +192,7 @@ int gravity_create(gravity_ctx **out, int device, void *cuda_stream) {
   if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, device));
   if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMalloc(&c.d_status, sizeof(unsigned)));
   if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMalloc(&c.t.geom, 8 * sizeof(double)));
+  if (rc == GRAVITY_OK) c.t.geom_cap = 1;
   if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMalloc(&c.t.bbox_ticket, sizeof(unsigned)));
   if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMalloc(&c.t.nnodes, sizeof(int32_t)));
   if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMalloc(&c.t.scalars, 128 * sizeof(uint32_t)));
@@ -157,11 +216,13 @@ int gravity_destroy(gravity_ctx *h) {
   cudaSetDevice(c.device);
   cudaStreamSynchronize(c.stream);
   grav::free_tree(c.t);
+  grav::free_segments(c.seg);
   grav::free_ptr(c.t.geom); grav::free_ptr(c.t.bbox_ticket); grav::free_ptr(c.t.nnodes);
   grav::free_ptr(c.t.scalars);
   grav::free_ptr(c.walk_stats);
   grav::free_ptr(c.walk_gstack);
   grav::free_ptr(c.walk_queues);
+  if (c.graph.exec) cudaGraphExecDestroy(c.graph.exec);
   grav::free_ptr(c.d_status);
   grav::free_ptr(c.dir_hi); grav::free_ptr(c.dir_lo);
   grav::free_ptr(c.h2d_pos); grav::free_ptr(c.h2d_mass); grav::free_ptr(c.h2d_acc);
@@ -183,6 +244,7 @@ int gravity_tree_build(gravity_ctx *h, int64_t n, const double *pos, const doubl
   int rc = grav::check_params(p);
   if (rc) return rc;
   Ctx &c = h->c;
+  if (c.seg.nseg > 1 && n != c.seg.n) return GRAVITY_E_ARG;
   if (p) c.params = *p; else gravity_params_default(&c.params);
   c.have_tree = false;
   c.n = n;
@@ -238,21 +300,84 @@ int leapfrog_step(gravity_ctx *h, int64_t n, double *pos, double *vel, const dou
   if (n == 0 || nsteps == 0) return GRAVITY_OK;
   if (!pos || !vel || !mass || !acc_cache) return GRAVITY_E_ARG;
   Ctx &c = h->c;
+  if (c.seg.nseg > 1 && n != c.seg.n) return GRAVITY_E_ARG;
   if (p) c.params = *p; else gravity_params_default(&c.params);
   if ((rc = grav::set_device(c))) return rc;
   if ((rc = grav::ensure_capacity(&c, n))) return rc;
   const bool kdk = c.params.scheme == 0;
   const double h_kick = kdk ? 0.5 * dt : dt;
-  for (int s = 0; s < nsteps; ++s) {
-    if ((rc = grav::launch_kick_drift(&c, n, pos, vel, acc_cache, h_kick, dt))) return rc;
+  auto one_step = [&]() -> int {
+    int r = grav::launch_kick_drift(&c, n, pos, vel, acc_cache, h_kick, dt);
+    if (r) return r;
     c.n = n;
-    if ((rc = grav::tree_build(&c, n, pos, mass))) return rc;
+    if ((r = grav::tree_build(&c, n, pos, mass))) return r;
     c.have_tree = true;
-    if ((rc = grav::walk_forces(&c, theta, eps, acc_cache, nullptr, kdk ? vel : nullptr,
-                                kdk ? h_kick : 0.0)))
+    return grav::walk_forces(&c, theta, eps, acc_cache, nullptr, kdk ? vel : nullptr,
+                             kdk ? h_kick : 0.0);
+  };
+  // The first step runs eagerly (it sizes every buffer); later steps replay a
+  // CUDA graph of one step captured on the caller's stream when graphs are enabled.
+  grav::StepGraph &g = c.graph;
+  const bool same = g.exec && g.stream == c.stream && g.n == n && g.pos == pos && g.vel == vel &&
+                    g.mass == mass && g.acc == acc_cache && g.dt == dt && g.theta == theta &&
+                    g.eps == eps && g.nseg == c.seg.nseg &&
+                    std::memcmp(&g.params, &c.params, sizeof(gravity_params)) == 0;
+  int s0 = 0;
+  if (!same) {
+    if ((rc = one_step())) return rc;
+    s0 = 1;
+    if (g.exec) { cudaGraphExecDestroy(g.exec); g.exec = nullptr; }
+    if (c.params.use_graph && c.stream != nullptr && nsteps > 2) {
+      cudaGraph_t graph = nullptr;
+      const int64_t k0 = c.launches;
+      if (cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        int rs = one_step();
+        cudaError_t ec = cudaStreamEndCapture(c.stream, &graph);
+        if (rs == GRAVITY_OK && ec == cudaSuccess && graph &&
+            cudaGraphInstantiate(&g.exec, graph, 0) == cudaSuccess) {
+          g.stream = c.stream; g.n = n; g.pos = pos; g.vel = vel; g.mass = mass;
+          g.acc = acc_cache; g.dt = dt; g.theta = theta; g.eps = eps; g.params = c.params;
+          g.nseg = c.seg.nseg; g.kernels = c.launches - k0;
+        } else {
+          g.exec = nullptr;
+        }
+        if (graph) cudaGraphDestroy(graph);
+        c.launches = k0;
+      }
+      cudaGetLastError();
+    }
+  }
+  for (int s = s0; s < nsteps; ++s) {
+    if (g.exec) {
+      GRAV_CUDA_TRY(cudaGraphLaunch(g.exec, c.stream));
+      c.launches += g.kernels;
+    } else if ((rc = one_step())) {
       return rc;
+    }
   }
   return GRAVITY_OK;
+}
+
+int gravity_set_clouds(gravity_ctx *h, int32_t nclouds, const int64_t *offsets_host) {
+  if (!h || nclouds < 0) return GRAVITY_E_ARG;
+  if (nclouds > 1 && !offsets_host) return GRAVITY_E_ARG;
+  if (offsets_host && nclouds >= 1) {          // off[0] = 0, strictly increasing
+    if (offsets_host[0] != 0) return GRAVITY_E_ARG;
+    for (int32_t k = 0; k < nclouds; ++k)
+      if (offsets_host[k + 1] <= offsets_host[k]) return GRAVITY_E_ARG;
+  }
+  int rc = grav::set_device(h->c);
+  if (rc) return rc;
+  h->c.have_tree = false;
+  return grav::set_segments(&h->c, nclouds, offsets_host);
+}
+
+int gravity_batch_tree_build(gravity_ctx *h, int32_t nclouds, const int64_t *offsets_host,
+                             const double *pos, const double *mass, const gravity_params *p) {
+  if (!h || nclouds < 1 || !offsets_host) return GRAVITY_E_ARG;
+  int rc = gravity_set_clouds(h, nclouds, offsets_host);
+  if (rc) return rc;
+  return gravity_tree_build(h, offsets_host[nclouds], pos, mass, p);
 }
 
 int gravity_sync(gravity_ctx *h) {
@@ -321,7 +446,13 @@ int gravity_debug_export(gravity_ctx *h, int what, void *dst, size_t bytes) {
   const void *src = nullptr;
   size_t need = 0;
   switch (what) {
-    case GRAVITY_DBG_ROOT: src = t.geom; need = 4 * sizeof(double); break;
+    case GRAVITY_DBG_ROOT: {
+      const int k = c.seg.nseg;
+      if (bytes < 4 * sizeof(double) * k) return GRAVITY_E_ARG;
+      GRAV_CUDA_TRY(cudaMemcpy2D(dst, 4 * sizeof(double), t.geom, 8 * sizeof(double),
+                                 4 * sizeof(double), k, cudaMemcpyDeviceToHost));
+      return GRAVITY_OK;
+    }
     case GRAVITY_DBG_KEYS: src = t.keys; need = sizeof(uint64_t) * c.n; break;
     case GRAVITY_DBG_PERM: src = t.idx; need = sizeof(uint32_t) * c.n; break;
     case GRAVITY_DBG_NNODES:

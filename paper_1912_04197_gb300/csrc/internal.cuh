@@ -20,8 +20,9 @@ enum : unsigned {
 };
 
 struct Tree {
-  // geometry: lo[3], side, scale = 2^21 / side
+  // geometry per cloud, 8 doubles each: lo[3], side, scale = 2^21 / side
   double *geom = nullptr;
+  int geom_cap = 0;              // clouds the geometry array holds
   // keys / sort
   uint64_t *keys = nullptr, *keys_alt = nullptr;
   uint32_t *idx = nullptr, *idx_alt = nullptr;   // after the sort: idx = perm (sorted -> caller)
@@ -58,6 +59,34 @@ struct Tree {
   float4 *nquadf = nullptr;                     // 2 per node: (xx,yy,zz,xy), (xz,yz,0,0)
 };
 
+// Independent clouds (segments) handled in one build and one walk launch: bodies
+// are given concatenated cloud by cloud; cloud k occupies [off[k], off[k+1]).
+struct Segs {
+  int nseg = 1;                  // number of clouds
+  int cbits = 0;                 // bits of the cloud id in the extended key (0 for one cloud)
+  int64_t *off = nullptr;        // device copy of the offsets (nseg + 1)
+  int32_t *seg_of = nullptr;     // cloud id of each body, caller order (nseg > 1)
+  int32_t *seg_sorted = nullptr; // cloud id of each body, sorted order (nseg > 1)
+  int32_t *task_begin = nullptr; // walk tasks: first body (sorted order), cloud end, cloud id
+  int32_t *task_end = nullptr;
+  int32_t *task_seg = nullptr;
+  int ntasks = 0;
+  int64_t n = 0;                 // total bodies the segmentation describes
+  int64_t body_cap = 0;
+};
+
+// Captured leapfrog step (a CUDA graph) and the arguments it was captured with.
+struct StepGraph {
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t stream = nullptr;
+  int64_t n = 0;
+  const void *pos = nullptr, *vel = nullptr, *mass = nullptr, *acc = nullptr;
+  double dt = 0, theta = 0, eps = 0;
+  gravity_params params{};
+  int nseg = 0;
+  int64_t kernels = 0;         // kernels in one replay
+};
+
 struct Ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -67,6 +96,8 @@ struct Ctx {
   bool have_tree = false;
   gravity_params params{};
   unsigned *d_status = nullptr;
+  Segs seg;                    // cloud segmentation (one cloud unless set)
+  StepGraph graph;             // cached captured leapfrog step
   int64_t launches = 0;        // kernels enqueued by this context (introspection)
   unsigned long long *walk_stats = nullptr;   // 16 counters filled by the counted walk
   void *walk_gstack = nullptr;                // walk stack overflow, per persistent warp
@@ -98,6 +129,8 @@ int launch_kick(Ctx *c, int64_t n, double *vel, const double *acc, double h_kick
 int probe_fp32(Ctx *c, int64_t iters, double *ms, double *flops);
 
 int ensure_capacity(Ctx *c, int64_t n);
+int set_segments(Ctx *c, int nseg, const int64_t *off_host);
+int fill_segment_ids(Ctx *c);
 int cuda_status(cudaError_t e);
 
 // ---- device helpers

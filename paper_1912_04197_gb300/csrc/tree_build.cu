@@ -121,6 +121,38 @@ k_bbox(const double *__restrict__ pos, int64_t n, unsigned long long *__restrict
   *ticket = 0;                            // ready for the next build
 }
 
+// Root cube of every cloud (several clouds): one block per cloud.
+__global__ void __launch_bounds__(kBBoxThreads)
+k_bbox_seg(const double *__restrict__ pos, const int64_t *__restrict__ off,
+           double *__restrict__ geom, unsigned *status) {
+  const int k = blockIdx.x;
+  const int64_t b = off[k], e = off[k + 1];
+  unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
+  bool bad = false;
+  const unsigned long long *p64 = reinterpret_cast<const unsigned long long *>(pos);
+  for (int64_t i = 3 * b + threadIdx.x; i < 3 * e; i += blockDim.x) {
+    const unsigned long long v = p64[i];
+    bad |= ((v >> 52) & 0x7FFull) == 0x7FFull;
+    const unsigned long long key = (v >> 63) ? ~v : (v | 0x8000000000000000ull);
+    const int a = (int)((i - 3 * b) % 3);
+    lo[a] = umin64(lo[a], key);
+    hi[a] = umax64(hi[a], key);
+  }
+  bad = __syncthreads_or(bad);
+  block_minmax(lo, hi);
+  if (threadIdx.x != 0) return;
+  if (bad) latch_error(status, kErrNonFinite);
+  double glo[3], ghi[3];
+  for (int a = 0; a < 3; ++a) { glo[a] = of_ord(lo[a]); ghi[a] = of_ord(hi[a]); }
+  double side = 0.0;
+  for (int a = 0; a < 3; ++a) side = fmax(side, __dsub_rn(ghi[a], glo[a]));
+  if (e - b <= 1 || !(side > 0.0) || !isfinite(side)) side = 1.0;
+  double *g = geom + 8 * k;
+  for (int a = 0; a < 3; ++a) g[a] = isfinite(glo[a]) ? glo[a] : 0.0;
+  g[3] = side;
+  g[4] = __ddiv_rn(2097152.0, side);
+}
+
 // ------------------------------------------------------------------ a2: Morton keys
 __device__ __forceinline__ uint64_t spread3(uint32_t v) {
   uint64_t x = v & 0x1FFFFFu;
@@ -139,10 +171,12 @@ __device__ __forceinline__ uint32_t grid_coord(double x, double lo, double scale
   return (uint32_t)min(max(q, 0), 2097151);
 }
 
-__global__ void k_keys(const double *__restrict__ pos, int64_t n, const double *__restrict__ geom,
-                       uint64_t *__restrict__ keys, uint32_t *__restrict__ idx) {
+__global__ void k_keys(const double *__restrict__ pos, int64_t n, const double *__restrict__ geom0,
+                       const int32_t *__restrict__ seg_of, uint64_t *__restrict__ keys,
+                       uint32_t *__restrict__ idx) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const double *geom = seg_of ? geom0 + 8 * (int64_t)seg_of[i] : geom0;   // the body's cloud
   const double scale = geom[4];
   uint32_t qx = grid_coord(pos[3 * i + 0], geom[0], scale);
   uint32_t qy = grid_coord(pos[3 * i + 1], geom[1], scale);
@@ -236,8 +270,17 @@ int exclusive_scan(Ctx *c, uint32_t *data, int64_t n, uint32_t *total_out) {
 // Stable LSD radix sort of (key, index) pairs, 8 passes of 8-bit digits.
 // Pass = per-tile digit histogram -> exclusive scan in digit-major order ->
 // stable scatter (ranks from warp match + per-warp counts, in index order).
+// Digit of element i in a radix pass: 8 bits of the Morton key, or, for the passes
+// that order clouds, 8 bits of the cloud id of the element's caller index.
+__device__ __forceinline__ unsigned rs_digit(uint64_t key, uint32_t val, int shift,
+                                             const int32_t *__restrict__ seg_of) {
+  if (seg_of) return ((unsigned)seg_of[val] >> shift) & 255u;
+  return (unsigned)(key >> shift) & 255u;
+}
+
 __global__ void __launch_bounds__(kRsThreads)
-k_rs_hist(const uint64_t *__restrict__ keys, int64_t n, int shift, uint32_t *__restrict__ hist,
+k_rs_hist(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals, int64_t n,
+          int shift, const int32_t *__restrict__ seg_of, uint32_t *__restrict__ hist,
           int ntiles) {
   __shared__ uint32_t cnt[256];
   cnt[threadIdx.x] = 0;
@@ -245,7 +288,7 @@ k_rs_hist(const uint64_t *__restrict__ keys, int64_t n, int shift, uint32_t *__r
   int64_t base = blockIdx.x * (int64_t)kRsTile;
   for (int k = 0; k < kRsItems; ++k) {
     int64_t i = base + k * kRsThreads + threadIdx.x;
-    if (i < n) atomicAdd(&cnt[(unsigned)(keys[i] >> shift) & 255u], 1u);
+    if (i < n) atomicAdd(&cnt[rs_digit(keys[i], seg_of ? vals[i] : 0u, shift, seg_of)], 1u);
   }
   __syncthreads();
   hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
@@ -254,7 +297,7 @@ k_rs_hist(const uint64_t *__restrict__ keys, int64_t n, int shift, uint32_t *__r
 __global__ void __launch_bounds__(kRsThreads)
 k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
              uint64_t *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n, int shift,
-             const uint32_t *__restrict__ offs, int ntiles) {
+             const int32_t *__restrict__ seg_of, const uint32_t *__restrict__ offs, int ntiles) {
   constexpr int W = kRsThreads / 32;
   __shared__ uint32_t s_base[256];
   __shared__ uint32_t s_w[W][256];
@@ -269,7 +312,7 @@ k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
     bool valid = i < n;
     uint64_t key = valid ? kin[i] : 0ull;
     uint32_t val = valid ? vin[i] : 0u;
-    unsigned d = valid ? ((unsigned)(key >> shift) & 255u) : 256u;
+    unsigned d = valid ? rs_digit(key, val, shift, seg_of) : 256u;
     unsigned peers = __match_any_sync(0xffffffffu, d);
     unsigned rank = __popc(peers & lt);
     if (valid && rank == 0) s_w[w][d] = __popc(peers);
@@ -293,23 +336,31 @@ k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
   }
 }
 
+// 8 passes over the 63-bit keys, then (several clouds) stable passes over the cloud
+// ids, so the order is by cloud, then key, then caller index.
 int radix_sort(Ctx *c, int64_t n) {
   Tree &t = c->t;
   int ntiles = (int)((n + kRsTile - 1) / kRsTile);
   uint64_t *ka = t.keys, *kb = t.keys_alt;
   uint32_t *va = t.idx, *vb = t.idx_alt;
-  for (int pass = 0; pass < 8; ++pass) {
-    int shift = 8 * pass;
-    k_rs_hist<<<ntiles, kRsThreads, 0, c->stream>>>(ka, n, shift, t.hist, ntiles);
+  const int cloud_passes = c->seg.nseg > 1 ? (c->seg.cbits + 7) / 8 : 0;
+  for (int pass = 0; pass < 8 + cloud_passes; ++pass) {
+    const bool cl = pass >= 8;
+    const int shift = cl ? 8 * (pass - 8) : 8 * pass;
+    const int32_t *so = cl ? c->seg.seg_of : nullptr;
+    k_rs_hist<<<ntiles, kRsThreads, 0, c->stream>>>(ka, va, n, shift, so, t.hist, ntiles);
     ++c->launches;
     int rc = exclusive_scan(c, t.hist, (int64_t)256 * ntiles, nullptr);
     if (rc) return rc;
-    k_rs_scatter<<<ntiles, kRsThreads, 0, c->stream>>>(ka, va, kb, vb, n, shift, t.hist, ntiles);
+    k_rs_scatter<<<ntiles, kRsThreads, 0, c->stream>>>(ka, va, kb, vb, n, shift, so, t.hist, ntiles);
     ++c->launches;
     uint64_t *tk = ka; ka = kb; kb = tk;
     uint32_t *tv = va; va = vb; vb = tv;
   }
-  // 8 passes: the sorted data is back in t.keys / t.idx
+  if ((8 + cloud_passes) % 2) {               // odd pass count: move the result back
+    GRAV_CUDA_TRY(cudaMemcpyAsync(t.keys, ka, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, c->stream));
+    GRAV_CUDA_TRY(cudaMemcpyAsync(t.idx, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, c->stream));
+  }
   return cuda_status(cudaGetLastError());
 }
 
@@ -317,10 +368,12 @@ int radix_sort(Ctx *c, int64_t n) {
 __global__ void k_gather(const double *__restrict__ pos, const double *__restrict__ mass,
                          const uint32_t *__restrict__ perm, int64_t n, double *__restrict__ pos_s,
                          double *__restrict__ mass_s, float4 *__restrict__ bhi,
-                         float4 *__restrict__ blo) {
+                         float4 *__restrict__ blo, const int32_t *__restrict__ seg_of,
+                         int32_t *__restrict__ seg_sorted) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   int64_t j = perm[i];
+  if (seg_of) seg_sorted[i] = seg_of[j];
   double x = pos[3 * j], y = pos[3 * j + 1], z = pos[3 * j + 2], m = mass[j];
   pos_s[3 * i] = x; pos_s[3 * i + 1] = y; pos_s[3 * i + 2] = z;
   mass_s[i] = m;
@@ -331,35 +384,48 @@ __global__ void k_gather(const double *__restrict__ pos, const double *__restric
 }
 
 // ------------------------------------------------------------------ a5: binary radix tree
-// Common prefix length (bits) of the extended keys (key, sorted index) at sorted
-// positions i and j; -1 outside [0, n).  Keys use 63 bits, so bit 63 is 0.
-__device__ __forceinline__ int delta(const uint64_t *__restrict__ k, int n, int i, int j) {
-  if (j < 0 || j >= n) return -1;
-  uint64_t a = k[i], b = k[j];
-  if (a != b) return __clzll((long long)(a ^ b)) - 1;
-  return 63 + __clz((int)((unsigned)i ^ (unsigned)j));
+// Extended key of sorted position i: (cloud id [cbits bits], 63-bit key, i).  delta
+// is the common prefix length in bits of two extended keys; -1 outside [0, n).
+// With one cloud cbits = 0 and the cloud part is absent.
+struct KeyView {
+  const uint64_t *k;
+  const int32_t *seg;          // cloud of each sorted body, or nullptr (one cloud)
+  int cbits;
+  int n;
+};
+
+__device__ __forceinline__ int delta(const KeyView &v, int i, int j) {
+  if (j < 0 || j >= v.n) return -1;
+  if (v.seg) {
+    const int si = v.seg[i], sj = v.seg[j];
+    if (si != sj) return __clz(si ^ sj) - (32 - v.cbits);
+  }
+  const uint64_t a = v.k[i], b = v.k[j];
+  if (a != b) return v.cbits + __clzll((long long)(a ^ b)) - 1;   // keys use 63 bits
+  return v.cbits + 63 + __clz((int)((unsigned)i ^ (unsigned)j));
 }
 
 // Karras' parallel construction: internal node i covers a key range with one end
 // at i; its direction, extent and split follow from prefix-length comparisons.
-__global__ void k_radix_tree(const uint64_t *__restrict__ k, int n, int32_t *__restrict__ child,
-                             int32_t *__restrict__ parent, int32_t *__restrict__ first,
-                             int32_t *__restrict__ last, int32_t *__restrict__ plen) {
+__global__ void k_radix_tree(KeyView v, int32_t *__restrict__ child, int32_t *__restrict__ parent,
+                             int32_t *__restrict__ first, int32_t *__restrict__ last,
+                             int32_t *__restrict__ plen) {
+  const int n = v.n;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n - 1) return;
-  int dir = (delta(k, n, i, i + 1) - delta(k, n, i, i - 1)) >= 0 ? 1 : -1;
-  int dmin = delta(k, n, i, i - dir);
+  int dir = (delta(v, i, i + 1) - delta(v, i, i - 1)) >= 0 ? 1 : -1;
+  int dmin = delta(v, i, i - dir);
   int lmax = 2;
-  while (delta(k, n, i, i + lmax * dir) > dmin) lmax <<= 1;
+  while (delta(v, i, i + lmax * dir) > dmin) lmax <<= 1;
   int len = 0;
   for (int t = lmax >> 1; t >= 1; t >>= 1)
-    if (delta(k, n, i, i + (len + t) * dir) > dmin) len += t;
+    if (delta(v, i, i + (len + t) * dir) > dmin) len += t;
   int j = i + len * dir;
-  int dnode = delta(k, n, i, j);
+  int dnode = delta(v, i, j);
   int s = 0;
   for (int div = 2;; div <<= 1) {
     int t = (len + div - 1) / div;
-    if (delta(k, n, i, i + (s + t) * dir) > dnode) s += t;
+    if (delta(v, i, i + (s + t) * dir) > dnode) s += t;
     if (t <= 1) break;
   }
   int gamma = i + s * dir + (dir < 0 ? -1 : 0);
@@ -377,12 +443,15 @@ __global__ void k_radix_tree(const uint64_t *__restrict__ k, int n, int32_t *__r
 }
 
 // ------------------------------------------------------------------ a6: octree
-// A binary node X is an octree cell when its capped depth floor(plen/3) exceeds
-// its binary parent's (or X is the root): the cell at that depth holds exactly X's
-// bodies, i.e. X is the deepest member of a chain of single-child cells.  A cell
-// is internal when it holds > leaf_max bodies and is above depth 21.  Its octree
-// children are the first binary descendants whose prefix reaches 3(depth+1) bits
-// (or bodies), found by a DFS of at most 7 binary nodes, in key = octant order.
+// A binary node X is an octree cell when its capped depth floor((plen - cbits)/3)
+// exceeds its binary parent's (or X is a cloud root): the cell at that depth holds
+// exactly X's bodies, i.e. X is the deepest member of a chain of single-child
+// cells.  A cell is internal when it holds > leaf_max bodies and is above depth 21.
+// Its octree children are the first binary descendants whose prefix reaches
+// cbits + 3(depth+1) bits (or bodies), found by a DFS of at most 7 binary nodes, in
+// key = octant order.  With several clouds, binary nodes whose prefix is shorter
+// than the cloud bits only connect clouds; their children just below are the cloud
+// roots, which take octree node ids 0 .. nclouds-1.
 struct Frontier {
   int32_t item[8];
   int count;
@@ -410,18 +479,25 @@ __device__ __forceinline__ bool frontier(const int32_t *__restrict__ child,
   return true;
 }
 
-__global__ void k_oct_count(int n, int leaf_max, const int32_t *__restrict__ child,
+__device__ __forceinline__ int cdepth(int plen, int cbits) {
+  return plen < cbits ? -1 : cap_depth(plen - cbits);
+}
+
+__global__ void k_oct_count(int n, int leaf_max, int cbits, const int32_t *__restrict__ child,
                             const int32_t *__restrict__ parent, const int32_t *__restrict__ first,
                             const int32_t *__restrict__ last, const int32_t *__restrict__ plen,
                             uint32_t *__restrict__ nchild, unsigned *status) {
   int X = blockIdx.x * blockDim.x + threadIdx.x;
   if (X >= n - 1) return;
-  int d = cap_depth(plen[X]);
-  bool cell = (X == 0) || cap_depth(plen[parent[X]]) < d;
-  int cnt = last[X] - first[X] + 1;
+  const int px = plen[X];
+  if (px < cbits) { nchild[X] = 0; return; }           // connector between clouds
+  const int d = cdepth(px, cbits);
+  const int P = parent[X];
+  const bool cell = P < 0 || plen[P] < cbits || cdepth(plen[P], cbits) < d;
+  const int cnt = last[X] - first[X] + 1;
   if (!(cell && cnt > leaf_max && d < kLevels)) { nchild[X] = 0; return; }
   Frontier f;
-  if (!frontier(child, plen, X, 3 * (d + 1), f) || f.count < 2) {
+  if (!frontier(child, plen, X, cbits + 3 * (d + 1), f) || f.count < 2) {
     latch_error(status, kErrTree);
     nchild[X] = 0;
     return;
@@ -429,62 +505,87 @@ __global__ void k_oct_count(int n, int leaf_max, const int32_t *__restrict__ chi
   nchild[X] = (uint32_t)f.count;
 }
 
-__global__ void k_oct_write(int n, int leaf_max, const int32_t *__restrict__ child,
-                            const int32_t *__restrict__ first, const int32_t *__restrict__ last,
-                            const int32_t *__restrict__ plen, const uint32_t *__restrict__ nchild,
-                            const uint32_t *__restrict__ base, const uint32_t *__restrict__ total,
-                            int4 *__restrict__ topo, int32_t *__restrict__ depth,
-                            int32_t *__restrict__ nnodes, int cap_nodes, unsigned *status) {
-  int X = blockIdx.x * blockDim.x + threadIdx.x;
-  if (X == 0) {
-    // the root (octree node 0)
-    int d0 = cap_depth(plen[0]);
-    if (nchild[0] > 0) {
-      topo[0] = make_int4(1 + (int)base[0], (int)nchild[0], 0, n);
-      depth[0] = d0;
-    } else {
-      topo[0] = make_int4(-1, 0, 0, n);
-      depth[0] = (n <= leaf_max) ? 0 : kLevels;
-    }
-    int nn = 1 + (int)*total;
-    if (nn > cap_nodes) { latch_error(status, kErrTree); nn = 1; }
-    *nnodes = nn;
+struct OctWriteArgs {
+  int n, leaf_max, cbits, nseg, cap_nodes;
+  const int32_t *child, *first, *last, *plen, *seg_sorted;
+  const uint32_t *nchild, *base, *total;
+  int4 *topo;
+  int32_t *depth, *nnodes;
+  unsigned *status;
+};
+
+// Record of a cloud root (binary internal node c, or body ~c) at octree id `id`.
+__device__ __forceinline__ void write_root(const OctWriteArgs &A, int c, int id) {
+  if (c < 0) {
+    const int b = ~c;
+    A.topo[id] = make_int4(-1, 0, b, b + 1);
+    A.depth[id] = 0;
+    return;
   }
-  if (X >= n - 1 || nchild[X] == 0) return;
-  int d = cap_depth(plen[X]);
+  const int b = A.first[c], e = A.last[c] + 1;
+  if (A.nchild[c] > 0) {
+    A.topo[id] = make_int4(A.nseg + (int)A.base[c], (int)A.nchild[c], b, e);
+    A.depth[id] = cdepth(A.plen[c], A.cbits);
+  } else {
+    A.topo[id] = make_int4(-1, 0, b, e);
+    A.depth[id] = (e - b <= A.leaf_max) ? 0 : kLevels;
+  }
+}
+
+__global__ void k_oct_write(OctWriteArgs A) {
+  const int X = blockIdx.x * blockDim.x + threadIdx.x;
+  if (X == 0) {
+    int nn = A.nseg + (int)*A.total;
+    if (nn > A.cap_nodes) { latch_error(A.status, kErrTree); nn = A.nseg; }
+    *A.nnodes = nn;
+    if (A.cbits == 0) write_root(A, 0, 0);                // one cloud: binary node 0 is the root
+  }
+  if (X >= A.n - 1) return;
+  if (A.plen[X] < A.cbits) {                              // connector: place the cloud roots below
+    for (int h = 0; h < 2; ++h) {
+      const int c = A.child[2 * X + h];
+      if (c < 0 || A.plen[c] >= A.cbits) {
+        const int b = c < 0 ? ~c : A.first[c];
+        write_root(A, c, A.seg_sorted[b]);
+      }
+    }
+    return;
+  }
+  if (A.nchild[X] == 0) return;
+  const int d = cdepth(A.plen[X], A.cbits);
   Frontier f;
-  frontier(child, plen, X, 3 * (d + 1), f);
-  int id0 = 1 + (int)base[X];
-  if (id0 + f.count > cap_nodes) { latch_error(status, kErrTree); return; }
+  frontier(A.child, A.plen, X, A.cbits + 3 * (d + 1), f);
+  const int id0 = A.nseg + (int)A.base[X];
+  if (id0 + f.count > A.cap_nodes) { latch_error(A.status, kErrTree); return; }
   for (int k = 0; k < f.count; ++k) {
-    int c = f.item[k], id = id0 + k;
+    const int c = f.item[k], id = id0 + k;
     if (c < 0) {
-      int b = ~c;
-      topo[id] = make_int4(-1, 0, b, b + 1);
-      depth[id] = d + 1;
+      const int b = ~c;
+      A.topo[id] = make_int4(-1, 0, b, b + 1);
+      A.depth[id] = d + 1;
     } else {
-      int b = first[c], e = last[c] + 1;
-      if (nchild[c] > 0) {
-        topo[id] = make_int4(1 + (int)base[c], (int)nchild[c], b, e);
-        depth[id] = cap_depth(plen[c]);
+      const int b = A.first[c], e = A.last[c] + 1;
+      if (A.nchild[c] > 0) {
+        A.topo[id] = make_int4(A.nseg + (int)A.base[c], (int)A.nchild[c], b, e);
+        A.depth[id] = cdepth(A.plen[c], A.cbits);
       } else {
-        topo[id] = make_int4(-1, 0, b, e);
-        depth[id] = (e - b <= leaf_max) ? d + 1 : kLevels;
+        A.topo[id] = make_int4(-1, 0, b, e);
+        A.depth[id] = (e - b <= A.leaf_max) ? d + 1 : kLevels;
       }
     }
   }
 }
 
-__global__ void k_oct_parent(int cap_nodes, const int4 *__restrict__ topo,
+__global__ void k_oct_parent(int cap_nodes, int nseg, const int4 *__restrict__ topo,
                              const int32_t *__restrict__ nnodes, int32_t *__restrict__ nparent,
                              unsigned *status) {
   int id = blockIdx.x * blockDim.x + threadIdx.x;
   int nn = *nnodes;
   if (id >= nn || id >= cap_nodes) return;
-  if (id == 0) nparent[0] = -1;
+  if (id < nseg) nparent[id] = -1;                        // cloud roots
   int4 t = topo[id];
   if (t.x < 0) return;
-  if (t.x <= 0 || t.x + t.y > nn) { latch_error(status, kErrTree); return; }
+  if (t.x < nseg || t.x + t.y > nn) { latch_error(status, kErrTree); return; }
   for (int k = 0; k < t.y; ++k) nparent[t.x + k] = id;
 }
 
@@ -514,6 +615,7 @@ struct MomArgs {
   const double *pos_s;
   const double *mass_s;
   const double *geom;
+  const int32_t *seg_sorted;   // cloud of each sorted body, or nullptr (one cloud)
   double *nmass;
   double *ncom;
   double *nsec;                // second moments T (xx, yy, zz, xy, xz, yz)
@@ -583,7 +685,9 @@ __device__ void write_records(const MomArgs &A, int id, double m, const double *
                               const double *T, bool single_body) {
   float h[3], lo[3];
   for (int a = 0; a < 3; ++a) split_df(com[a], h[a], lo[a]);
-  double l = ldexp(A.geom[3], -A.ndepth[id]);
+  const int4 t = A.topo[id];
+  const double side = A.geom[8 * (A.seg_sorted ? A.seg_sorted[t.z] : 0) + 3];
+  double l = ldexp(side, -A.ndepth[id]);
   float l2 = single_body ? -1.0f : __double2float_rn(dm(l, l));
   A.rec0[id] = make_float4(h[0], h[1], h[2], __double2float_rn(m));
   A.rec1[id] = make_float4(lo[0], lo[1], lo[2], l2);
@@ -677,6 +781,12 @@ __global__ void k_level_moments(MomArgs A, int bucket) {
   }
 }
 
+// Cloud id of every body (caller order), one block per cloud.
+__global__ void k_fill_seg(const int64_t *__restrict__ off, int32_t *__restrict__ seg_of) {
+  const int k = blockIdx.x;
+  for (int64_t i = off[k] + threadIdx.x; i < off[k + 1]; i += blockDim.x) seg_of[i] = k;
+}
+
 // Root of a single body: node 0 is a leaf at depth 0.
 __global__ void k_single_root(int4 *topo, int32_t *depth, int32_t *nparent, int32_t *nnodes) {
   topo[0] = make_int4(-1, 0, 0, 1);
@@ -691,55 +801,71 @@ inline unsigned blocks_for(int64_t n, int threads) {
 
 }  // namespace
 
+int fill_segment_ids(Ctx *c) {
+  k_fill_seg<<<c->seg.nseg, 256, 0, c->stream>>>(c->seg.off, c->seg.seg_of);
+  ++c->launches;
+  return cuda_status(cudaGetLastError());
+}
+
 int tree_build(Ctx *c, int64_t n, const double *pos, const double *mass) {
   Tree &t = c->t;
+  Segs &sg = c->seg;
   cudaStream_t s = c->stream;
   const int leaf_max = c->params.leaf_max;
-  // a1: root cube (also validates the coordinates)
-  int64_t nb64 = (3 * n + 4 * kBBoxThreads - 1) / (4 * kBBoxThreads);
-  if (nb64 > 4 * (int64_t)c->num_sms) nb64 = 4 * (int64_t)c->num_sms;
-  nb64 = (nb64 + 2) / 3 * 3;                 // stride multiple of 3 (see k_bbox)
-  int nb = (int)nb64;
-  if (nb < 1) nb = 1;
-  k_bbox<<<nb, kBBoxThreads, 0, s>>>(pos, n, reinterpret_cast<unsigned long long *>(t.bbox_part),
-                                     t.bbox_ticket, t.geom, c->d_status);
+  const bool multi = sg.nseg > 1;
+  // a1: root cube of each cloud (also validates the coordinates)
+  if (!multi) {
+    int64_t nb64 = (3 * n + 4 * kBBoxThreads - 1) / (4 * kBBoxThreads);
+    if (nb64 > 4 * (int64_t)c->num_sms) nb64 = 4 * (int64_t)c->num_sms;
+    nb64 = (nb64 + 2) / 3 * 3;               // stride multiple of 3 (see k_bbox)
+    int nb = (int)nb64;
+    if (nb < 1) nb = 1;
+    k_bbox<<<nb, kBBoxThreads, 0, s>>>(pos, n, reinterpret_cast<unsigned long long *>(t.bbox_part),
+                                       t.bbox_ticket, t.geom, c->d_status);
+  } else {
+    k_bbox_seg<<<sg.nseg, kBBoxThreads, 0, s>>>(pos, sg.off, t.geom, c->d_status);
+  }
   ++c->launches;
   // a2: keys
-  k_keys<<<blocks_for(n, 256), 256, 0, s>>>(pos, n, t.geom, t.keys, t.idx);
+  k_keys<<<blocks_for(n, 256), 256, 0, s>>>(pos, n, t.geom, multi ? sg.seg_of : nullptr, t.keys,
+                                             t.idx);
   ++c->launches;
-  // a3: sort
+  // a3: sort (by cloud, then key, then caller index)
   int rc = radix_sort(c, n);
   if (rc) return rc;
   // a4: gather sorted bodies
   k_gather<<<blocks_for(n, 256), 256, 0, s>>>(pos, mass, t.idx, n, t.pos_s, t.mass_s, t.body_hi,
-                                               t.body_lo);
+                                               t.body_lo, multi ? sg.seg_of : nullptr,
+                                               sg.seg_sorted);
   ++c->launches;
   const int cap_nodes = (int)(2 * c->cap);
   if (n == 1) {
     k_single_root<<<1, 1, 0, s>>>(t.topo, t.ndepth, t.nparent, t.nnodes);
     ++c->launches;
   } else {
-    int ni = (int)(n - 1);
+    const int ni = (int)(n - 1);
+    const KeyView kv{t.keys, multi ? sg.seg_sorted : nullptr, multi ? sg.cbits : 0, (int)n};
     // a5: binary radix tree
-    k_radix_tree<<<blocks_for(ni, 256), 256, 0, s>>>(t.keys, (int)n, t.bchild, t.bparent, t.bfirst,
-                                                     t.blast, t.bplen);
+    k_radix_tree<<<blocks_for(ni, 256), 256, 0, s>>>(kv, t.bchild, t.bparent, t.bfirst, t.blast,
+                                                     t.bplen);
     ++c->launches;
     // a6: octree
-    k_oct_count<<<blocks_for(ni, 256), 256, 0, s>>>((int)n, leaf_max, t.bchild, t.bparent,
+    k_oct_count<<<blocks_for(ni, 256), 256, 0, s>>>((int)n, leaf_max, kv.cbits, t.bchild, t.bparent,
                                                     t.bfirst, t.blast, t.bplen, t.bnchild,
                                                     c->d_status);
     ++c->launches;
     uint32_t *base = t.bbase;
     GRAV_CUDA_TRY(cudaMemcpyAsync(base, t.bnchild, sizeof(uint32_t) * ni,
                                   cudaMemcpyDeviceToDevice, s));
-    uint32_t *total = t.scalars;             // number of non-root octree nodes
+    uint32_t *total = t.scalars;             // number of octree nodes below the cloud roots
     rc = exclusive_scan(c, base, ni, total);
     if (rc) return rc;
-    k_oct_write<<<blocks_for(ni, 256), 256, 0, s>>>((int)n, leaf_max, t.bchild, t.bfirst, t.blast,
-                                                    t.bplen, t.bnchild, base, total, t.topo,
-                                                    t.ndepth, t.nnodes, cap_nodes, c->d_status);
+    OctWriteArgs W{(int)n, leaf_max, kv.cbits, sg.nseg, cap_nodes, t.bchild, t.bfirst, t.blast,
+                   t.bplen, kv.seg, t.bnchild, base, total, t.topo, t.ndepth, t.nnodes,
+                   c->d_status};
+    k_oct_write<<<blocks_for(ni, 256), 256, 0, s>>>(W);
     ++c->launches;
-    k_oct_parent<<<blocks_for(cap_nodes, 256), 256, 0, s>>>(cap_nodes, t.topo, t.nnodes,
+    k_oct_parent<<<blocks_for(cap_nodes, 256), 256, 0, s>>>(cap_nodes, sg.nseg, t.topo, t.nnodes,
                                                             t.nparent, c->d_status);
     ++c->launches;
   }
@@ -752,8 +878,8 @@ int tree_build(Ctx *c, int64_t n, const double *pos, const double *mass) {
                                          t.nlist);
   ++c->launches;
   MomArgs A{t.topo, t.ndepth, t.nnodes, t.nlist, t.scalars + kSlotOff, t.pos_s, t.mass_s,
-            t.geom, t.nmass, t.ncom, t.nquad, t.nrec0, t.nrec1, t.nquadf, c->params.order,
-            cap_nodes, (int)n, c->d_status};
+            t.geom, multi ? sg.seg_sorted : nullptr, t.nmass, t.ncom, t.nquad, t.nrec0, t.nrec1,
+            t.nquadf, c->params.order, cap_nodes, (int)n, c->d_status};
   const unsigned grid = (unsigned)(4 * c->num_sms);
   k_leaf_moments<<<grid, 128, 0, s>>>(A);
   ++c->launches;

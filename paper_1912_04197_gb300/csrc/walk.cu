@@ -94,6 +94,9 @@ struct WalkArgs {
   unsigned *task_counter;         // [nqueues] per-queue counters, zeroed before the launch
   int nqueues;
   uint2 *gstack;                  // [persistent warps][kGlobStack] (first|cnt|kind, mask)
+  const int32_t *task_begin;      // several clouds: per task first body, cloud end, cloud id
+  const int32_t *task_end;
+  const int32_t *task_seg;
   unsigned long long *stats;      // counted variant only
 };
 
@@ -286,7 +289,6 @@ k_walk(WalkArgs A) {
 
   const int n = A.n;
   const int nn = *A.nnodes;
-  const double side = A.geom[3];
   const float theta2f = A.theta2f;
   const float eps2 = A.eps2;
   const bool acc64 = A.acc64 != 0;
@@ -314,10 +316,13 @@ k_walk(WalkArgs A) {
     task = __shfl_sync(0xffffffffu, task, 0);
     if (task < 0) break;
 
-    const int wbeg = task * 32;
-    const int wend = min(n, wbeg + 32);
+    // task: up to 32 consecutive bodies of one cloud; the walk starts at the cloud root
+    const int wbeg = A.task_begin ? A.task_begin[task] : task * 32;
+    const int wend = min(A.task_begin ? A.task_end[task] : n, wbeg + 32);
+    const int root = A.task_seg ? A.task_seg[task] : 0;
+    const double side = A.geom[8 * root + 3];
     const int gi = wbeg + lane;
-    const bool valid = gi < n;
+    const bool valid = gi < wend;
 
     float xh = 0, yh = 0, zh = 0, xl = 0, yl = 0, zl = 0;
     if (valid) {
@@ -361,7 +366,7 @@ k_walk(WalkArgs A) {
     bool abort = false;
     {
       const unsigned vm = __ballot_sync(0xffffffffu, valid);
-      if (lane == 0) st.set(0, 0u, vm);        // root node, count 1, kind node
+      if (lane == 0) st.set(0, (uint32_t)root, vm);   // root node, count 1, kind node
     }
     __syncwarp();
 
@@ -733,7 +738,14 @@ int walk_forces(Ctx *c, double theta, double eps, double *acc, int32_t *counts, 
   A.topo = t.topo; A.ndepth = t.ndepth; A.ncom = t.ncom; A.geom = t.geom;
   A.perm = t.idx; A.nnodes = t.nnodes;
   A.n = (int)c->n;
-  A.ntasks = (int)((c->n + 31) / 32);
+  if (c->seg.nseg > 1) {
+    A.ntasks = c->seg.ntasks;
+    A.task_begin = c->seg.task_begin;
+    A.task_end = c->seg.task_end;
+    A.task_seg = c->seg.task_seg;
+  } else {
+    A.ntasks = (int)((c->n + 31) / 32);
+  }
   A.theta2d = theta * theta;
   A.theta2f = (float)(theta * theta);
   A.eps2 = (float)(eps * eps);

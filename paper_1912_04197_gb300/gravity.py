@@ -38,7 +38,7 @@ class gravity_params(ctypes.Structure):
     _fields_ = [("G", ctypes.c_double), ("order", ctypes.c_int32), ("leaf_max", ctypes.c_int32),
                 ("accum", ctypes.c_int32), ("mac_guard", ctypes.c_int32),
                 ("scheme", ctypes.c_int32), ("walk_cfg", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 def _load() -> ctypes.CDLL:
@@ -65,6 +65,8 @@ def _load() -> ctypes.CDLL:
         "gravity_stats": (I, [P, ctypes.POINTER(I64)]),
         "gravity_probe_fp32": (I, [P, I64, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "gravity_direct_noalloc": (I, [I64, P, P, D, D, P, P]),
+        "gravity_set_clouds": (I, [P, ctypes.c_int32, P]),
+        "gravity_batch_tree_build": (I, [P, ctypes.c_int32, P, P, P, PP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -156,6 +158,31 @@ def gravity_tree_build(ctx: Context, pos: torch.Tensor, mass: torch.Tensor, p=No
                                    None if p is None else ctypes.byref(p)), "gravity_tree_build")
 
 
+def _offsets(offsets) -> np.ndarray:
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    if off.ndim != 1 or len(off) < 2:
+        raise ValueError("offsets must be a 1-D array of nclouds + 1 entries")
+    return off
+
+
+def gravity_set_clouds(ctx: Context, offsets):
+    """Independent clouds: cloud k = bodies offsets[k]:offsets[k+1] (host array)."""
+    off = _offsets(offsets)
+    _check(_lib.gravity_set_clouds(ctx.handle, len(off) - 1, off.ctypes.data_as(ctypes.c_void_p)),
+           "gravity_set_clouds")
+
+
+def gravity_batch_tree_build(ctx: Context, offsets, pos: torch.Tensor, mass: torch.Tensor,
+                             p=None):
+    off = _offsets(offsets)
+    if int(off[-1]) != pos.shape[0] or mass.numel() != pos.shape[0]:
+        raise ValueError("offsets[-1] must equal the number of bodies")
+    _check(_lib.gravity_batch_tree_build(ctx.handle, len(off) - 1,
+                                         off.ctypes.data_as(ctypes.c_void_p), _dev(pos, "pos", 3),
+                                         _dev(mass, "mass"), None if p is None else ctypes.byref(p)),
+           "gravity_batch_tree_build")
+
+
 def gravity_forces(ctx: Context, theta: float, eps: float, acc: torch.Tensor) -> torch.Tensor:
     _check(_lib.gravity_forces(ctx.handle, float(theta), float(eps), _dev(acc, "acc", 3)),
            "gravity_forces")
@@ -237,13 +264,15 @@ def gravity_debug_export(ctx: Context, what: int, n: int) -> np.ndarray:
                "gravity_debug_export")
         return out
     dt, width = _DBG_DTYPES[what]
-    if what in (DBG_ROOT, DBG_WALKSTATS):
+    if what == DBG_ROOT:
+        count = max(1, int(n))          # n = number of clouds for the root cubes
+    elif what == DBG_WALKSTATS:
         count = 1
     elif what in (DBG_KEYS, DBG_PERM):
         count = n
     else:
         count = int(gravity_debug_export(ctx, DBG_NNODES, n)[0])
-    flat = what in (DBG_ROOT, DBG_WALKSTATS) or width == 1
+    flat = what == DBG_WALKSTATS or width == 1
     out = np.zeros((count * width,) if flat else (count, width), dt)
     _check(_lib.gravity_debug_export(ctx.handle, what, out.ctypes.data_as(ctypes.c_void_p),
                                      out.nbytes), "gravity_debug_export")

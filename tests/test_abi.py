@@ -43,4 +43,4 @@ def test_params_default_needs_no_gpu():
     lib.gravity_params_default(buf)
     G = ctypes.cast(buf, ctypes.POINTER(ctypes.c_double))[0]
     ints = ctypes.cast(ctypes.byref(buf, 8), ctypes.POINTER(ctypes.c_int32))
-    assert G == 1.0 and [ints[i] for i in range(6)] == [0, 1, 0, 1, 0, -1]
+    assert G == 1.0 and [ints[i] for i in range(7)] == [0, 1, 0, 1, 0, -1, 1]

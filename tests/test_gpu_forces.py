@@ -150,3 +150,35 @@ def test_host_entry_point(gpu):
     gpu.gravity_forces_host(ctx, ph, mh, 0.5, 1e-3, gpu.params(leaf_max=8), ah)
     a, _ = _gpu_forces(gpu, pos, m, 0.5, 1e-3, leaf_max=8)
     assert np.array_equal(ah.numpy(), a)
+
+
+@pytest.mark.parametrize("clouds", [False, True])
+def test_leapfrog_graph_replay_matches_eager(gpu, clouds):
+    # on a non-default stream leapfrog_step captures one step as a CUDA graph and
+    # replays it; the result must equal launching every kernel (same kernels, same order)
+    if clouds:
+        off, pos, vel, m = inputs.ensemble(nclouds=12, seed=2, nmin=100, nmax=3000)
+    else:
+        off = None
+        pos, vel, m = inputs.rubble_pile(20_000, seed=9)
+    out = []
+    for use_graph in (0, 1):
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            ctx = gpu.Context(0)
+            if clouds:
+                gpu.gravity_set_clouds(ctx, off)
+            P = torch.tensor(pos, device="cuda")
+            V = torch.tensor(vel, device="cuda")
+            M = torch.tensor(m, device="cuda")
+            A = torch.empty_like(P)
+            p = gpu.params(order=2, leaf_max=16, use_graph=use_graph)
+            gpu.gravity_tree_build(ctx, P, M, p)
+            gpu.gravity_forces(ctx, 0.5, 1e-3, A)
+            gpu.leapfrog_step(ctx, P, V, M, A, 1e-3, 8, 0.5, 1e-3, p)
+            gpu.leapfrog_step(ctx, P, V, M, A, 1e-3, 4, 0.5, 1e-3, p)   # reuses the graph
+            gpu.gravity_sync(ctx)
+        stream.synchronize()
+        out.append((P.cpu().numpy(), V.cpu().numpy(), A.cpu().numpy()))
+    for x, y in zip(out[0], out[1]):
+        assert np.array_equal(x, y)

@@ -41,7 +41,7 @@ def test_keys_and_order_bitexact(gpu, case):
     pos, _, m = _cases()[case]
     ctx = _build(gpu, pos, m)
     n = len(pos)
-    root = gpu.gravity_debug_export(ctx, gpu.DBG_ROOT, n)
+    root = gpu.gravity_debug_export(ctx, gpu.DBG_ROOT, 1)[0]
     lo, side = oracle.root_cube(pos)
     assert root[:3].tolist() == lo.tolist() and root[3] == side
     keys = gpu.gravity_debug_export(ctx, gpu.DBG_KEYS, n)
@@ -96,7 +96,7 @@ def test_moments_bitexact(gpu, case, leaf_max, order):
         # other roundings): compare on the node's natural scale m l^2
         gq = gpu.gravity_debug_export(ctx, gpu.DBG_QUAD, n)[order_ids]
         depth = gpu.gravity_debug_export(ctx, gpu.DBG_DEPTH, n)[order_ids]
-        side = gpu.gravity_debug_export(ctx, gpu.DBG_ROOT, n)[3]
+        side = gpu.gravity_debug_export(ctx, gpu.DBG_ROOT, 1)[0][3]
         scale = (om * (side * 2.0 ** -depth.astype(np.float64)) ** 2)[:, None]
         assert np.all(np.abs(gq - oq) <= 1e-12 * scale)
 
@@ -110,7 +110,7 @@ def test_single_and_coincident(gpu):
     topo = gpu.gravity_debug_export(ctx, gpu.DBG_TOPO, 100)
     depth = gpu.gravity_debug_export(ctx, gpu.DBG_DEPTH, 100)
     assert topo.tolist() == [[-1, 0, 0, 100]] and depth.tolist() == [21]
-    root = gpu.gravity_debug_export(ctx, gpu.DBG_ROOT, 100)
+    root = gpu.gravity_debug_export(ctx, gpu.DBG_ROOT, 1)[0]
     assert root[3] == 1.0
 
 

@@ -45,6 +45,6 @@ def force_errors(a, ref, absum):
     d = np.linalg.norm(np.asarray(a) - np.asarray(ref), axis=1)
     r = np.linalg.norm(ref, axis=1)
     floor = 1e-3 * np.sqrt(np.mean(r * r)) if len(r) else 0.0
-    rel = d / np.maximum(r, floor)
+    rel = d / np.maximum(np.maximum(r, floor), 1e-300)
     scale = d / np.maximum(absum, 1e-300)
     return rel, scale
