@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=65536, help="oracle targets in cpu_baseline")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble leg")
+    ap.add_argument("--no-tune", action="store_true", help="default walk shape, no autotuning")
+    ap.add_argument("--ensemble-steps", type=int, default=50)
     return ap.parse_args()
 
 
@@ -217,6 +220,9 @@ def run_ours(args, rank, world, local_rank):
     acc = torch.empty_like(P)
     ctx = g.Context(dev)
     p = g.params(order=args.order, leaf_max=args.leaf_max, accum=args.accum)
+    if not args.no_tune:
+        from paper_1912_04197_gb300 import autotune
+        p.walk_cfg = autotune.tune_walk(ctx, P, M, p, args.theta, args.eps)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
     stream = torch.cuda.current_stream(dev)
 
@@ -334,6 +340,8 @@ def run_ours(args, rank, world, local_rank):
                "ms_per_step": 1e3 * float(tt.item()),
                "api": "gravity_forces_host (pinned host buffers, copies + build + walk + sync)"}
 
+    ens = None if args.no_ensemble else ensemble_leg(args, g, dev, rank)
+
     if rank != 0:
         return 0
     cpu = None
@@ -348,9 +356,52 @@ def run_ours(args, rank, world, local_rank):
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "gpu_launches_per_step": launches / args.steps, "clocks": clk,
             "timed_wall_s": wall}
+    line["config"]["walk_cfg"] = int(p.walk_cfg)
+    if ens is not None:
+        line["ensemble"] = ens
     line.update(extra)
     print(json.dumps(line), flush=True)
     return 0
+
+
+def ensemble_leg(args, g, dev, rank):
+    """Batched ensemble: 256 independent spinning clouds (N_k log-uniform in
+    [1024, 65536]), one build + one walk launch per step, KDK leapfrog steps
+    replayed as a CUDA graph on a side stream, autotuned walk shape."""
+    import torch
+    from paper_1912_04197_gb300 import autotune, inputs
+    off, pos, vel, m = inputs.ensemble(nclouds=256, seed=args.seed + 100 + rank)
+    n = len(pos)
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        ctx = g.Context(dev)
+        g.gravity_set_clouds(ctx, off)
+        P = torch.tensor(pos, device=dev)
+        V = torch.tensor(vel, device=dev)
+        M = torch.tensor(m, device=dev)
+        A = torch.empty_like(P)
+        p = g.params(order=args.order, leaf_max=args.leaf_max)
+        if not args.no_tune:
+            p.walk_cfg = autotune.tune_walk(ctx, P, M, p, args.theta, args.eps, clouds=256)
+        g.gravity_tree_build(ctx, P, M, p)
+        g.gravity_forces(ctx, args.theta, args.eps, A)
+        g.leapfrog_step(ctx, P, V, M, A, 1e-3, 3, args.theta, args.eps, p)   # warm-up + capture
+        k0 = g.gravity_stats(ctx)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.leapfrog_step(ctx, P, V, M, A, 1e-3, args.ensemble_steps, args.theta, args.eps, p)
+        e1.record(stream)
+        e1.synchronize()
+        g.gravity_sync(ctx)
+        ms = e0.elapsed_time(e1)
+        kernels = g.gravity_stats(ctx) - k0
+    steps = args.ensemble_steps
+    return {"workload": f"256 independent clouds, {n} bodies (N_k log-uniform in [1024, 65536]), "
+                        f"uniform spheres with random spin, eps={args.eps}, theta={args.theta}, "
+                        f"order {args.order}, leaf {args.leaf_max}, dt=1e-3",
+            "steps": steps, "ms_per_step": ms / steps, "value": n * steps / (ms * 1e-3),
+            "unit": "body-forces/s (leapfrog steps, one force evaluation each)",
+            "graph": True, "kernels_per_step": kernels / steps, "walk_cfg": int(p.walk_cfg)}
 
 
 def main():

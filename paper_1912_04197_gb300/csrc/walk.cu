@@ -37,8 +37,19 @@ constexpr int kWalkWarps = 4;
 constexpr int kSmemStack = 128;                // stack entries in shared memory
 constexpr int kGlobStack = 1152;               // further entries in global memory, per warp
 constexpr int kStackCap = kSmemStack + kGlobStack;
-constexpr int kFlushAt = 16;                   // evaluate a list once it holds this many terms
-constexpr int kListCap = kFlushAt + 32;        // a batch appends at most 32 terms per list
+constexpr int kFlushMax = 16;                  // lists are evaluated once they hold flush_at
+constexpr int kListCap = kFlushMax + 32;       // (<= kFlushMax) terms; a batch appends <= 32
+
+// Walk launch shapes selectable at run time (gravity_params.walk_cfg, autotuned):
+// cfg = fi + 3 bi + 9 qi with flush_at = {16, 12, 8}[fi], resident blocks per SM =
+// occupancy maximum - bi, and task queues per SM (qi = 0) or one global queue (qi = 1).
+constexpr int kWalkConfigs = 18;
+struct WalkShape { int flush_at, blocks_less, one_queue; };
+inline WalkShape walk_shape(int cfg) {
+  if (cfg < 0 || cfg >= kWalkConfigs) cfg = 0;
+  const int fl[3] = {16, 12, 8};
+  return WalkShape{fl[cfg % 3], (cfg / 3) % 3, cfg / 9};
+}
 constexpr uint32_t kKindBody = 0x80000000u;
 constexpr uint32_t kFirstMask = 0x01FFFFFFu;   // 25-bit first index
 constexpr int kCntShift = 25;                  // 6-bit (count - 1)
@@ -93,6 +104,7 @@ struct WalkArgs {
   int max_iter;
   unsigned *task_counter;         // [nqueues] per-queue counters, zeroed before the launch
   int nqueues;
+  int flush_at;
   uint2 *gstack;                  // [persistent warps][kGlobStack] (first|cnt|kind, mask)
   const int32_t *task_begin;      // several clouds: per task first body, cloud end, cloud id
   const int32_t *task_end;
@@ -590,7 +602,7 @@ k_walk(WalkArgs A) {
       __syncwarp();
 
       // ---- evaluate full lists
-      if (npt >= kFlushAt) {
+      if (npt >= A.flush_at) {
         if (COUNT) { w_mono += npt; split_costs(M.lb, 3, npt, lane, w_split); }
         float px, py, pz;
         flush_point<EPS0, COUNT>(M, npt, lane, xh, yh, zh, xl, yl, zl, eps2, px, py, pz, gi,
@@ -599,7 +611,7 @@ k_walk(WalkArgs A) {
         npt = 0;
         __syncwarp();
       }
-      if (nfar >= kFlushAt) {
+      if (nfar >= A.flush_at) {
         if (COUNT) { w_quad += nfar; split_costs(M.fc, 2, nfar, lane, w_split); }
         float px, py, pz;
         flush_far<ORDER, EPS0, COUNT>(&S, nfar, lane, xr, yr, zr, eps2, px, py, pz, c_m2p);
@@ -608,7 +620,7 @@ k_walk(WalkArgs A) {
         __syncwarp();
       }
       if constexpr (ORDER == 2) {
-        if (nnear >= kFlushAt) {
+        if (nnear >= A.flush_at) {
           if (COUNT) { w_quad += nnear; split_costs(S.qb, 3, nnear, lane, w_split); }
           float px, py, pz;
           flush_near<EPS0, COUNT>(S, nnear, lane, xh, yh, zh, xl, yl, zl, eps2, px, py, pz,
@@ -707,7 +719,11 @@ int launch_walk(Ctx *c, WalkArgs A) {
     GRAV_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, 32 * kWalkWarps, smem));
     blocks_per_sm[dev] = b > 0 ? b : 1;
   }
-  int blocks = blocks_per_sm[dev] * c->num_sms;
+  const WalkShape shape = walk_shape(c->params.walk_cfg);
+  A.flush_at = shape.flush_at;
+  int bps = blocks_per_sm[dev] - shape.blocks_less;
+  if (bps < 1) bps = 1;
+  int blocks = bps * c->num_sms;
   const int need = (A.ntasks + kWalkWarps - 1) / kWalkWarps;
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
@@ -720,7 +736,7 @@ int launch_walk(Ctx *c, WalkArgs A) {
     c->walk_gstack_cap = gneed;
   }
   A.gstack = reinterpret_cast<uint2 *>(c->walk_gstack);
-  A.nqueues = c->num_sms;
+  A.nqueues = shape.one_queue ? 1 : c->num_sms;
   GRAV_CUDA_TRY(cudaMemsetAsync(A.task_counter, 0, sizeof(unsigned) * A.nqueues, c->stream));
   kern<<<blocks, 32 * kWalkWarps, smem, c->stream>>>(A);
   ++c->launches;
