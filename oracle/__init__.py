@@ -72,6 +72,10 @@ def _load():
             lib.orc_tree_export_moments.restype = None
             lib.orc_tree_forces.argtypes = [P, D, D, D, I, I64, P, P, P, P]
             lib.orc_tree_forces.restype = None
+            lib.orc_tree_vjp.argtypes = [P, D, D, D, I, P, P]
+            lib.orc_tree_vjp.restype = I
+            lib.orc_tree_forces_frozen.argtypes = [P, D, D, D, I, P, P]
+            lib.orc_tree_forces_frozen.restype = I
             lib.orc_direct.argtypes = [I64, P, P, D, D, I64, P, P, P]
             lib.orc_direct.restype = None
             lib.orc_leapfrog.argtypes = [I64, P, P, P, P, D, I, I, I, D, D, D, I, I, I]
@@ -204,6 +208,29 @@ class Tree:
         return acc, absum, counts
 
 
+def tree_vjp(tree: "Tree", lam, theta: float, eps: float, G: float = 1.0, mac_guard: int = 1):
+    """(d acc / d pos)^T lam on the frozen tree (monopole), caller order (n,3)."""
+    lam = _f64(lam, 3).reshape(-1, 3)
+    grad = np.zeros((tree.n, 3))
+    rc = _load().orc_tree_vjp(tree._h, float(theta), float(eps), float(G), int(mac_guard),
+                              _ptr(lam), _ptr(grad))
+    if rc:
+        raise OracleError(rc)
+    return grad
+
+
+def tree_forces_frozen(tree: "Tree", pos_new, theta: float, eps: float, G: float = 1.0,
+                       mac_guard: int = 1):
+    """Accelerations at pos_new with the decisions of the tree's own positions."""
+    pos_new = _f64(pos_new, 3).reshape(-1, 3)
+    acc = np.zeros((tree.n, 3))
+    rc = _load().orc_tree_forces_frozen(tree._h, float(theta), float(eps), float(G),
+                                        int(mac_guard), _ptr(pos_new), _ptr(acc))
+    if rc:
+        raise OracleError(rc)
+    return acc
+
+
 def direct(pos, mass, eps: float, G: float = 1.0, targets=None):
     """Eq. (Newton) with softening (Eq. Force_rComp): (acc[ntarg,3], absum[ntarg])."""
     pos = _f64(pos, 3).reshape(-1, 3)
@@ -248,3 +275,33 @@ def diagnostics(pos, vel, mass, eps, G=1.0):
     _load().orc_diagnostics(len(pos), _ptr(pos), _ptr(vel), _ptr(mass), float(eps), float(G),
                             _ptr(out))
     return float(out[0]), out[1:4].copy(), out[4:7].copy()
+
+
+def leapfrog_grad(pos0, vel0, mass, xbar, vbar, dt, nsteps, *, theta=0.5, eps=1e-3, G=1.0,
+                  leaf_max=1, mac_guard=1):
+    """Reverse-mode gradient of KDK leapfrog (Sec. 2.3) with the tree's decisions frozen
+    at every step: given the cotangents (xbar, vbar) of (x_N, v_N), return those of
+    (x_0, v_0).  With h = dt/2 the step is kick(h), drift(dt), kick(h); reversing
+    kick(h) adds h J(x)^T vbar to xbar, reversing drift(dt) adds dt xbar to vbar; the
+    two kicks at an interior time level share one vbar, so they combine to dt."""
+    mass = _f64(mass).reshape(-1)
+    x = _f64(pos0, 3).reshape(-1, 3).copy()
+    v = _f64(vel0, 3).reshape(-1, 3).copy()
+    a = tree_forces(x, mass, theta, eps, G, leaf_max=leaf_max, mac_guard=mac_guard)
+    xs = [x.copy()]
+    for _ in range(nsteps):
+        x, v, a = step(x, v, mass, a, dt, 1, theta=theta, eps=eps, G=G, leaf_max=leaf_max,
+                       mac_guard=mac_guard)
+        xs.append(x.copy())
+
+    def jt(xn, u):
+        return tree_vjp(Tree(xn, mass, leaf_max=leaf_max), u, theta, eps, G, mac_guard)
+
+    h = 0.5 * dt
+    xb = _f64(xbar, 3).reshape(-1, 3).copy()
+    vb = _f64(vbar, 3).reshape(-1, 3).copy()
+    xb += h * jt(xs[nsteps], vb)
+    for k in range(nsteps - 1, -1, -1):
+        vb += dt * xb
+        xb += (h if k == 0 else dt) * jt(xs[k], vb)
+    return xb, vb

@@ -32,10 +32,12 @@
 //     a leaf holding several bodies is tested like an internal node.
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <numeric>
+#include <utility>
 #include <vector>
 
 namespace {
@@ -242,16 +244,16 @@ struct WalkCtx {
 // Force computation (Sec. 2.1): traverse from the root; a single-body leaf is a
 // body-to-body term; otherwise test l < theta * D (l = cell side, D = distance
 // to the node COM); accept -> node term and stop; open -> all children (or, for a
-// bucket leaf, its bodies).
-void walk_rec(const WalkCtx &w, int64_t k, WalkOut &o) {
+// bucket leaf, its bodies).  The decisions are made here once; the visitor
+// receives the accepted node terms (node(k)), body-to-body terms (body(j), j != B)
+// and opening tests (test()).
+template <class V>
+void decide_rec(const WalkCtx &w, int64_t k, V &v) {
   const Tree &t = *w.t;
   const Node &nd = t.nodes[k];
   int64_t cnt = nd.end - nd.begin;
   if (nd.leaf && cnt == 1) {
-    if (nd.begin != w.ib) {
-      point_term(o, t.m[nd.begin], &t.x[3 * nd.begin], w.xb, w.eps2);
-      o.p2p++;
-    }
+    if (nd.begin != w.ib) v.body(nd.begin);
     return;
   }
   bool contains = (nd.begin <= w.ib && w.ib < nd.end);
@@ -260,25 +262,98 @@ void walk_rec(const WalkCtx &w, int64_t k, WalkOut &o) {
     double d0 = nd.com[0] - w.xb[0], d1 = nd.com[1] - w.xb[1], d2 = nd.com[2] - w.xb[2];
     double D2 = (d0 * d0 + d1 * d1) + d2 * d2;
     double l = std::ldexp(t.side, -nd.depth);
-    o.tests++;
+    v.test();
     if (l * l < w.theta2 * D2) open = false;
   }
   if (!open) {
-    o.m2p++;
-    if (t.order >= 2) quad_term(o, nd, w.xb, w.eps2);
-    else point_term(o, nd.m, nd.com, w.xb, w.eps2);
+    v.node(k);
     return;
   }
   if (nd.leaf) {
-    for (int64_t j = nd.begin; j < nd.end; ++j) {
-      if (j == w.ib) continue;
-      point_term(o, t.m[j], &t.x[3 * j], w.xb, w.eps2);
-      o.p2p++;
-    }
+    for (int64_t j = nd.begin; j < nd.end; ++j)
+      if (j != w.ib) v.body(j);
     return;
   }
-  for (int64_t c : nd.children) walk_rec(w, c, o);
+  for (int64_t c : nd.children) decide_rec(w, c, v);
 }
+
+// Visitor: accelerations (Eqs. Force_leaf, Force_thetaTrue, Force_rComp).
+struct ForceVisitor {
+  const WalkCtx &w;
+  WalkOut &o;
+  void test() { o.tests++; }
+  void node(int64_t k) {
+    const Tree &t = *w.t;
+    const Node &nd = t.nodes[k];
+    o.m2p++;
+    if (t.order >= 2) quad_term(o, nd, w.xb, w.eps2);
+    else point_term(o, nd.m, nd.com, w.xb, w.eps2);
+  }
+  void body(int64_t j) {
+    const Tree &t = *w.t;
+    point_term(o, t.m[j], &t.x[3 * j], w.xb, w.eps2);
+    o.p2p++;
+  }
+};
+
+void walk_rec(const WalkCtx &w, int64_t k, WalkOut &o) {
+  ForceVisitor v{w, o};
+  decide_rec(w, k, v);
+}
+
+// Jacobian of the softened point term f(d) = d / (|d|^2 + eps^2)^{3/2} with respect
+// to d: J = (I - 3 d d^T / r^2) / r^3, r^2 = |d|^2 + eps^2 (symmetric).  Returns
+// J u for a vector u; zero when r^2 = 0.
+inline void jac_times(const double *d, double eps2, const double *u, double *out) {
+  double r2 = ((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]) + eps2;
+  if (r2 == 0.0) { out[0] = out[1] = out[2] = 0.0; return; }
+  double r = std::sqrt(r2);
+  double inv3 = 1.0 / (r2 * r);
+  double du = (d[0] * u[0] + d[1] * u[1]) + d[2] * u[2];
+  double c = 3.0 * du / r2;
+  for (int a = 0; a < 3; ++a) out[a] = inv3 * (u[a] - c * d[a]);
+}
+
+// Visitor: vector-Jacobian product of the accelerations on the frozen tree
+// (monopole terms).  For a term a_B += m_s f(s - x_B) with cotangent u = lambda_B:
+// grad x_B -= m_s J u, and grad s += m_s J u, where s is a body or a node COM.
+struct VjpVisitor {
+  const WalkCtx &w;
+  const double *lam;            // cotangent of body B's acceleration (times G)
+  double *gb;                   // gradient of x_B
+  std::vector<double> &gnode;   // gradient of node COMs (this target's share)
+  std::vector<std::pair<int64_t, std::array<double, 3>>> &gbody;
+  void test() {}
+  void term(const double *src, double m, double *gs) {
+    double d[3] = {src[0] - w.xb[0], src[1] - w.xb[1], src[2] - w.xb[2]};
+    double ju[3];
+    jac_times(d, w.eps2, lam, ju);
+    for (int a = 0; a < 3; ++a) { gb[a] -= m * ju[a]; gs[a] += m * ju[a]; }
+  }
+  void node(int64_t k) {
+    const Node &nd = w.t->nodes[k];
+    term(nd.com, nd.m, &gnode[3 * k]);
+  }
+  void body(int64_t j) {
+    std::array<double, 3> gs{0, 0, 0};
+    term(&w.t->x[3 * j], w.t->m[j], gs.data());
+    gbody.push_back({j, gs});
+  }
+};
+
+// Visitor: accelerations with the decisions already taken but every source at new
+// positions (node COMs recomputed from the new body positions): the force of the
+// frozen tree, for finite-difference checks of the product above.
+struct FrozenVisitor {
+  const WalkCtx &w;
+  const double *xnew;           // sorted new positions
+  const std::vector<double> &cnew;   // new node COMs
+  const double *xb_new;
+  WalkOut &o;
+  void test() {}
+  void node(int64_t k) { point_term(o, w.t->nodes[k].m, &cnew[3 * k], xb_new, w.eps2); }
+  void body(int64_t j) { point_term(o, w.t->m[j], &xnew[3 * j], xb_new, w.eps2); }
+};
 
 }  // namespace
 
@@ -439,6 +514,70 @@ void orc_tree_forces(const void *h, double theta, double eps, double G, int mac_
     if (absum) absum[k] = G * o.absum;
     if (counts) { counts[3 * k] = o.tests; counts[3 * k + 1] = o.m2p; counts[3 * k + 2] = o.p2p; }
   }
+}
+
+// Vector-Jacobian product of the tree accelerations (monopole, order 0) with the
+// interaction decisions frozen: grad = (d acc / d pos)^T lambda, both (n,3) in caller
+// order, G applied.  A node COM is sum m_j x_j / M over its bodies, so its gradient
+// reaches each member j as (m_j / M) times the node's share.
+int orc_tree_vjp(const void *h, double theta, double eps, double G, int mac_guard,
+                 const double *lambda, double *grad) {
+  const Tree *t = (const Tree *)h;
+  if (t->order != 0) return ORC_E_ARG;
+  const int64_t n = t->n;
+  std::vector<int64_t> inv(n);
+  for (int64_t i = 0; i < n; ++i) inv[t->perm[i]] = i;
+  const double theta2 = theta * theta, eps2 = eps * eps;
+  std::vector<double> gs(3 * n, 0.0);                  // sorted order
+  std::vector<double> gnode(3 * t->nodes.size(), 0.0);
+  for (int64_t ib = 0; ib < n; ++ib) {
+    int64_t ci = t->perm[ib];
+    double lam[3] = {G * lambda[3 * ci], G * lambda[3 * ci + 1], G * lambda[3 * ci + 2]};
+    WalkCtx w{t, theta2, eps2, mac_guard, ib, &t->x[3 * ib]};
+    std::vector<std::pair<int64_t, std::array<double, 3>>> gbody;
+    VjpVisitor v{w, lam, &gs[3 * ib], gnode, gbody};
+    decide_rec(w, 0, v);
+    for (auto &p : gbody)
+      for (int a = 0; a < 3; ++a) gs[3 * p.first + a] += p.second[a];
+  }
+  for (size_t k = 0; k < t->nodes.size(); ++k) {
+    const Node &nd = t->nodes[k];
+    for (int64_t j = nd.begin; j < nd.end; ++j)
+      for (int a = 0; a < 3; ++a) gs[3 * j + a] += (t->m[j] / nd.m) * gnode[3 * k + a];
+  }
+  for (int64_t ib = 0; ib < n; ++ib)
+    for (int a = 0; a < 3; ++a) grad[3 * t->perm[ib] + a] = gs[3 * ib + a];
+  return ORC_OK;
+}
+
+// Accelerations of the frozen tree at new positions pos_new (caller order), the
+// decisions being those taken at the tree's own positions (monopole terms).
+int orc_tree_forces_frozen(const void *h, double theta, double eps, double G, int mac_guard,
+                           const double *pos_new, double *acc) {
+  const Tree *t = (const Tree *)h;
+  if (t->order != 0) return ORC_E_ARG;
+  const int64_t n = t->n;
+  std::vector<double> xs(3 * n);
+  for (int64_t i = 0; i < n; ++i)
+    for (int a = 0; a < 3; ++a) xs[3 * i + a] = pos_new[3 * t->perm[i] + a];
+  std::vector<double> cnew(3 * t->nodes.size());
+  for (size_t k = 0; k < t->nodes.size(); ++k) {
+    const Node &nd = t->nodes[k];
+    double s[3] = {0, 0, 0};
+    for (int64_t j = nd.begin; j < nd.end; ++j)
+      for (int a = 0; a < 3; ++a) s[a] = s[a] + t->m[j] * xs[3 * j + a];
+    for (int a = 0; a < 3; ++a) cnew[3 * k + a] = s[a] / nd.m;
+  }
+  const double theta2 = theta * theta, eps2 = eps * eps;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t ib = 0; ib < n; ++ib) {
+    WalkCtx w{t, theta2, eps2, mac_guard, ib, &t->x[3 * ib]};
+    WalkOut o;
+    FrozenVisitor v{w, xs.data(), cnew, &xs[3 * ib], o};
+    decide_rec(w, 0, v);
+    for (int a = 0; a < 3; ++a) acc[3 * t->perm[ib] + a] = G * o.a[a];
+  }
+  return ORC_OK;
 }
 
 // Eq. (Newton), per unit mass of body i, with the softened r of Eq. (Force_rComp):

@@ -1,0 +1,66 @@
+"""Pins of the oracle's adjoint (vector-Jacobian product on the frozen tree, and the
+reverse pass of the leapfrog) against finite differences and a symmetry of the
+Jacobian that the mathematics fixes."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1912_04197_gb300 import inputs
+
+pytestmark = pytest.mark.oracle
+
+
+@pytest.mark.parametrize("theta,leaf_max,eps", [(0.0, 1, 1e-2), (0.5, 1, 1e-2), (0.7, 8, 0.0)])
+def test_vjp_matches_frozen_finite_differences(theta, leaf_max, eps):
+    pos, _, m = inputs.uniform_sphere(600, seed=1)
+    m = m * np.random.default_rng(2).lognormal(0, 0.3, len(m))
+    t = oracle.Tree(pos, m, leaf_max=leaf_max)
+    rng = np.random.default_rng(3)
+    lam = rng.standard_normal(pos.shape)
+    g = oracle.tree_vjp(t, lam, theta, eps, G=1.3)
+    h = 1e-6
+    for _ in range(4):
+        e = rng.standard_normal(pos.shape)
+        fp = oracle.tree_forces_frozen(t, pos + h * e, theta, eps, G=1.3)
+        fm = oracle.tree_forces_frozen(t, pos - h * e, theta, eps, G=1.3)
+        fd = ((fp - fm) * lam).sum() / (2 * h)
+        assert abs(fd - (g * e).sum()) <= 1e-6 * np.abs(g * e).sum(), (fd, (g * e).sum())
+    # the frozen force at the tree's own positions is the ordinary tree force
+    a0 = oracle.tree_forces(pos, m, theta, eps, 1.3, leaf_max=leaf_max)
+    assert np.allclose(oracle.tree_forces_frozen(t, pos, theta, eps, G=1.3), a0, rtol=0,
+                       atol=1e-12 * np.abs(a0).max())
+
+
+def test_direct_jacobian_mass_symmetry():
+    # M (d a / d x) is symmetric for the direct sum: m_i m_j J(d_ij) with J even and
+    # symmetric, so u^T M J w = w^T M J u for any u, w
+    pos, _, _ = inputs.uniform_sphere(300, seed=4)
+    m = np.random.default_rng(5).random(300) + 0.2
+    t = oracle.Tree(pos, m)
+    rng = np.random.default_rng(6)
+    u, w = rng.standard_normal(pos.shape), rng.standard_normal(pos.shape)
+    lhs = (oracle.tree_vjp(t, m[:, None] * u, 0.0, 0.05) * w).sum()
+    rhs = (oracle.tree_vjp(t, m[:, None] * w, 0.0, 0.05) * u).sum()
+    assert abs(lhs - rhs) <= 1e-10 * (abs(lhs) + abs(rhs))
+
+
+def test_leapfrog_gradient_matches_finite_differences_direct():
+    # theta = 0: the dynamics is smooth (no decisions), so finite differences of the
+    # whole simulation check the reverse pass
+    pos, vel, m = inputs.rubble_pile(150, seed=8)
+    dt, ns, eps = 2e-3, 12, 5e-2
+    rng = np.random.default_rng(9)
+    cx, cv = rng.standard_normal(pos.shape), rng.standard_normal(pos.shape)
+
+    def L(x0, v0):
+        a = oracle.tree_forces(x0, m, 0.0, eps)
+        x, v, _ = oracle.step(x0, v0, m, a, dt, ns, theta=0.0, eps=eps)
+        return (cx * x).sum() + (cv * v).sum()
+
+    gx, gv = oracle.leapfrog_grad(pos, vel, m, cx, cv, dt, ns, theta=0.0, eps=eps)
+    h = 1e-6
+    for _ in range(3):
+        ex, ev = rng.standard_normal(pos.shape), rng.standard_normal(pos.shape)
+        fd = (L(pos + h * ex, vel + h * ev) - L(pos - h * ex, vel - h * ev)) / (2 * h)
+        an = (gx * ex).sum() + (gv * ev).sum()
+        assert abs(fd - an) <= 1e-6 * (np.abs(gx * ex).sum() + np.abs(gv * ev).sum()), (fd, an)
