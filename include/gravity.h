@@ -108,6 +108,52 @@ int gravity_forces(gravity_ctx *ctx, double theta, double eps, double *acc);
 int gravity_forces_counted(gravity_ctx *ctx, double theta, double eps, double *acc,
                            int32_t *counts);
 
+/* Vector-Jacobian product of the tree accelerations with respect to the body
+ * positions, the interaction decisions of the current tree held fixed (the tree
+ * of the last gravity_tree_build; monopole terms of Eq. (Force_thetaTrue) and
+ * Eq. (Force_leaf) with the softening of Eq. (Force_rComp)).  The paper has no
+ * adjoint: this is the differentiation layer built on its force kernel.
+ *   grad_pos = (d acc / d pos)^T lambda
+ * For each accepted term a_i += G m_s f(s - x_i), f(d) = d / (|d|^2 + eps^2)^{3/2},
+ * with w = G m_s J(d) lambda_i, J = (I - 3 d d^T / r^2) / r^3: x_i takes -w and the
+ * source s takes +w; a node's COM is sum_j m_j x_j / M, so its share reaches body j
+ * as (m_j / M) w.  theta, eps and the opening decisions are those of gravity_forces
+ * with the same arguments.
+ * lambda, grad_pos: device, (n,3) FP64 row-major, caller order; lambda is read,
+ * grad_pos written (every row).  Requires order 0 (GRAVITY_E_ARG otherwise);
+ * GRAVITY_E_NOTREE without a tree.  Works with several clouds as gravity_forces.
+ * FP32 terms, compensated per-body sums, FP64 scatter (atomics: the last bits may
+ * differ between runs).  Asynchronous on the context's stream; allocates scratch of
+ * 96 bytes per body of capacity on first use (synchronises then). */
+int gravity_forces_vjp(gravity_ctx *ctx, double theta, double eps, const double *lambda,
+                       double *grad_pos);
+
+/* Reverse pass (adjoint) of leapfrog_step, kick-drift-kick, over one checkpointed
+ * segment of nsteps steps starting at the saved state (pos0, vel0) (device, (n,3)
+ * FP64, read only).  The segment's positions x_0 .. x_nsteps are recomputed with the
+ * forward kernels (identical results), then, from the last level down, each level k
+ * applies xbar += c_k J(x_k)^T vbar (J = d a / d x on the tree of x_k, decisions
+ * frozen: gravity_forces_vjp) followed by the reverse of the drift before it,
+ * vbar += dt xbar.  c_k = dt/2 at the trajectory's two end levels, dt at interior
+ * levels (two half kicks share one x_k and one vbar).  flags:
+ *   GRAVITY_ADJ_END    the segment ends at the trajectory's final level: that level's
+ *                      half kick is included (on entry xbar, vbar are the cotangents
+ *                      of the final x, v); without it the caller already applied level
+ *                      nsteps (as the first level of the following segment)
+ *   GRAVITY_ADJ_START  the segment starts at the trajectory's initial level: its half
+ *                      kick closes the pass and no drift follows it
+ * Segments are processed from the last to the first; with both flags one call
+ * reverses a whole trajectory.  xbar, vbar: device, (n,3), caller order, updated in
+ * place.  With GRAVITY_ADJ_START they end as the cotangents of (pos0, vel0);
+ * without it the reverse of the drift that produced pos0 is applied too, which is
+ * where the preceding segment's call continues.  p: order 0 and scheme 0 only
+ * (GRAVITY_E_ARG otherwise).  Allocates (nsteps + 1) * 24 bytes per body for the
+ * levels on first use (synchronises then); leaves the tree of pos0 in the context. */
+enum gravity_adjoint_flags { GRAVITY_ADJ_END = 1, GRAVITY_ADJ_START = 2 };
+int leapfrog_adjoint(gravity_ctx *ctx, int64_t n, const double *pos0, const double *vel0,
+                     const double *mass, double dt, int nsteps, double theta, double eps,
+                     const gravity_params *p, int flags, double *xbar, double *vbar);
+
 /* Independent clouds ("batched ensemble"): many separate N-body problems handled
  * by one tree build and one walk launch.  offsets_host (host memory, nclouds + 1
  * int64) gives cloud k as bodies [offsets[k], offsets[k+1]) of the arrays passed

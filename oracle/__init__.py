@@ -72,7 +72,7 @@ def _load():
             lib.orc_tree_export_moments.restype = None
             lib.orc_tree_forces.argtypes = [P, D, D, D, I, I64, P, P, P, P]
             lib.orc_tree_forces.restype = None
-            lib.orc_tree_vjp.argtypes = [P, D, D, D, I, P, P]
+            lib.orc_tree_vjp.argtypes = [P, D, D, D, I, P, P, P]
             lib.orc_tree_vjp.restype = I
             lib.orc_tree_forces_frozen.argtypes = [P, D, D, D, I, P, P]
             lib.orc_tree_forces_frozen.restype = I
@@ -208,15 +208,18 @@ class Tree:
         return acc, absum, counts
 
 
-def tree_vjp(tree: "Tree", lam, theta: float, eps: float, G: float = 1.0, mac_guard: int = 1):
-    """(d acc / d pos)^T lam on the frozen tree (monopole), caller order (n,3)."""
+def tree_vjp(tree: "Tree", lam, theta: float, eps: float, G: float = 1.0, mac_guard: int = 1,
+             with_absum: bool = False):
+    """(d acc / d pos)^T lam on the frozen tree (monopole), caller order (n,3).
+    with_absum: also return per body the sum of |term| magnitudes it takes part in."""
     lam = _f64(lam, 3).reshape(-1, 3)
     grad = np.zeros((tree.n, 3))
+    absum = np.zeros(tree.n) if with_absum else None
     rc = _load().orc_tree_vjp(tree._h, float(theta), float(eps), float(G), int(mac_guard),
-                              _ptr(lam), _ptr(grad))
+                              _ptr(lam), _ptr(grad), _ptr(absum))
     if rc:
         raise OracleError(rc)
-    return grad
+    return (grad, absum) if with_absum else grad
 
 
 def tree_forces_frozen(tree: "Tree", pos_new, theta: float, eps: float, G: float = 1.0,
@@ -294,14 +297,26 @@ def leapfrog_grad(pos0, vel0, mass, xbar, vbar, dt, nsteps, *, theta=0.5, eps=1e
                        mac_guard=mac_guard)
         xs.append(x.copy())
 
+    return leapfrog_reverse(xs, mass, xbar, vbar, dt, theta=theta, eps=eps, G=G,
+                            leaf_max=leaf_max, mac_guard=mac_guard)
+
+
+def leapfrog_reverse(levels, mass, xbar, vbar, dt, *, theta=0.5, eps=1e-3, G=1.0, leaf_max=1,
+                     mac_guard=1):
+    """The reverse pass of leapfrog_grad on given positions levels[0..N] (each (n,3)):
+    xbar += h J(x_N)^T vbar; then for k = N-1 .. 0: vbar += dt xbar (drift of step k),
+    xbar += c_k J(x_k)^T vbar with c_0 = h = dt/2 and c_k = dt otherwise."""
+    mass = _f64(mass).reshape(-1)
+    nsteps = len(levels) - 1
+
     def jt(xn, u):
         return tree_vjp(Tree(xn, mass, leaf_max=leaf_max), u, theta, eps, G, mac_guard)
 
     h = 0.5 * dt
     xb = _f64(xbar, 3).reshape(-1, 3).copy()
     vb = _f64(vbar, 3).reshape(-1, 3).copy()
-    xb += h * jt(xs[nsteps], vb)
+    xb += h * jt(levels[nsteps], vb)
     for k in range(nsteps - 1, -1, -1):
         vb += dt * xb
-        xb += (h if k == 0 else dt) * jt(xs[k], vb)
+        xb += (h if k == 0 else dt) * jt(levels[k], vb)
     return xb, vb

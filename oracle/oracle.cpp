@@ -321,22 +321,27 @@ struct VjpVisitor {
   const WalkCtx &w;
   const double *lam;            // cotangent of body B's acceleration (times G)
   double *gb;                   // gradient of x_B
+  double *ab;                   // sum of |m J u| over B's terms
   std::vector<double> &gnode;   // gradient of node COMs (this target's share)
-  std::vector<std::pair<int64_t, std::array<double, 3>>> &gbody;
+  std::vector<double> &anode;   // sum of |m J u| per node
+  std::vector<std::pair<int64_t, std::array<double, 4>>> &gbody;
   void test() {}
-  void term(const double *src, double m, double *gs) {
+  double term(const double *src, double m, double *gs) {
     double d[3] = {src[0] - w.xb[0], src[1] - w.xb[1], src[2] - w.xb[2]};
     double ju[3];
     jac_times(d, w.eps2, lam, ju);
     for (int a = 0; a < 3; ++a) { gb[a] -= m * ju[a]; gs[a] += m * ju[a]; }
+    double mag = m * std::sqrt((ju[0] * ju[0] + ju[1] * ju[1]) + ju[2] * ju[2]);
+    *ab += mag;
+    return mag;
   }
   void node(int64_t k) {
     const Node &nd = w.t->nodes[k];
-    term(nd.com, nd.m, &gnode[3 * k]);
+    anode[k] += term(nd.com, nd.m, &gnode[3 * k]);
   }
   void body(int64_t j) {
-    std::array<double, 3> gs{0, 0, 0};
-    term(&w.t->x[3 * j], w.t->m[j], gs.data());
+    std::array<double, 4> gs{0, 0, 0, 0};
+    gs[3] = term(&w.t->x[3 * j], w.t->m[j], gs.data());
     gbody.push_back({j, gs});
   }
 };
@@ -519,34 +524,40 @@ void orc_tree_forces(const void *h, double theta, double eps, double G, int mac_
 // Vector-Jacobian product of the tree accelerations (monopole, order 0) with the
 // interaction decisions frozen: grad = (d acc / d pos)^T lambda, both (n,3) in caller
 // order, G applied.  A node COM is sum m_j x_j / M over its bodies, so its gradient
-// reaches each member j as (m_j / M) times the node's share.
+// reaches each member j as (m_j / M) times the node's share.  absum (optional, n)
+// receives for each body the sum of |m J u| over the terms it takes part in (as target,
+// as source body, and its m_j / M share of each node's), the scale of the rounding.
 int orc_tree_vjp(const void *h, double theta, double eps, double G, int mac_guard,
-                 const double *lambda, double *grad) {
+                 const double *lambda, double *grad, double *absum) {
   const Tree *t = (const Tree *)h;
   if (t->order != 0) return ORC_E_ARG;
   const int64_t n = t->n;
-  std::vector<int64_t> inv(n);
-  for (int64_t i = 0; i < n; ++i) inv[t->perm[i]] = i;
   const double theta2 = theta * theta, eps2 = eps * eps;
-  std::vector<double> gs(3 * n, 0.0);                  // sorted order
-  std::vector<double> gnode(3 * t->nodes.size(), 0.0);
+  std::vector<double> gs(3 * n, 0.0), as(n, 0.0);      // sorted order
+  std::vector<double> gnode(3 * t->nodes.size(), 0.0), anode(t->nodes.size(), 0.0);
   for (int64_t ib = 0; ib < n; ++ib) {
     int64_t ci = t->perm[ib];
     double lam[3] = {G * lambda[3 * ci], G * lambda[3 * ci + 1], G * lambda[3 * ci + 2]};
     WalkCtx w{t, theta2, eps2, mac_guard, ib, &t->x[3 * ib]};
-    std::vector<std::pair<int64_t, std::array<double, 3>>> gbody;
-    VjpVisitor v{w, lam, &gs[3 * ib], gnode, gbody};
+    std::vector<std::pair<int64_t, std::array<double, 4>>> gbody;
+    VjpVisitor v{w, lam, &gs[3 * ib], &as[ib], gnode, anode, gbody};
     decide_rec(w, 0, v);
-    for (auto &p : gbody)
+    for (auto &p : gbody) {
       for (int a = 0; a < 3; ++a) gs[3 * p.first + a] += p.second[a];
+      as[p.first] += p.second[3];
+    }
   }
   for (size_t k = 0; k < t->nodes.size(); ++k) {
     const Node &nd = t->nodes[k];
-    for (int64_t j = nd.begin; j < nd.end; ++j)
+    for (int64_t j = nd.begin; j < nd.end; ++j) {
       for (int a = 0; a < 3; ++a) gs[3 * j + a] += (t->m[j] / nd.m) * gnode[3 * k + a];
+      as[j] += (t->m[j] / nd.m) * anode[k];
+    }
   }
-  for (int64_t ib = 0; ib < n; ++ib)
+  for (int64_t ib = 0; ib < n; ++ib) {
     for (int a = 0; a < 3; ++a) grad[3 * t->perm[ib] + a] = gs[3 * ib + a];
+    if (absum) absum[t->perm[ib]] = as[ib];
+  }
   return ORC_OK;
 }
 

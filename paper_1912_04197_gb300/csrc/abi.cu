@@ -25,6 +25,20 @@ int cuda_status(cudaError_t e) {
   return GRAVITY_E_CUDA;
 }
 
+// One step of leapfrog_step (the kernels it enqueues, in order): kick-drift, tree
+// build at the new positions, walk with the closing kick fused (KDK) or plain (Euler).
+int integrate_one(Ctx &c, int64_t n, double *pos, double *vel, const double *mass,
+                  double *acc, double dt, double theta, double eps) {
+  const bool kdk = c.params.scheme == 0;
+  const double h_kick = kdk ? 0.5 * dt : dt;
+  int r = launch_kick_drift(&c, n, pos, vel, acc, h_kick, dt);
+  if (r) return r;
+  c.n = n;
+  if ((r = tree_build(&c, n, pos, mass))) return r;
+  c.have_tree = true;
+  return walk_forces(&c, theta, eps, acc, nullptr, kdk ? vel : nullptr, kdk ? h_kick : 0.0);
+}
+
 namespace {
 
 template <typename T>
@@ -222,6 +236,8 @@ int gravity_destroy(gravity_ctx *h) {
   grav::free_ptr(c.walk_stats);
   grav::free_ptr(c.walk_gstack);
   grav::free_ptr(c.walk_queues);
+  grav::free_ptr(c.vjp_own); grav::free_ptr(c.vjp_body); grav::free_ptr(c.vjp_node);
+  grav::free_ptr(c.adj_levels); grav::free_ptr(c.adj_work);
   if (c.graph.exec) cudaGraphExecDestroy(c.graph.exec);
   grav::free_ptr(c.d_status);
   grav::free_ptr(c.dir_hi); grav::free_ptr(c.dir_lo);
@@ -278,6 +294,20 @@ int gravity_forces_counted(gravity_ctx *h, double theta, double eps, double *acc
   return forces_common(h, theta, eps, acc, counts);
 }
 
+int gravity_forces_vjp(gravity_ctx *h, double theta, double eps, const double *lambda,
+                       double *grad_pos) {
+  if (!h || !(theta >= 0.0) || !(eps >= 0.0) || !std::isfinite(theta) || !std::isfinite(eps))
+    return GRAVITY_E_ARG;
+  Ctx &c = h->c;
+  if (!c.have_tree) return GRAVITY_E_NOTREE;
+  if (c.params.order != 0) return GRAVITY_E_ARG;
+  if (c.n == 0) return GRAVITY_OK;
+  if (!lambda || !grad_pos) return GRAVITY_E_ARG;
+  int rc = grav::set_device(c);
+  if (rc) return rc;
+  return grav::walk_vjp(&c, theta, eps, lambda, grad_pos);
+}
+
 int gravity_direct(gravity_ctx *h, int64_t n, const double *pos, const double *mass, double eps,
                    double G, double *acc) {
   if (!h || n < 0 || !(eps >= 0.0) || !std::isfinite(eps) || !std::isfinite(G))
@@ -304,16 +334,8 @@ int leapfrog_step(gravity_ctx *h, int64_t n, double *pos, double *vel, const dou
   if (p) c.params = *p; else gravity_params_default(&c.params);
   if ((rc = grav::set_device(c))) return rc;
   if ((rc = grav::ensure_capacity(&c, n))) return rc;
-  const bool kdk = c.params.scheme == 0;
-  const double h_kick = kdk ? 0.5 * dt : dt;
   auto one_step = [&]() -> int {
-    int r = grav::launch_kick_drift(&c, n, pos, vel, acc_cache, h_kick, dt);
-    if (r) return r;
-    c.n = n;
-    if ((r = grav::tree_build(&c, n, pos, mass))) return r;
-    c.have_tree = true;
-    return grav::walk_forces(&c, theta, eps, acc_cache, nullptr, kdk ? vel : nullptr,
-                             kdk ? h_kick : 0.0);
+    return grav::integrate_one(c, n, pos, vel, mass, acc_cache, dt, theta, eps);
   };
   // The first step runs eagerly (it sizes every buffer); later steps replay a
   // CUDA graph of one step captured on the caller's stream when graphs are enabled.
@@ -354,6 +376,74 @@ int leapfrog_step(gravity_ctx *h, int64_t n, double *pos, double *vel, const dou
     } else if ((rc = one_step())) {
       return rc;
     }
+  }
+  return GRAVITY_OK;
+}
+
+int leapfrog_adjoint(gravity_ctx *h, int64_t n, const double *pos0, const double *vel0,
+                     const double *mass, double dt, int nsteps, double theta, double eps,
+                     const gravity_params *p, int flags, double *xbar, double *vbar) {
+  if (!h || n < 0 || n > grav::kMaxBodies || nsteps < 0 || !std::isfinite(dt)) return GRAVITY_E_ARG;
+  if (!(theta >= 0.0) || !(eps >= 0.0) || !std::isfinite(theta) || !std::isfinite(eps))
+    return GRAVITY_E_ARG;
+  if (flags & ~(GRAVITY_ADJ_END | GRAVITY_ADJ_START)) return GRAVITY_E_ARG;
+  int rc = grav::check_params(p);
+  if (rc) return rc;
+  gravity_params q;
+  if (p) q = *p; else gravity_params_default(&q);
+  if (q.order != 0 || q.scheme != 0) return GRAVITY_E_ARG;
+  if (n == 0) return GRAVITY_OK;
+  if (!pos0 || !vel0 || !mass || !xbar || !vbar) return GRAVITY_E_ARG;
+  Ctx &c = h->c;
+  if (c.seg.nseg > 1 && n != c.seg.n) return GRAVITY_E_ARG;
+  c.params = q;
+  if ((rc = grav::set_device(c))) return rc;
+  if ((rc = grav::ensure_capacity(&c, n))) return rc;
+  const int64_t n3 = 3 * n;
+  const int64_t lev_need = n3 * (int64_t)(nsteps + 1);
+  if (c.adj_levels_cap < lev_need || c.adj_work_cap < 3 * n3) {
+    GRAV_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    if (c.adj_levels_cap < lev_need) {
+      grav::free_ptr(c.adj_levels);
+      c.adj_levels_cap = 0;
+      GRAV_CUDA_TRY(cudaMalloc(&c.adj_levels, sizeof(double) * lev_need));
+      c.adj_levels_cap = lev_need;
+    }
+    if (c.adj_work_cap < 3 * n3) {
+      grav::free_ptr(c.adj_work);
+      c.adj_work_cap = 0;
+      GRAV_CUDA_TRY(cudaMalloc(&c.adj_work, sizeof(double) * 3 * n3));
+      c.adj_work_cap = 3 * n3;
+    }
+  }
+  double *vel = c.adj_work, *acc = c.adj_work + n3, *g = c.adj_work + 2 * n3;
+  auto level = [&](int k) { return c.adj_levels + n3 * (int64_t)k; };
+  // recompute the segment's levels from the checkpoint with the forward kernels
+  GRAV_CUDA_TRY(cudaMemcpyAsync(level(0), pos0, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c.stream));
+  GRAV_CUDA_TRY(cudaMemcpyAsync(vel, vel0, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c.stream));
+  c.n = n;
+  if ((rc = grav::tree_build(&c, n, level(0), mass))) return rc;
+  c.have_tree = true;
+  if ((rc = grav::walk_forces(&c, theta, eps, acc, nullptr, nullptr, 0.0))) return rc;
+  const int last = (flags & GRAVITY_ADJ_END) ? nsteps : nsteps - 1;
+  for (int k = 0; k < last; ++k) {
+    GRAV_CUDA_TRY(cudaMemcpyAsync(level(k + 1), level(k), sizeof(double) * n3,
+                                  cudaMemcpyDeviceToDevice, c.stream));
+    if ((rc = grav::integrate_one(c, n, level(k + 1), vel, mass, acc, dt, theta, eps))) return rc;
+  }
+  // reverse: level k takes xbar += c_k J(x_k)^T vbar, then the drift before it
+  const double hk = 0.5 * dt;
+  for (int k = last; k >= 0; --k) {
+    const bool top = k == nsteps;                    // only with GRAVITY_ADJ_END
+    const bool first = k == 0 && (flags & GRAVITY_ADJ_START);
+    if (k != last) {                                 // the tree is at level `last` already
+      c.n = n;
+      if ((rc = grav::tree_build(&c, n, level(k), mass))) return rc;
+      c.have_tree = true;
+    }
+    if ((rc = grav::walk_vjp(&c, theta, eps, vbar, g))) return rc;
+    const double coef = (top || first) ? hk : dt;
+    if ((rc = grav::launch_adjoint_kick_drift(&c, n, xbar, vbar, g, coef, dt, !first))) return rc;
   }
   return GRAVITY_OK;
 }

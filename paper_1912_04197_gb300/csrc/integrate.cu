@@ -22,7 +22,29 @@ __global__ void k_kick(int64_t n3, double *__restrict__ vel, const double *__res
   vel[i] = __dadd_rn(vel[i], __dmul_rn(h, acc[i]));
 }
 
+// Reverse of one time level of the leapfrog: xbar += c g (g = J(x)^T vbar from the
+// vector-Jacobian product), then, unless this is the trajectory's first level, the
+// reverse of the drift before it: vbar += dt xbar.
+__global__ void k_adjoint_kick_drift(int64_t n3, double *__restrict__ xbar,
+                                     double *__restrict__ vbar, const double *__restrict__ g,
+                                     double c, double dt, int drift) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n3) return;
+  const double xb = __dadd_rn(xbar[i], __dmul_rn(c, g[i]));
+  xbar[i] = xb;
+  if (drift) vbar[i] = __dadd_rn(vbar[i], __dmul_rn(dt, xb));
+}
+
 }  // namespace
+
+int launch_adjoint_kick_drift(Ctx *c, int64_t n, double *xbar, double *vbar, const double *g,
+                              double coef, double dt, bool drift) {
+  int64_t n3 = 3 * n;
+  k_adjoint_kick_drift<<<(unsigned)((n3 + 255) / 256), 256, 0, c->stream>>>(n3, xbar, vbar, g,
+                                                                           coef, dt, drift ? 1 : 0);
+  ++c->launches;
+  return cuda_status(cudaGetLastError());
+}
 
 int launch_kick_drift(Ctx *c, int64_t n, double *pos, double *vel, const double *acc,
                       double h_kick, double dt) {

@@ -103,6 +103,13 @@ struct Ctx {
   void *walk_gstack = nullptr;                // walk stack overflow, per persistent warp
   unsigned *walk_queues = nullptr;            // walk task-queue counters, one per SM
   size_t walk_gstack_cap = 0;                 // in 8-byte entries
+  // vector-Jacobian product scratch (sorted order; nodes 2 cap)
+  double *vjp_own = nullptr, *vjp_body = nullptr, *vjp_node = nullptr;
+  int64_t vjp_cap = 0;
+  // leapfrog adjoint: positions of the recomputed levels, velocity, acceleration
+  // and product work arrays
+  double *adj_levels = nullptr, *adj_work = nullptr;
+  int64_t adj_levels_cap = 0, adj_work_cap = 0;   // in doubles
   Tree t;
   // direct-sum staging (caller order hi/lo)
   float4 *dir_hi = nullptr, *dir_lo = nullptr;
@@ -117,6 +124,7 @@ int tree_build(Ctx *c, int64_t n, const double *pos, const double *mass);
 // ---- launchers (walk.cu)
 int walk_forces(Ctx *c, double theta, double eps, double *acc, int32_t *counts,
                 double *vel, double kick);
+int walk_vjp(Ctx *c, double theta, double eps, const double *lambda, double *grad);
 // ---- launchers (direct.cu)
 int direct_forces(Ctx *c, int64_t n, const double *pos, const double *mass, double eps,
                   double G, double *acc);
@@ -124,6 +132,8 @@ int direct_forces(Ctx *c, int64_t n, const double *pos, const double *mass, doub
 int launch_kick_drift(Ctx *c, int64_t n, double *pos, double *vel, const double *acc,
                       double h_kick, double dt);
 int launch_kick(Ctx *c, int64_t n, double *vel, const double *acc, double h_kick);
+int launch_adjoint_kick_drift(Ctx *c, int64_t n, double *xbar, double *vbar, const double *g,
+                              double coef, double dt, bool drift);
 
 // ---- probe.cu
 int probe_fp32(Ctx *c, int64_t iters, double *ms, double *flops);

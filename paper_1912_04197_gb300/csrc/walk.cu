@@ -58,6 +58,8 @@ constexpr int kCntShift = 25;                  // 6-bit (count - 1)
 // the timed path): batches, items, mixed nodes, FP64 decisions, point-list entries,
 // node-term entries, deepest stack, lane-terms evaluated by active lanes, lockstep
 // iterations of lists split by 16 / 8 / 1 lanes, full-mask entries, far entries.
+enum { kModeForce = 0, kModeCount = 1, kModeVjp = 2 };
+
 enum { kStatBatches, kStatItems, kStatMixed, kStatFp64, kStatMono, kStatQuad, kStatMaxSp,
        kStatLaneTerms, kStatSplit2, kStatSplit4, kStatSplit32, kStatFull, kStatFar,
        kStatCount = 16 };
@@ -69,7 +71,16 @@ struct WarpSmem {
   float4 lb[kListCap];            //             (x_lo, y_lo, z_lo, lane mask bits)
   float4 fa[kListCap];            // far list:   (c_rel xyz, m)
   float4 fc[kListCap];            //             (q_xz, q_yz, lane mask bits, 0)
-  int32_t ltag[kListCap];         // counting: -1 node term, else sorted body index
+  int32_t ltag[kListCap];         // counting / VJP: -(node+1) node term, else sorted body index
+};
+
+// Vector-Jacobian product (order 0): far-list sources and the lane-to-source
+// transposition buffer (chunks of kVjpChunk entries, rows padded to 33 floats).
+constexpr int kVjpChunk = 8;
+struct WarpSmemV {
+  WarpSmem base;
+  int32_t ftag[kListCap];         // node of each far entry
+  float vt[3][kVjpChunk][33];     // per component, entry and lane: the term's gradient
 };
 
 struct WarpSmemQ {
@@ -110,6 +121,10 @@ struct WalkArgs {
   const int32_t *task_end;
   const int32_t *task_seg;
   unsigned long long *stats;      // counted variant only
+  const double *lambda;           // VJP: cotangent of the accelerations, caller order (n,3)
+  double *g_own;                  // VJP: gradient of each body from its own terms, sorted order
+  double *g_body;                 // VJP: gradient scattered to body sources, sorted order
+  double *g_node;                 // VJP: gradient scattered to node COMs
 };
 
 __device__ __forceinline__ int warp_incl_scan_i(int v, int lane) {
@@ -248,6 +263,73 @@ __device__ __forceinline__ void flush_near(const WarpSmemQ &S, int cnt, int lane
   }
 }
 
+// Vector-Jacobian product of the monopole terms of a point (FAR = false) or far
+// list.  A term a_i += m f(d), f(d) = d (|d|^2 + eps^2)^{-3/2}, d = s - x_i, with
+// cotangent u_i gives w = m J(d) u_i, J = (I - 3 d d^T / r^2) / r^3 (symmetric):
+// the body's own gradient takes -w (the sum over the list is returned in p*), the
+// source s (a body, or a node whose COM moves with its bodies) takes +w.  The +w of
+// the 32 lanes are summed per entry through shared memory (one lane per entry and
+// component) and added with one FP64 atomic per entry and component.  The point
+// list's own-body entry is skipped: its term does not depend on x_i.
+template <bool FAR, bool EPS0>
+__device__ __forceinline__ void flush_vjp(WarpSmemV &V, int cnt, int lane, float xh, float yh,
+                                          float zh, float xl, float yl, float zl, float xr,
+                                          float yr, float zr, float eps2, float ux, float uy,
+                                          float uz, int gi, float &px, float &py, float &pz,
+                                          double *g_body, double *g_node) {
+  const WarpSmem &S = V.base;
+  px = py = pz = 0.f;
+  for (int c0 = 0; c0 < cnt; c0 += kVjpChunk) {
+    const int ce = min(kVjpChunk, cnt - c0);
+#pragma unroll
+    for (int e = 0; e < kVjpChunk; ++e) {
+      if (e < ce) {
+        const int k = c0 + e;
+        float dx, dy, dz, m;
+        bool act;
+        if (FAR) {
+          const float4 a = S.fa[k], c = S.fc[k];
+          act = (__float_as_uint(c.z) >> lane) & 1u;
+          dx = a.x - xr; dy = a.y - yr; dz = a.z - zr; m = a.w;
+        } else {
+          const float4 a = S.la[k], b = S.lb[k];
+          act = ((__float_as_uint(b.w) >> lane) & 1u) && S.ltag[k] != gi;
+          dx = (a.x - xh) + (b.x - xl);
+          dy = (a.y - yh) + (b.y - yl);
+          dz = (a.z - zh) + (b.z - zl);
+          m = a.w;
+        }
+        const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+        const float inv = inv_r<EPS0>(r2, act);
+        const float inv2 = inv * inv;
+        const float s = m * (inv2 * inv);
+        const float c3 = 3.f * fmaf(dx, ux, fmaf(dy, uy, dz * uz)) * inv2;
+        const float wx = s * fmaf(-c3, dx, ux);
+        const float wy = s * fmaf(-c3, dy, uy);
+        const float wz = s * fmaf(-c3, dz, uz);
+        px += wx; py += wy; pz += wz;
+        V.vt[0][e][lane] = wx;
+        V.vt[1][e][lane] = wy;
+        V.vt[2][e][lane] = wz;
+      }
+    }
+    __syncwarp();
+    const int e = lane & (kVjpChunk - 1), comp = lane / kVjpChunk;
+    if (comp < 3 && e < ce) {
+      float sum = 0.f;
+#pragma unroll 8
+      for (int j = 0; j < 32; ++j) sum += V.vt[comp][e][j];
+      if (sum != 0.f) {
+        const int tag = FAR ? V.ftag[c0 + e] : S.ltag[c0 + e];
+        double *dst = (!FAR && tag >= 0) ? g_body + 3 * (int64_t)tag
+                                         : g_node + 3 * (int64_t)(FAR ? tag : -tag - 1);
+        atomicAdd(dst + comp, (double)sum);
+      }
+    }
+    __syncwarp();
+  }
+}
+
 // Counted variant only: lockstep iteration counts of lane-group-split lists.
 __device__ __forceinline__ void split_costs(const float4 *m4, int comp, int cnt, int lane,
                                             unsigned long long *st) {
@@ -288,10 +370,14 @@ struct Stack {
   }
 };
 
-template <int ORDER, bool EPS0, bool COUNT>
+template <int ORDER, bool EPS0, int MODE>
 __global__ void __launch_bounds__(32 * kWalkWarps)
 k_walk(WalkArgs A) {
-  using Smem = typename std::conditional<ORDER == 2, WarpSmemQ, WarpSmem>::type;
+  constexpr bool COUNT = MODE == kModeCount;
+  constexpr bool VJP = MODE == kModeVjp;
+  static_assert(!VJP || ORDER == 0, "the vector-Jacobian product covers monopole terms");
+  using Smem = typename std::conditional<
+      ORDER == 2, WarpSmemQ, typename std::conditional<VJP, WarpSmemV, WarpSmem>::type>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
@@ -340,6 +426,13 @@ k_walk(WalkArgs A) {
     if (valid) {
       const float4 h = A.bhi[gi], l = A.blo[gi];
       xh = h.x; yh = h.y; zh = h.z; xl = l.x; yl = l.y; zl = l.z;
+    }
+    float ux = 0.f, uy = 0.f, uz = 0.f;       // VJP: cotangent of this body's acceleration, x G
+    if (VJP && valid) {
+      const int64_t ci = A.perm[gi];
+      ux = (float)(A.G * A.lambda[3 * ci]);
+      uy = (float)(A.G * A.lambda[3 * ci + 1]);
+      uz = (float)(A.G * A.lambda[3 * ci + 2]);
     }
     // warp origin = lane 0's body (always valid); warp-relative FP32 coordinates
     const float ohx = __shfl_sync(0xffffffffu, xh, 0), ohy = __shfl_sync(0xffffffffu, yh, 0),
@@ -535,7 +628,7 @@ k_walk(WalkArgs A) {
           const int p = npt + __popc(bm & ((1u << lane) - 1u));
           M.la[p] = r0;
           M.lb[p] = make_float4(r1.x, r1.y, r1.z, __uint_as_float(accm));
-          if (COUNT) M.ltag[p] = single ? tp.z : -1;
+          if (COUNT || VJP) M.ltag[p] = single ? tp.z : -(item + 1);
         }
         npt += __popc(bm);
       }
@@ -547,6 +640,7 @@ k_walk(WalkArgs A) {
           const float cy = (r0.y - ohy) + (r1.y - oly);
           const float cz = (r0.z - ohz) + (r1.z - olz);
           M.fa[p] = make_float4(cx, cy, cz, r0.w);
+          if constexpr (VJP) S.ftag[p] = item;
           if constexpr (ORDER == 2) {
             S.fb[p] = q0;
             M.fc[p] = make_float4(q1.x, q1.y, __uint_as_float(accm), 0.f);
@@ -605,8 +699,12 @@ k_walk(WalkArgs A) {
       if (npt >= A.flush_at) {
         if (COUNT) { w_mono += npt; split_costs(M.lb, 3, npt, lane, w_split); }
         float px, py, pz;
-        flush_point<EPS0, COUNT>(M, npt, lane, xh, yh, zh, xl, yl, zl, eps2, px, py, pz, gi,
-                                 c_m2p, c_p2p);
+        if constexpr (VJP)
+          flush_vjp<false, EPS0>(S, npt, lane, xh, yh, zh, xl, yl, zl, xr, yr, zr, eps2, ux, uy, uz,
+                                 gi, px, py, pz, A.g_body, A.g_node);
+        else
+          flush_point<EPS0, COUNT>(M, npt, lane, xh, yh, zh, xl, yl, zl, eps2, px, py, pz, gi,
+                                   c_m2p, c_p2p);
         acc.add(acc64, px, py, pz);
         npt = 0;
         __syncwarp();
@@ -614,7 +712,11 @@ k_walk(WalkArgs A) {
       if (nfar >= A.flush_at) {
         if (COUNT) { w_quad += nfar; split_costs(M.fc, 2, nfar, lane, w_split); }
         float px, py, pz;
-        flush_far<ORDER, EPS0, COUNT>(&S, nfar, lane, xr, yr, zr, eps2, px, py, pz, c_m2p);
+        if constexpr (VJP)
+          flush_vjp<true, EPS0>(S, nfar, lane, xh, yh, zh, xl, yl, zl, xr, yr, zr, eps2, ux, uy, uz,
+                                gi, px, py, pz, A.g_body, A.g_node);
+        else
+          flush_far<ORDER, EPS0, COUNT>(&S, nfar, lane, xr, yr, zr, eps2, px, py, pz, c_m2p);
         acc.add(acc64, px, py, pz);
         nfar = 0;
         __syncwarp();
@@ -640,12 +742,20 @@ k_walk(WalkArgs A) {
       }
       float px, py, pz;
       if (npt > 0) {
-        flush_point<EPS0, COUNT>(M, npt, lane, xh, yh, zh, xl, yl, zl, eps2, px, py, pz, gi,
-                                 c_m2p, c_p2p);
+        if constexpr (VJP)
+          flush_vjp<false, EPS0>(S, npt, lane, xh, yh, zh, xl, yl, zl, xr, yr, zr, eps2, ux, uy, uz,
+                                 gi, px, py, pz, A.g_body, A.g_node);
+        else
+          flush_point<EPS0, COUNT>(M, npt, lane, xh, yh, zh, xl, yl, zl, eps2, px, py, pz, gi,
+                                   c_m2p, c_p2p);
         acc.add(acc64, px, py, pz);
       }
       if (nfar > 0) {
-        flush_far<ORDER, EPS0, COUNT>(&S, nfar, lane, xr, yr, zr, eps2, px, py, pz, c_m2p);
+        if constexpr (VJP)
+          flush_vjp<true, EPS0>(S, nfar, lane, xh, yh, zh, xl, yl, zl, xr, yr, zr, eps2, ux, uy, uz,
+                                gi, px, py, pz, A.g_body, A.g_node);
+        else
+          flush_far<ORDER, EPS0, COUNT>(&S, nfar, lane, xr, yr, zr, eps2, px, py, pz, c_m2p);
         acc.add(acc64, px, py, pz);
       }
       if constexpr (ORDER == 2) {
@@ -674,7 +784,14 @@ k_walk(WalkArgs A) {
         atomicAdd(&A.stats[kStatFar], w_far);
       }
     }
-    if (valid) {
+    if (VJP && valid) {                         // own-term gradient, sorted order
+      double gx, gy, gz;
+      acc.get(acc64, gx, gy, gz);
+      A.g_own[3 * gi] = -gx;
+      A.g_own[3 * gi + 1] = -gy;
+      A.g_own[3 * gi + 2] = -gz;
+    }
+    if (!VJP && valid) {
       double ax, ay, az;
       acc.get(acc64, ax, ay, az);
       ax *= A.G; ay *= A.G; az *= A.G;
@@ -696,11 +813,13 @@ k_walk(WalkArgs A) {
   }
 }
 
-template <int ORDER, bool EPS0, bool COUNT>
+template <int ORDER, bool EPS0, int MODE>
 int launch_walk(Ctx *c, WalkArgs A) {
-  using Smem = typename std::conditional<ORDER == 2, WarpSmemQ, WarpSmem>::type;
+  using Smem = typename std::conditional<
+      ORDER == 2, WarpSmemQ,
+      typename std::conditional<MODE == kModeVjp, WarpSmemV, WarpSmem>::type>::type;
   const size_t smem = sizeof(Smem) * kWalkWarps;
-  auto kern = k_walk<ORDER, EPS0, COUNT>;
+  auto kern = k_walk<ORDER, EPS0, MODE>;
   static int blocks_per_sm[64] = {0};
   const int dev = c->device < 64 ? c->device : 63;
   if (blocks_per_sm[dev] == 0) {
@@ -779,11 +898,109 @@ int walk_forces(Ctx *c, double theta, double eps, double *acc, int32_t *counts, 
   const bool q = c->params.order == 2;
   const bool e0 = !(A.eps2 > 0.f);
   if (counts) {
-    if (q) return e0 ? launch_walk<2, true, true>(c, A) : launch_walk<2, false, true>(c, A);
-    return e0 ? launch_walk<0, true, true>(c, A) : launch_walk<0, false, true>(c, A);
+    if (q) return e0 ? launch_walk<2, true, kModeCount>(c, A) : launch_walk<2, false, kModeCount>(c, A);
+    return e0 ? launch_walk<0, true, kModeCount>(c, A) : launch_walk<0, false, kModeCount>(c, A);
   }
-  if (q) return e0 ? launch_walk<2, true, false>(c, A) : launch_walk<2, false, false>(c, A);
-  return e0 ? launch_walk<0, true, false>(c, A) : launch_walk<0, false, false>(c, A);
+  if (q) return e0 ? launch_walk<2, true, kModeForce>(c, A) : launch_walk<2, false, kModeForce>(c, A);
+  return e0 ? launch_walk<0, true, kModeForce>(c, A) : launch_walk<0, false, kModeForce>(c, A);
+}
+
+namespace {
+
+// Closing pass of the vector-Jacobian product: a node COM is sum_j m_j x_j / M over
+// its bodies, so the gradient scattered to a node reaches each of its bodies j as
+// (m_j / M) g_node.  One thread per leaf sums g_node / M along the leaf's ancestor
+// chain and writes, for each of its bodies, own + body-source + m_j * that sum in
+// caller order.
+__global__ void k_vjp_finish(const int4 *__restrict__ topo, const int32_t *__restrict__ nparent,
+                             const double *__restrict__ nmass, const int32_t *__restrict__ nnodes,
+                             const double *__restrict__ mass_s, const uint32_t *__restrict__ perm,
+                             const double *__restrict__ g_own, const double *__restrict__ g_body,
+                             const double *__restrict__ g_node, double *__restrict__ grad,
+                             int64_t node_cap, unsigned *status) {
+  const int64_t nn = *nnodes;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nn && k < node_cap;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int4 tp = topo[k];
+    if (tp.x >= 0) continue;                  // leaves only
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    int a = (int)k, guard = 0;
+    for (; a >= 0 && guard < 4 * kLevels + 8; a = nparent[a], ++guard) {
+      const double M = nmass[a];
+      if (M > 0.0) {
+        sx = __dadd_rn(sx, __ddiv_rn(g_node[3 * (int64_t)a], M));
+        sy = __dadd_rn(sy, __ddiv_rn(g_node[3 * (int64_t)a + 1], M));
+        sz = __dadd_rn(sz, __ddiv_rn(g_node[3 * (int64_t)a + 2], M));
+      }
+    }
+    if (a >= 0) { latch_error(status, kErrTree); continue; }
+    for (int j = tp.z; j < tp.w; ++j) {
+      const double m = mass_s[j];
+      const int64_t ci = perm[j];
+      grad[3 * ci] = g_own[3 * (int64_t)j] + g_body[3 * (int64_t)j] + m * sx;
+      grad[3 * ci + 1] = g_own[3 * (int64_t)j + 1] + g_body[3 * (int64_t)j + 1] + m * sy;
+      grad[3 * ci + 2] = g_own[3 * (int64_t)j + 2] + g_body[3 * (int64_t)j + 2] + m * sz;
+    }
+  }
+}
+
+}  // namespace
+
+int walk_vjp(Ctx *c, double theta, double eps, const double *lambda, double *grad) {
+  Tree &t = c->t;
+  const int64_t n = c->n;
+  const int64_t node_cap = 2 * c->cap;
+  if (c->vjp_cap < c->cap) {
+    GRAV_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (c->vjp_own) cudaFree(c->vjp_own);
+    if (c->vjp_body) cudaFree(c->vjp_body);
+    if (c->vjp_node) cudaFree(c->vjp_node);
+    c->vjp_own = c->vjp_body = c->vjp_node = nullptr;
+    c->vjp_cap = 0;
+    GRAV_CUDA_TRY(cudaMalloc(&c->vjp_own, sizeof(double) * 3 * c->cap));
+    GRAV_CUDA_TRY(cudaMalloc(&c->vjp_body, sizeof(double) * 3 * c->cap));
+    GRAV_CUDA_TRY(cudaMalloc(&c->vjp_node, sizeof(double) * 3 * node_cap));
+    c->vjp_cap = c->cap;
+  }
+  GRAV_CUDA_TRY(cudaMemsetAsync(c->vjp_body, 0, sizeof(double) * 3 * n, c->stream));
+  GRAV_CUDA_TRY(cudaMemsetAsync(c->vjp_node, 0, sizeof(double) * 3 * 2 * n, c->stream));
+  WalkArgs A{};
+  A.bhi = t.body_hi; A.blo = t.body_lo; A.pos_s = t.pos_s;
+  A.rec0 = t.nrec0; A.rec1 = t.nrec1; A.quadf = t.nquadf;
+  A.topo = t.topo; A.ndepth = t.ndepth; A.ncom = t.ncom; A.geom = t.geom;
+  A.perm = t.idx; A.nnodes = t.nnodes;
+  A.n = (int)n;
+  if (c->seg.nseg > 1) {
+    A.ntasks = c->seg.ntasks;
+    A.task_begin = c->seg.task_begin;
+    A.task_end = c->seg.task_end;
+    A.task_seg = c->seg.task_seg;
+  } else {
+    A.ntasks = (int)((n + 31) / 32);
+  }
+  A.theta2d = theta * theta;
+  A.theta2f = (float)(theta * theta);
+  A.eps2 = (float)(eps * eps);
+  A.G = c->params.G;
+  A.mac_guard = c->params.mac_guard;
+  A.acc64 = c->params.accum == 1;
+  A.status = c->d_status;
+  A.max_iter = (int)(8 * n + 64);
+  A.task_counter = c->walk_queues;
+  A.lambda = lambda;
+  A.g_own = c->vjp_own; A.g_body = c->vjp_body; A.g_node = c->vjp_node;
+  const bool e0 = !(A.eps2 > 0.f);
+  int rc = e0 ? launch_walk<0, true, kModeVjp>(c, A) : launch_walk<0, false, kModeVjp>(c, A);
+  if (rc) return rc;
+  const int threads = 256;
+  int64_t blocks = (2 * n + threads - 1) / threads;
+  if (blocks > 8 * (int64_t)c->num_sms) blocks = 8 * (int64_t)c->num_sms;
+  if (blocks < 1) blocks = 1;
+  k_vjp_finish<<<(int)blocks, threads, 0, c->stream>>>(t.topo, t.nparent, t.nmass, t.nnodes,
+                                                       t.mass_s, t.idx, c->vjp_own, c->vjp_body,
+                                                       c->vjp_node, grad, node_cap, c->d_status);
+  ++c->launches;
+  return cuda_status(cudaGetLastError());
 }
 
 }  // namespace grav

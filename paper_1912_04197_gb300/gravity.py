@@ -23,6 +23,8 @@ GRAVITY_E_CUDA = -4
 GRAVITY_E_TIMEOUT = -5
 GRAVITY_E_INTERNAL = -6
 GRAVITY_E_NOTREE = -7
+GRAVITY_ADJ_END = 1
+GRAVITY_ADJ_START = 2
 
 DBG_ROOT, DBG_KEYS, DBG_PERM, DBG_NNODES, DBG_TOPO, DBG_DEPTH, DBG_PARENT, DBG_MASS, DBG_COM, \
     DBG_QUAD, DBG_WALKSTATS = range(11)
@@ -56,8 +58,10 @@ def _load() -> ctypes.CDLL:
         "gravity_tree_build": (I, [P, I64, P, P, PP]),
         "gravity_forces": (I, [P, D, D, P]),
         "gravity_forces_counted": (I, [P, D, D, P, P]),
+        "gravity_forces_vjp": (I, [P, D, D, P, P]),
         "gravity_direct": (I, [P, I64, P, P, D, D, P]),
         "leapfrog_step": (I, [P, I64, P, P, P, P, D, I, D, D, PP]),
+        "leapfrog_adjoint": (I, [P, I64, P, P, P, D, I, D, D, PP, I, P, P]),
         "gravity_forces_host": (I, [P, I64, P, P, D, D, PP, P]),
         "gravity_sync": (I, [P]),
         "gravity_debug_export": (I, [P, I, P, ctypes.c_size_t]),
@@ -196,6 +200,14 @@ def gravity_forces_counted(ctx: Context, theta: float, eps: float, acc: torch.Te
     return acc
 
 
+def gravity_forces_vjp(ctx: Context, theta: float, eps: float, lam: torch.Tensor,
+                       grad: torch.Tensor) -> torch.Tensor:
+    """grad = (d acc / d pos)^T lam on the current tree's frozen decisions (order 0)."""
+    _check(_lib.gravity_forces_vjp(ctx.handle, float(theta), float(eps), _dev(lam, "lambda", 3),
+                                   _dev(grad, "grad", 3)), "gravity_forces_vjp")
+    return grad
+
+
 def gravity_direct(ctx: Context, pos, mass, eps: float, G: float, acc) -> torch.Tensor:
     _check(_lib.gravity_direct(ctx.handle, pos.shape[0], _dev(pos, "pos", 3), _dev(mass, "mass"),
                                float(eps), float(G), _dev(acc, "acc", 3)), "gravity_direct")
@@ -216,6 +228,16 @@ def leapfrog_step(ctx: Context, pos, vel, mass, acc_cache, dt: float, nsteps: in
                               _dev(mass, "mass"), _dev(acc_cache, "acc_cache", 3), float(dt),
                               int(nsteps), float(theta), float(eps),
                               None if p is None else ctypes.byref(p)), "leapfrog_step")
+
+
+def leapfrog_adjoint(ctx: Context, pos0, vel0, mass, dt: float, nsteps: int, theta: float,
+                     eps: float, p, flags: int, xbar, vbar):
+    """Reverse pass of a checkpointed leapfrog segment; xbar, vbar updated in place."""
+    _check(_lib.leapfrog_adjoint(ctx.handle, pos0.shape[0], _dev(pos0, "pos0", 3),
+                                 _dev(vel0, "vel0", 3), _dev(mass, "mass"), float(dt), int(nsteps),
+                                 float(theta), float(eps), None if p is None else ctypes.byref(p),
+                                 int(flags), _dev(xbar, "xbar", 3), _dev(vbar, "vbar", 3)),
+           "leapfrog_adjoint")
 
 
 def gravity_forces_host(ctx: Context, pos_host: torch.Tensor, mass_host: torch.Tensor,

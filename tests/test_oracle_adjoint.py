@@ -64,3 +64,32 @@ def test_leapfrog_gradient_matches_finite_differences_direct():
         fd = (L(pos + h * ex, vel + h * ev) - L(pos - h * ex, vel - h * ev)) / (2 * h)
         an = (gx * ex).sum() + (gv * ev).sum()
         assert abs(fd - an) <= 1e-6 * (np.abs(gx * ex).sum() + np.abs(gv * ev).sum()), (fd, an)
+
+
+def test_vjp_absum_two_body_closed_form():
+    # two bodies, d = x1 - x0: body 0 takes part in its own term (source 1, cotangent
+    # u0) and as the source of body 1's term (cotangent u1), so its magnitude sum is
+    # m1 |J(d) u0| + m0 |J(d) u1|, J = (I - 3 d d^T / r^2) / r^3, r^2 = |d|^2 + eps^2
+    x = np.array([[0.1, -0.2, 0.3], [0.7, 0.4, -0.5]])
+    m = np.array([0.3, 1.7])
+    u = np.array([[1.0, -2.0, 0.5], [0.25, 0.75, -1.5]])
+    eps = 0.05
+    d = x[1] - x[0]
+    r2 = d @ d + eps * eps
+    J = (np.eye(3) - 3.0 * np.outer(d, d) / r2) / r2 ** 1.5
+    g, a = oracle.tree_vjp(oracle.Tree(x, m), u, 0.0, eps, with_absum=True)
+    w0, w1 = m[1] * J @ u[0], m[0] * J @ u[1]      # terms of body 0 and of body 1
+    assert np.allclose(g[0], -w0 + w1, rtol=1e-14, atol=0)
+    assert np.allclose(g[1], -w1 + w0, rtol=1e-14, atol=0)
+    want = np.linalg.norm(w0) + np.linalg.norm(w1)
+    assert np.allclose(a, [want, want], rtol=1e-14, atol=0)
+
+
+def test_vjp_absum_bounds_gradient():
+    # triangle inequality: |grad_j| <= absum_j for every body, with and without nodes
+    pos, _, m = inputs.clumpy_plummer(800, seed=8)
+    lam = np.random.default_rng(9).standard_normal(pos.shape)
+    for theta, leaf in ((0.0, 1), (0.6, 4)):
+        g, a = oracle.tree_vjp(oracle.Tree(pos, m, leaf_max=leaf), lam, theta, 1e-3,
+                               with_absum=True)
+        assert np.all(np.linalg.norm(g, axis=1) <= a * (1 + 1e-12))
