@@ -40,6 +40,9 @@ UNIT = "body-forces/s"
 #                         m r^-3 + that 2, accumulate s d - Q d r^-5 12
 #   opening test: d 3, D^2 5, theta^2 D^2 1, compare 1
 FLOP_POINT, FLOP_QUAD, FLOP_MAC = 20, 51, 10
+#   vector-Jacobian product term: d 3, r^2 6, 1/sqrt 2, r^-2 1, r^-3 1, m r^-3 1, d.u 5,
+#                                 3 (d.u) r^-2 2, w = s (u - c d) 9, own sum 3, source sum 3
+FLOP_VJP = 36
 FP32_LANES_PER_SM = 128
 
 
@@ -63,6 +66,7 @@ def parse():
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble leg")
     ap.add_argument("--no-tune", action="store_true", help="default walk shape, no autotuning")
     ap.add_argument("--ensemble-steps", type=int, default=50)
+    ap.add_argument("--no-grad", action="store_true", help="skip the gradient (adjoint) leg")
     return ap.parse_args()
 
 
@@ -341,6 +345,7 @@ def run_ours(args, rank, world, local_rank):
                "api": "gravity_forces_host (pinned host buffers, copies + build + walk + sync)"}
 
     ens = None if args.no_ensemble else ensemble_leg(args, g, dev, rank)
+    grad = None if args.no_grad else gradient_leg(args, g, dev, rank)
 
     if rank != 0:
         return 0
@@ -359,6 +364,8 @@ def run_ours(args, rank, world, local_rank):
     line["config"]["walk_cfg"] = int(p.walk_cfg)
     if ens is not None:
         line["ensemble"] = ens
+    if grad is not None:
+        line["gradient"] = grad
     line.update(extra)
     print(json.dumps(line), flush=True)
     return 0
@@ -402,6 +409,127 @@ def ensemble_leg(args, g, dev, rank):
             "steps": steps, "ms_per_step": ms / steps, "value": n * steps / (ms * 1e-3),
             "unit": "body-forces/s (leapfrog steps, one force evaluation each)",
             "graph": True, "kernels_per_step": kernels / steps, "walk_cfg": int(p.walk_cfg)}
+
+
+def gradient_leg(args, g, dev, rank):
+    """Differentiation: N = 65536 bodies uniform in the unit sphere at rest, m = 1/N,
+    eps = 1e-3, 200 KDK steps of dt = 1e-3 at theta = 0.5 (monopole, leaf 1), checkpoints
+    every 20 steps; loss = axis-ratio deviation (target 1 : 0.8 : 0.6) of the final
+    second-moment tensor; gradient with respect to the initial positions and velocities.
+    Reports forward / backward times, the vector-Jacobian-product kernel against the FP32
+    roofline, the gradient against central differences of the same GPU forward (along the
+    gradient, along random directions, and on seeded single coordinates) and against the
+    gradient of the exact sum (theta = 0)."""
+    import torch
+    from paper_1912_04197_gb300 import inputs
+    from paper_1912_04197_gb300.adjoint import leapfrog
+    from paper_1912_04197_gb300.loss import axis_ratio_loss
+    n, nsteps, dt, eps, every = 65536, 200, 1e-3, 1e-3, 20
+    theta = args.theta
+    pos, vel, m = inputs.uniform_sphere(n, seed=args.seed + 200 + rank)
+    stream = torch.cuda.current_stream(dev)
+    ctx = g.Context(dev)
+    M = torch.tensor(m, device=dev)
+    p = g.params(order=0, leaf_max=1)
+
+    def run(th):
+        x0 = torch.tensor(pos, device=dev, requires_grad=True)
+        v0 = torch.tensor(vel, device=dev, requires_grad=True)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        x, _ = leapfrog(x0, v0, M, dt, nsteps, theta=th, eps=eps, leaf_max=1,
+                        checkpoint_every=every, ctx=ctx)
+        L = axis_ratio_loss(x, M)
+        ev[1].record(stream)
+        gx, gv = torch.autograd.grad(L, (x0, v0))
+        ev[2].record(stream)
+        torch.cuda.synchronize(dev)
+        g.gravity_sync(ctx)
+        return (float(L.detach()), gx.cpu().numpy(), gv.cpu().numpy(),
+                ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]))
+
+    run(theta)                                                        # warm-up
+    k0 = g.gravity_stats(ctx)
+    L, gx, gv, t_fwd, t_bwd = run(theta)
+    kernels = g.gravity_stats(ctx) - k0
+
+    def loss_at(x, v, th=theta):
+        P = torch.tensor(x, device=dev)
+        V = torch.tensor(v, device=dev)
+        A = torch.empty_like(P)
+        g.gravity_tree_build(ctx, P, M, p)
+        g.gravity_forces(ctx, th, eps, A)
+        g.leapfrog_step(ctx, P, V, M, A, dt, nsteps, th, eps, p)
+        return float(axis_ratio_loss(P, M))
+
+    rng = np.random.default_rng(args.seed + 201)
+    gn = np.sqrt((gx * gx).sum() + (gv * gv).sum())
+    gmax = max(np.abs(gx).max(), np.abs(gv).max())
+    dirs = [("gradient", gx / gmax, gv / gmax)]
+    for k in range(4):
+        dirs.append((f"random{k}", rng.standard_normal(pos.shape), rng.standard_normal(pos.shape)))
+    fd_dirs = []
+    for h in (1e-3, 1e-4):
+        for name, dx, dv in dirs:
+            fd = (loss_at(pos + h * dx, vel + h * dv) - loss_at(pos - h * dx, vel - h * dv)) / (2 * h)
+            ad = float((gx * dx).sum() + (gv * dv).sum())
+            cs = gn * float(np.sqrt((dx * dx).sum() + (dv * dv).sum()))
+            fd_dirs.append({"direction": name, "h": h, "fd": fd, "adjoint": ad,
+                            "rel_err": abs(fd - ad) / abs(ad) if ad else None,
+                            "err_over_norm_bound": abs(fd - ad) / cs})
+    coords = rng.choice(3 * n, size=32, replace=False)
+    coord_rel, h_c = [], 1e-3
+    for c in coords:
+        i, a = divmod(int(c), 3)
+        dx = np.zeros_like(pos)
+        dx[i, a] = 1.0
+        fd = (loss_at(pos + h_c * dx, vel) - loss_at(pos - h_c * dx, vel)) / (2 * h_c)
+        coord_rel.append(abs(fd - gx[i, a]) / (abs(gx[i, a]) + 1e-300))
+
+    # gradient of the exact sum: the same pipeline at theta = 0
+    _, gx0, gv0, t_fwd0, t_bwd0 = run(0.0)
+    d_exact = {"rel_l2_x": float(np.linalg.norm(gx - gx0) / np.linalg.norm(gx0)),
+               "rel_l2_v": float(np.linalg.norm(gv - gv0) / np.linalg.norm(gv0)),
+               "fwd_ms_theta0": t_fwd0, "bwd_ms_theta0": t_bwd0}
+
+    # the vector-Jacobian-product kernel alone, on the tree of the initial positions
+    P0 = torch.tensor(pos, device=dev)
+    lam = torch.tensor(rng.standard_normal(pos.shape), device=dev)
+    out = torch.empty_like(P0)
+    cnt = torch.empty((n, 3), dtype=torch.int32, device=dev)
+    g.gravity_tree_build(ctx, P0, M, p)
+    g.gravity_forces_counted(ctx, theta, eps, out, cnt)
+    c = cnt.to(torch.int64).sum(0).cpu().numpy()
+    terms, tests = int(c[0] + c[1]), int(c[2])
+    for _ in range(3):
+        g.gravity_forces_vjp(ctx, theta, eps, lam, out)
+    reps = 20
+    v0e, v1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    v0e.record(stream)
+    for _ in range(reps):
+        g.gravity_forces_vjp(ctx, theta, eps, lam, out)
+    v1e.record(stream)
+    torch.cuda.synchronize(dev)
+    g.gravity_sync(ctx)
+    t_vjp = v0e.elapsed_time(v1e) / reps
+    props = torch.cuda.get_device_properties(dev)
+    flops = terms * FLOP_VJP + tests * FLOP_MAC
+    return {"workload": f"N={n} uniform sphere at rest, m=1/N, eps={eps}, {nsteps} KDK steps "
+                        f"dt={dt}, theta={theta} monopole, leaf 1, checkpoints every {every}; "
+                        "loss (rho2-0.8)^2+(rho3-0.6)^2 of the final second-moment tensor",
+            "loss": L, "forward_ms": t_fwd, "backward_ms": t_bwd,
+            "backward_over_forward": t_bwd / t_fwd, "kernels": kernels,
+            "vs_finite_differences": {"directions": fd_dirs,
+                                      "coordinates": {"count": 32, "h": h_c,
+                                                      "median_rel_err": float(np.median(coord_rel)),
+                                                      "max_rel_err": float(np.max(coord_rel))}},
+            "vs_exact_sum_gradient": d_exact,
+            "vjp_kernel": {"ms": t_vjp, "terms": terms, "opening_tests": tests,
+                           "flop_per_term": FLOP_VJP, "achieved_tflops": flops / (t_vjp * 1e-3) / 1e12,
+                           "frac_of_fp32_peak_at_max_clock":
+                               flops / (t_vjp * 1e-3) /
+                               (props.multi_processor_count * FP32_LANES_PER_SM * 2 * 2070e6),
+                           "includes": "VJP walk + leaf-chain finishing pass + 2 memsets"}}
 
 
 def main():
