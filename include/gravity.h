@@ -196,6 +196,18 @@ int gravity_direct(gravity_ctx *ctx, int64_t n, const double *pos, const double 
 int gravity_direct_noalloc(int64_t n, const double *pos, const double *mass, double eps,
                            double G, double *acc, void *cuda_stream);
 
+/* Conserved quantities of the softened N-body system (the energy and momenta that
+ * Sec. 3.1 tracks), on the device:
+ *   out[0] = E = sum_i m_i |v_i|^2 / 2 - G sum_{i<j} m_i m_j / sqrt(|x_j - x_i|^2 + eps^2)
+ *   out[1..3] = P = sum_i m_i v_i,   out[4..6] = L = sum_i m_i x_i x v_i
+ * pos, vel: device (n,3) FP64; mass: device (n) FP64; out: DEVICE, 7 doubles, written
+ * asynchronously on the context's stream.  The potential is an O(n^2) sum of FP32 pair
+ * terms on hi/lo coordinates (relative error ~1e-7 of |E_pot|); kinetic energy and
+ * momenta are FP64 sums in a fixed order (deterministic).  A pair with r^2 = 0 adds
+ * nothing.  n = 0 writes zeros. */
+int gravity_diagnostics(gravity_ctx *ctx, int64_t n, const double *pos, const double *vel,
+                        const double *mass, double eps, double G, double *out);
+
 /* nsteps steps of a symplectic integrator (Sec. 2.3) with the tree rebuilt every
  * step (Sec. 2.1).  p->scheme 0 (kick-drift-kick leapfrog):
  *   v += dt/2 a;  x += dt v;  a = a(x);  v += dt/2 a

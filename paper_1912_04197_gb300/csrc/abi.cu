@@ -240,7 +240,7 @@ int gravity_destroy(gravity_ctx *h) {
   grav::free_ptr(c.adj_levels); grav::free_ptr(c.adj_work);
   if (c.graph.exec) cudaGraphExecDestroy(c.graph.exec);
   grav::free_ptr(c.d_status);
-  grav::free_ptr(c.dir_hi); grav::free_ptr(c.dir_lo);
+  grav::free_ptr(c.dir_hi); grav::free_ptr(c.dir_lo); grav::free_ptr(c.diag_buf);
   grav::free_ptr(c.h2d_pos); grav::free_ptr(c.h2d_mass); grav::free_ptr(c.h2d_acc);
   cudaGetLastError();
   delete h;
@@ -317,6 +317,21 @@ int gravity_direct(gravity_ctx *h, int64_t n, const double *pos, const double *m
   int rc = grav::set_device(h->c);
   if (rc) return rc;
   return grav::direct_forces(&h->c, n, pos, mass, eps, G, acc);
+}
+
+int gravity_diagnostics(gravity_ctx *h, int64_t n, const double *pos, const double *vel,
+                        const double *mass, double eps, double G, double *out) {
+  if (!h || n < 0 || !(eps >= 0.0) || !std::isfinite(eps) || !std::isfinite(G) || !out)
+    return GRAVITY_E_ARG;
+  if (n > 0 && (!pos || !vel || !mass)) return GRAVITY_E_ARG;
+  Ctx &c = h->c;
+  int rc = grav::set_device(c);
+  if (rc) return rc;
+  if (n == 0) {
+    GRAV_CUDA_TRY(cudaMemsetAsync(out, 0, 7 * sizeof(double), c.stream));
+    return GRAVITY_OK;
+  }
+  return grav::diagnostics(&c, n, pos, vel, mass, eps, G, out);
 }
 
 int leapfrog_step(gravity_ctx *h, int64_t n, double *pos, double *vel, const double *mass,

@@ -91,6 +91,86 @@ k_direct(const float4 *__restrict__ hi, const float4 *__restrict__ lo, int64_t n
   }
 }
 
+// Softened potential of every body, phi_i = sum_{j != i} m_j / sqrt(|d_ij|^2 + eps^2)
+// (the Plummer potential consistent with the softened force; Sec. 3.1's energy),
+// same tiling and arithmetic as k_direct; the self pair is excluded by index and a
+// pair with r^2 = 0 adds nothing.  Writes m_i phi_i (FP64).
+__global__ void __launch_bounds__(kDirThreads)
+k_potential(const float4 *__restrict__ hi, const float4 *__restrict__ lo, const double *mass,
+            int64_t n, float eps2, double *__restrict__ mphi) {
+  __shared__ float4 sh[kDirThreads], sl[kDirThreads];
+  const int64_t i = blockIdx.x * (int64_t)kDirThreads + threadIdx.x;
+  const float4 h = i < n ? hi[i] : make_float4(0, 0, 0, 0);
+  const float4 l = i < n ? lo[i] : make_float4(0, 0, 0, 0);
+  float sh_hi = 0.f, sh_lo = 0.f;
+  for (int64_t t0 = 0; t0 < n; t0 += kDirThreads) {
+    const int64_t j = t0 + threadIdx.x;
+    sh[threadIdx.x] = j < n ? hi[j] : make_float4(0, 0, 0, 0);
+    sl[threadIdx.x] = j < n ? lo[j] : make_float4(0, 0, 0, 0);
+    __syncthreads();
+    float ps = 0.f;
+    const int64_t self = i - t0;
+#pragma unroll 8
+    for (int k = 0; k < kDirThreads; ++k) {
+      const float4 a = sh[k], b = sl[k];
+      const float dx = (a.x - h.x) + (b.x - l.x);
+      const float dy = (a.y - h.y) + (b.y - l.y);
+      const float dz = (a.z - h.z) + (b.z - l.z);
+      const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+      const float inv = (r2 > 0.f && k != self) ? rsqrtf(r2) : 0.f;
+      ps = fmaf(a.w, inv, ps);
+    }
+    two_sum_add(sh_hi, sh_lo, ps);
+    __syncthreads();
+  }
+  if (i < n) mphi[i] = mass[i] * ((double)sh_hi + (double)sh_lo);
+}
+
+// Per-block FP64 partial sums of kinetic energy, m phi, momentum and angular
+// momentum (8 values per block, fixed grid and order: deterministic).
+constexpr int kDiagThreads = 256;
+constexpr int kDiagBlocks = 256;
+
+__global__ void __launch_bounds__(kDiagThreads)
+k_diag_partial(const double *__restrict__ pos, const double *__restrict__ vel,
+               const double *__restrict__ mass, const double *__restrict__ mphi, int64_t n,
+               double *__restrict__ part) {
+  double q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int64_t i = blockIdx.x * (int64_t)kDiagThreads + threadIdx.x; i < n;
+       i += (int64_t)kDiagBlocks * kDiagThreads) {
+    const double m = mass[i];
+    const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+    const double vx = vel[3 * i], vy = vel[3 * i + 1], vz = vel[3 * i + 2];
+    q[0] += 0.5 * m * (vx * vx + vy * vy + vz * vz);
+    q[1] += mphi[i];
+    q[2] += m * vx; q[3] += m * vy; q[4] += m * vz;
+    q[5] += m * (y * vz - z * vy);
+    q[6] += m * (z * vx - x * vz);
+    q[7] += m * (x * vy - y * vx);
+  }
+  __shared__ double red[8][kDiagThreads];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) red[k][threadIdx.x] = q[k];
+  __syncthreads();
+  for (int s = kDiagThreads / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x < 8) part[8 * blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// Sums the block partials in block order: out = E, P xyz, L xyz.
+__global__ void k_diag_final(const double *__restrict__ part, double G, double *__restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int b = 0; b < kDiagBlocks; ++b)
+    for (int k = 0; k < 8; ++k) q[k] += part[8 * b + k];
+  out[0] = q[0] - 0.5 * G * q[1];     // every pair appears twice in sum_i m_i phi_i
+  for (int k = 0; k < 6; ++k) out[1 + k] = q[2 + k];
+}
+
 }  // namespace
 
 int direct_forces(Ctx *c, int64_t n, const double *pos, const double *mass, double eps, double G,
@@ -110,6 +190,34 @@ int direct_forces(Ctx *c, int64_t n, const double *pos, const double *mass, doub
   k_direct<<<(unsigned)((n + per_block - 1) / per_block), kDirThreads, 0, c->stream>>>(
       c->dir_hi, c->dir_lo, n, (float)(eps * eps), G, acc);
   ++c->launches;
+  return cuda_status(cudaGetLastError());
+}
+
+int diagnostics(Ctx *c, int64_t n, const double *pos, const double *vel, const double *mass,
+                double eps, double G, double *out_dev) {
+  if (n > c->dir_cap) {
+    if (c->dir_hi) cudaFree(c->dir_hi);
+    if (c->dir_lo) cudaFree(c->dir_lo);
+    c->dir_hi = c->dir_lo = nullptr;
+    c->dir_cap = 0;
+    GRAV_CUDA_TRY(cudaMalloc(&c->dir_hi, sizeof(float4) * n));
+    GRAV_CUDA_TRY(cudaMalloc(&c->dir_lo, sizeof(float4) * n));
+    c->dir_cap = n;
+  }
+  if (n > c->diag_cap) {
+    if (c->diag_buf) cudaFree(c->diag_buf);
+    c->diag_buf = nullptr;
+    c->diag_cap = 0;
+    GRAV_CUDA_TRY(cudaMalloc(&c->diag_buf, sizeof(double) * (n + 8 * kDiagBlocks + 8)));
+    c->diag_cap = n;
+  }
+  double *mphi = c->diag_buf, *part = c->diag_buf + n;
+  k_split<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(pos, mass, n, c->dir_hi, c->dir_lo);
+  k_potential<<<(unsigned)((n + kDirThreads - 1) / kDirThreads), kDirThreads, 0, c->stream>>>(
+      c->dir_hi, c->dir_lo, mass, n, (float)(eps * eps), mphi);
+  k_diag_partial<<<kDiagBlocks, kDiagThreads, 0, c->stream>>>(pos, vel, mass, mphi, n, part);
+  k_diag_final<<<1, 32, 0, c->stream>>>(part, G, out_dev);
+  c->launches += 4;
   return cuda_status(cudaGetLastError());
 }
 

@@ -114,6 +114,9 @@ struct Ctx {
   // direct-sum staging (caller order hi/lo)
   float4 *dir_hi = nullptr, *dir_lo = nullptr;
   int64_t dir_cap = 0;
+  // diagnostics: m phi per body, block partials, result (nodes of 8 doubles)
+  double *diag_buf = nullptr;
+  int64_t diag_cap = 0;
   // host-buffer entry point staging
   double *h2d_pos = nullptr, *h2d_mass = nullptr, *h2d_acc = nullptr;
   int64_t h2d_cap = 0;
@@ -128,6 +131,8 @@ int walk_vjp(Ctx *c, double theta, double eps, const double *lambda, double *gra
 // ---- launchers (direct.cu)
 int direct_forces(Ctx *c, int64_t n, const double *pos, const double *mass, double eps,
                   double G, double *acc);
+int diagnostics(Ctx *c, int64_t n, const double *pos, const double *vel, const double *mass,
+                double eps, double G, double *out_dev);
 // ---- launchers (integrate.cu)
 int launch_kick_drift(Ctx *c, int64_t n, double *pos, double *vel, const double *acc,
                       double h_kick, double dt);

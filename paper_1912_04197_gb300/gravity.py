@@ -60,6 +60,7 @@ def _load() -> ctypes.CDLL:
         "gravity_forces_counted": (I, [P, D, D, P, P]),
         "gravity_forces_vjp": (I, [P, D, D, P, P]),
         "gravity_direct": (I, [P, I64, P, P, D, D, P]),
+        "gravity_diagnostics": (I, [P, I64, P, P, P, D, D, P]),
         "leapfrog_step": (I, [P, I64, P, P, P, P, D, I, D, D, PP]),
         "leapfrog_adjoint": (I, [P, I64, P, P, P, D, I, D, D, PP, I, P, P]),
         "gravity_forces_host": (I, [P, I64, P, P, D, D, PP, P]),
@@ -212,6 +213,15 @@ def gravity_direct(ctx: Context, pos, mass, eps: float, G: float, acc) -> torch.
     _check(_lib.gravity_direct(ctx.handle, pos.shape[0], _dev(pos, "pos", 3), _dev(mass, "mass"),
                                float(eps), float(G), _dev(acc, "acc", 3)), "gravity_direct")
     return acc
+
+
+def gravity_diagnostics(ctx: Context, pos, vel, mass, eps: float, G: float,
+                        out: torch.Tensor) -> torch.Tensor:
+    """out (device, 7 float64) = E, P xyz, L xyz."""
+    _check(_lib.gravity_diagnostics(ctx.handle, pos.shape[0], _dev(pos, "pos", 3),
+                                    _dev(vel, "vel", 3), _dev(mass, "mass"), float(eps), float(G),
+                                    _dev(out, "out")), "gravity_diagnostics")
+    return out
 
 
 def gravity_direct_noalloc(pos, mass, eps: float, G: float, acc) -> torch.Tensor:
