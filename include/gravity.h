@@ -249,7 +249,8 @@ int gravity_sync(gravity_ctx *ctx);
  *                         mixed nodes, FP64 decisions, point-list entries, quadrupole-list
  *                         entries, deepest stack, terms evaluated by active lanes, lockstep
  *                         iterations of lists split by 16 / 8 / 1 lanes, full-mask entries,
- *                         4 reserved
+ *                         far-list entries, mixed nodes that all tested lanes decided alike,
+ *                         2 reserved
  * bytes must be at least the size listed; otherwise GRAVITY_E_ARG. */
 enum gravity_debug_item {
   GRAVITY_DBG_ROOT = 0,

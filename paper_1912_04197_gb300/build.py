@@ -20,6 +20,10 @@ LIB = os.path.join(BUILD, "libgravity.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]
+# FP32 pair-term kernels flush single-precision denormals (operands of these terms are
+# never denormal at the scales the library supports: r^2 >= eps^2 or a real distance,
+# masses and moments far above 1e-38); the flush shortens rsqrt and saves ~4 % of the walk.
+FILE_FLAGS = {"walk.cu": ["-ftz=true"], "direct.cu": ["-ftz=true"]}
 
 
 def _nvcc() -> str:
@@ -37,7 +41,8 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+    deps = (sources() + glob.glob(os.path.join(CSRC, "*.cuh")) +
+            glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)])
     return any(os.path.getmtime(p) > t for p in deps)
 
 
@@ -50,7 +55,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, *extra_flags, "-I", INCLUDE, "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, *FILE_FLAGS.get(os.path.basename(src), []), *extra_flags,
+               "-I", INCLUDE, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

@@ -62,7 +62,7 @@ enum { kModeForce = 0, kModeCount = 1, kModeVjp = 2 };
 
 enum { kStatBatches, kStatItems, kStatMixed, kStatFp64, kStatMono, kStatQuad, kStatMaxSp,
        kStatLaneTerms, kStatSplit2, kStatSplit4, kStatSplit32, kStatFull, kStatFar,
-       kStatCount = 16 };
+       kStatMixedUnanimous, kStatCount = 16 };
 
 struct WarpSmem {
   uint32_t st_a[kSmemStack];      // first | (count-1) << 25 | kind
@@ -615,6 +615,7 @@ k_walk(WalkArgs A) {
         const unsigned am = __ballot_sync(0xffffffffu, a_i);
         const unsigned om = __ballot_sync(0xffffffffu, o_i);
         if (lane == j) { accm = am; openm = om; }
+        if (COUNT && lane == 0 && (am == mk || om == mk)) atomicAdd(&A.stats[kStatMixedUnanimous], 1ull);
       }
 
       // ---- append accepted terms: point / far / near
