@@ -600,11 +600,13 @@ __global__ void k_oct_parent(int cap_nodes, int nseg, const int4 *__restrict__ t
 // Q = 3 T - tr(T) I, identical in exact arithmetic to sum m (3 y y^T - |y|^2 I).
 //
 // GB300's FP64 pipe costs the same per warp instruction however many lanes are
-// active, so the pass runs on full warps: nodes are counting-sorted into buckets
-// (all leaves; then internal nodes by depth, deepest first), leaves are done in
+// active, so the pass runs on full, uniform warps: nodes are counting-sorted into
+// buckets (leaves by body count 1 .. 16 and more, so that the lanes of a warp loop
+// equally long; then internal nodes by depth, deepest first), leaves are done in
 // one launch and each depth level in one launch after the deeper levels.
-constexpr int kBuckets = kLevels + 2;      // 0 = leaves, 1 + (21 - depth) = internal
-constexpr int kSlotCnt = 0, kSlotFill = 32, kSlotOff = 64;   // offsets into t.scalars
+constexpr int kLeafBuckets = 17;
+constexpr int kBuckets = kLeafBuckets + kLevels;   // + internal depths 20 .. 0
+constexpr int kSlotCnt = 0, kSlotFill = 40, kSlotOff = 80;   // offsets into t.scalars
 
 struct MomArgs {
   const int4 *topo;
@@ -633,7 +635,8 @@ __device__ __forceinline__ double da(double a, double b) { return __dadd_rn(a, b
 __device__ __forceinline__ double ds(double a, double b) { return __dsub_rn(a, b); }
 
 __device__ __forceinline__ int bucket_of(int4 t, int depth) {
-  return t.x < 0 ? 0 : 1 + (kLevels - depth);
+  const int b = t.x < 0 ? min(t.w - t.z, kLeafBuckets) - 1 : kLeafBuckets + (kLevels - 1 - depth);
+  return min(max(b, 0), kBuckets - 1);
 }
 
 __global__ void k_bucket_count(const int4 *__restrict__ topo, const int32_t *__restrict__ ndepth,
@@ -703,7 +706,7 @@ __device__ void write_records(const MomArgs &A, int id, double m, const double *
 }
 
 __global__ void k_leaf_moments(MomArgs A) {
-  const uint32_t b0 = A.boff[0], b1 = A.boff[1];
+  const uint32_t b0 = A.boff[0], b1 = A.boff[kLeafBuckets];
   for (uint32_t k = b0 + blockIdx.x * blockDim.x + threadIdx.x; k < b1;
        k += gridDim.x * blockDim.x) {
     const int id = A.nlist[k];
@@ -870,7 +873,7 @@ int tree_build(Ctx *c, int64_t n, const double *pos, const double *mass) {
     ++c->launches;
   }
   // a7: moments (bucketed by depth, full warps)
-  GRAV_CUDA_TRY(cudaMemsetAsync(t.scalars + kSlotCnt, 0, sizeof(uint32_t) * 64, s));
+  GRAV_CUDA_TRY(cudaMemsetAsync(t.scalars + kSlotCnt, 0, sizeof(uint32_t) * kSlotOff, s));
   const unsigned nb_nodes = blocks_for(cap_nodes, 256);
   k_bucket_count<<<nb_nodes, 256, 0, s>>>(t.topo, t.ndepth, t.nnodes, cap_nodes, t.scalars);
   ++c->launches;
@@ -884,7 +887,7 @@ int tree_build(Ctx *c, int64_t n, const double *pos, const double *mass) {
   k_leaf_moments<<<grid, 128, 0, s>>>(A);
   ++c->launches;
   for (int d = kLevels - 1; d >= 0; --d) {
-    k_level_moments<<<grid, 128, 0, s>>>(A, 1 + (kLevels - d));
+    k_level_moments<<<grid, 128, 0, s>>>(A, kLeafBuckets + (kLevels - 1 - d));
     ++c->launches;
   }
   return cuda_status(cudaGetLastError());
