@@ -95,7 +95,7 @@ int ensure_capacity(Ctx *c, int64_t n) {
 #define GRAV_ALLOC(p, cnt) if (e == cudaSuccess) e = alloc(p, cnt)
   GRAV_ALLOC(t.keys, cap); GRAV_ALLOC(t.keys_alt, cap);
   GRAV_ALLOC(t.idx, cap); GRAV_ALLOC(t.idx_alt, cap);
-  GRAV_ALLOC(t.hist, 256 * ntiles);
+  GRAV_ALLOC(t.hist, 257 * 10 + 10 * 256 * ntiles);   // radix sort: counts + tile states
   GRAV_ALLOC(t.scan_aux, scan_n / 4096 + 64);
   GRAV_ALLOC(t.bbox_part, 6 * (4 * (int64_t)c->num_sms + 3));
   GRAV_ALLOC(t.pos_s, 3 * cap); GRAV_ALLOC(t.mass_s, cap);

@@ -267,72 +267,181 @@ int exclusive_scan(Ctx *c, uint32_t *data, int64_t n, uint32_t *total_out) {
 }
 
 // ------------------------------------------------------------------ a3: radix sort
-// Stable LSD radix sort of (key, index) pairs, 8 passes of 8-bit digits.
-// Pass = per-tile digit histogram -> exclusive scan in digit-major order ->
-// stable scatter (ranks from warp match + per-warp counts, in index order).
-// Digit of element i in a radix pass: 8 bits of the Morton key, or, for the passes
-// that order clouds, 8 bits of the cloud id of the element's caller index.
+// Stable LSD radix sort of (key, index) pairs, 8 passes of 8-bit digits (then, with
+// several clouds, passes over the cloud id), one kernel per pass ("one sweep"):
+//   * one upfront kernel counts the digits of every pass (the multiset of a pass's
+//     digits does not depend on the order the earlier passes leave);
+//   * in a pass, each block claims the next 2048-key tile in order, ranks its keys
+//     stably (warp match on the digit, per-warp running counts, items in index
+//     order), publishes its per-digit counts, and finds the counts of all earlier
+//     tiles by a decoupled look-back over their published values (a bounded wait on
+//     tiles not yet published: those were claimed earlier by running blocks, which
+//     publish before they wait themselves, so the wait always ends);
+//   * destination = digit base (scan of the pass histogram) + earlier tiles' count of
+//     the digit + earlier warps' count in this tile + rank within the warp.
+// Digit of element i in a pass: 8 bits of the Morton key, or, for the passes that
+// order clouds, 8 bits of the cloud id of the element's caller index.
+constexpr int kRsMaxPasses = 10;                 // 8 key passes + up to 2 cloud-id passes
+constexpr uint32_t kRsFlagAgg = 1u << 30, kRsFlagPre = 2u << 30, kRsValue = (1u << 30) - 1;
+constexpr int kRsSpin = 1 << 22;
+constexpr int kRsLook = 32;                      // predecessor tiles read per look-back round
+
 __device__ __forceinline__ unsigned rs_digit(uint64_t key, uint32_t val, int shift,
                                              const int32_t *__restrict__ seg_of) {
   if (seg_of) return ((unsigned)seg_of[val] >> shift) & 255u;
   return (unsigned)(key >> shift) & 255u;
 }
 
+// Digit counts of all passes: ghist[pass][256].
 __global__ void __launch_bounds__(kRsThreads)
-k_rs_hist(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals, int64_t n,
-          int shift, const int32_t *__restrict__ seg_of, uint32_t *__restrict__ hist,
-          int ntiles) {
-  __shared__ uint32_t cnt[256];
-  cnt[threadIdx.x] = 0;
+k_rs_count(const uint64_t *__restrict__ keys, int64_t n, int key_passes, int cloud_passes,
+           const int32_t *__restrict__ seg_of, uint32_t *__restrict__ ghist) {
+  __shared__ uint32_t cnt[kRsMaxPasses][256];
+  const int np = key_passes + cloud_passes;
+  for (int p = 0; p < np; ++p) cnt[p][threadIdx.x] = 0;
   __syncthreads();
-  int64_t base = blockIdx.x * (int64_t)kRsTile;
-  for (int k = 0; k < kRsItems; ++k) {
-    int64_t i = base + k * kRsThreads + threadIdx.x;
-    if (i < n) atomicAdd(&cnt[rs_digit(keys[i], seg_of ? vals[i] : 0u, shift, seg_of)], 1u);
+  for (int64_t i = blockIdx.x * (int64_t)kRsThreads + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kRsThreads) {
+    const uint64_t k = keys[i];
+    for (int p = 0; p < key_passes; ++p) atomicAdd(&cnt[p][(unsigned)(k >> (8 * p)) & 255u], 1u);
+    if (cloud_passes) {
+      const unsigned sg = (unsigned)seg_of[i];   // caller order: same multiset of ids
+      for (int p = 0; p < cloud_passes; ++p) atomicAdd(&cnt[key_passes + p][(sg >> (8 * p)) & 255u], 1u);
+    }
   }
   __syncthreads();
-  hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
+  for (int p = 0; p < np; ++p)
+    if (cnt[p][threadIdx.x]) atomicAdd(&ghist[256 * p + threadIdx.x], cnt[p][threadIdx.x]);
+}
+
+// Exclusive scan of one value per thread over a 256-thread block.
+__device__ __forceinline__ uint32_t block_excl_scan256(uint32_t v, uint32_t *s_tmp) {
+  const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t inc = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (l >= o) inc += t;
+  }
+  if (l == 31) s_tmp[w] = inc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t r = 0;
+    for (int ww = 0; ww < kRsThreads / 32; ++ww) { const uint32_t t = s_tmp[ww]; s_tmp[ww] = r; r += t; }
+  }
+  __syncthreads();
+  const uint32_t ex = s_tmp[w] + inc - v;
+  __syncthreads();
+  return ex;
 }
 
 __global__ void __launch_bounds__(kRsThreads)
-k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
-             uint64_t *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n, int shift,
-             const int32_t *__restrict__ seg_of, const uint32_t *__restrict__ offs, int ntiles) {
+k_rs_sweep(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+           uint64_t *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n, int shift,
+           const int32_t *__restrict__ seg_of, const uint32_t *__restrict__ ghist,
+           uint32_t *__restrict__ status, unsigned *__restrict__ tile_counter, int ntiles,
+           unsigned *err) {
   constexpr int W = kRsThreads / 32;
-  __shared__ uint32_t s_base[256];
-  __shared__ uint32_t s_w[W][256];
+  __shared__ uint32_t s_w[W][256];      // per-warp digit counts, then exclusive bases
+  __shared__ int32_t s_off[256];        // global position of the tile's local position 0, per digit
+  __shared__ uint32_t s_tloc[256];      // tile-local exclusive digit offsets
+  __shared__ uint32_t s_tmp[W];
+  __shared__ uint64_t s_key[kRsTile];   // the tile in local sorted order
+  __shared__ uint32_t s_val[kRsTile];
+  __shared__ uint8_t s_dig[kRsTile];
+  __shared__ int s_tile;
   const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
   const unsigned lt = (1u << l) - 1u;
-  s_base[tid] = offs[(int64_t)tid * ntiles + blockIdx.x];
-  const int64_t base = blockIdx.x * (int64_t)kRsTile;
+  if (tid == 0) s_tile = (int)atomicAdd(tile_counter, 1u);
+  for (int ww = 0; ww < W; ++ww) s_w[ww][tid] = 0;
+  __syncthreads();
+  const int tile = s_tile;
+  if (tile >= ntiles) return;
+  // ---- stable ranks within each warp (warp w holds items [w*256, w*256 + 256) of the tile)
+  const int64_t base = (int64_t)tile * kRsTile + w * (32 * kRsItems);
+  uint64_t key[kRsItems];
+  uint32_t val[kRsItems], pos[kRsItems];
+  unsigned dig[kRsItems];
+#pragma unroll
   for (int k = 0; k < kRsItems; ++k) {
-    for (int ww = 0; ww < W; ++ww) s_w[ww][tid] = 0;
-    __syncthreads();
-    int64_t i = base + k * kRsThreads + tid;
-    bool valid = i < n;
-    uint64_t key = valid ? kin[i] : 0ull;
-    uint32_t val = valid ? vin[i] : 0u;
-    unsigned d = valid ? rs_digit(key, val, shift, seg_of) : 256u;
-    unsigned peers = __match_any_sync(0xffffffffu, d);
-    unsigned rank = __popc(peers & lt);
-    if (valid && rank == 0) s_w[w][d] = __popc(peers);
-    __syncthreads();
-    uint32_t run = s_base[tid];
-    for (int ww = 0; ww < W; ++ww) {
-      uint32_t cnum = s_w[ww][tid];
-      s_w[ww][tid] = run;
-      run += cnum;
+    const int64_t i = base + k * 32 + l;
+    const bool valid = i < n;
+    key[k] = valid ? kin[i] : 0ull;
+    val[k] = valid ? vin[i] : 0u;
+    dig[k] = valid ? rs_digit(key[k], val[k], shift, seg_of) : 256u;
+  }
+#pragma unroll
+  for (int k = 0; k < kRsItems; ++k) {
+    const unsigned d = dig[k];
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const int leader = __ffs(peers) - 1;
+    uint32_t before = 0;
+    if (l == leader && d < 256u) {
+      before = s_w[w][d];
+      s_w[w][d] = before + __popc(peers);
     }
-    s_base[tid] = run;
-    __syncthreads();
-    if (valid) {
-      uint32_t p = s_w[w][d] + rank;
-      if (p < (uint64_t)n) {                 // always true for consistent histograms
-        kout[p] = key;
-        vout[p] = val;
+    before = __shfl_sync(0xffffffffu, before, leader);
+    pos[k] = before + __popc(peers & lt);
+    __syncwarp();
+  }
+  __syncthreads();
+  // ---- per digit (thread = digit): warp bases, tile count, publish, look back
+  uint32_t run = 0;
+  for (int ww = 0; ww < W; ++ww) {
+    const uint32_t c = s_w[ww][tid];
+    s_w[ww][tid] = run;
+    run += c;
+  }
+  const uint32_t count = run;
+  volatile uint32_t *st = status + (int64_t)tile * 256 + tid;
+  *st = (tile == 0 ? kRsFlagPre : kRsFlagAgg) | count;
+  // look back kRsLook tiles per round (independent loads), nearest first
+  uint32_t excl = 0;
+  int spin = 0;                               // one bounded budget for the whole look-back
+  bool found = tile == 0;
+  for (int j0 = tile - 1; !found && j0 >= 0; j0 -= kRsLook) {
+    uint32_t v[kRsLook];
+#pragma unroll
+    for (int k = 0; k < kRsLook; ++k)
+      v[k] = j0 - k >= 0 ? *(const volatile uint32_t *)(status + (int64_t)(j0 - k) * 256 + tid)
+                         : kRsFlagPre;
+#pragma unroll
+    for (int k = 0; k < kRsLook; ++k) {
+      if (found) break;
+      const volatile uint32_t *sj = status + (int64_t)(j0 - k) * 256 + tid;
+      while ((v[k] >> 30) == 0 && ++spin < kRsSpin) v[k] = *sj;
+      if ((v[k] >> 30) == 0) { atomicOr(err, kErrTimeout); found = true; break; }
+      excl += v[k] & kRsValue;
+      found = (v[k] >> 30) == 2u;
+    }
+  }
+  if (tile > 0) *st = kRsFlagPre | (excl + count);
+  // ---- digit bases (scan of the pass histogram) and tile-local digit offsets
+  const uint32_t gbase = block_excl_scan256(ghist[tid], s_tmp);
+  const uint32_t tloc = block_excl_scan256(count, s_tmp);
+  s_tloc[tid] = tloc;
+  s_off[tid] = (int32_t)(gbase + excl) - (int32_t)tloc;
+  __syncthreads();
+  // ---- local sort into shared memory, then coalesced write-out of each digit's run
+#pragma unroll
+  for (int k = 0; k < kRsItems; ++k) {
+    const unsigned d = dig[k];
+    if (d < 256u) {
+      const uint32_t lp = s_tloc[d] + s_w[w][d] + pos[k];
+      if (lp < (uint32_t)kRsTile) {          // always true for consistent counts
+        s_key[lp] = key[k];
+        s_val[lp] = val[k];
+        s_dig[lp] = (uint8_t)d;
       }
     }
-    __syncthreads();
+  }
+  __syncthreads();
+  const int nvalid = (int)min((int64_t)kRsTile, n - (int64_t)tile * kRsTile);
+  for (int lp = tid; lp < nvalid; lp += kRsThreads) {
+    const int64_t p = (int64_t)s_off[s_dig[lp]] + lp;
+    if (p >= 0 && p < n) {                   // always true for consistent counts
+      kout[p] = s_key[lp];
+      vout[p] = s_val[lp];
+    }
   }
 }
 
@@ -340,24 +449,35 @@ k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
 // ids, so the order is by cloud, then key, then caller index.
 int radix_sort(Ctx *c, int64_t n) {
   Tree &t = c->t;
-  int ntiles = (int)((n + kRsTile - 1) / kRsTile);
+  const int ntiles = (int)((n + kRsTile - 1) / kRsTile);
   uint64_t *ka = t.keys, *kb = t.keys_alt;
   uint32_t *va = t.idx, *vb = t.idx_alt;
   const int cloud_passes = c->seg.nseg > 1 ? (c->seg.cbits + 7) / 8 : 0;
-  for (int pass = 0; pass < 8 + cloud_passes; ++pass) {
+  const int np = 8 + cloud_passes;
+  // t.hist: [kRsMaxPasses][256] digit counts, [kRsMaxPasses] tile counters,
+  // then [kRsMaxPasses][ntiles][256] published tile counts
+  uint32_t *ghist = t.hist, *counters = t.hist + 256 * kRsMaxPasses;
+  uint32_t *status = counters + kRsMaxPasses;
+  GRAV_CUDA_TRY(cudaMemsetAsync(t.hist, 0,
+                                sizeof(uint32_t) * ((size_t)(256 + 1) * kRsMaxPasses +
+                                                    (size_t)np * ntiles * 256), c->stream));
+  int cb = (int)((n + kRsThreads - 1) / kRsThreads);
+  if (cb > 2 * c->num_sms) cb = 2 * c->num_sms;
+  k_rs_count<<<cb, kRsThreads, 0, c->stream>>>(t.keys, n, 8, cloud_passes, c->seg.seg_of, ghist);
+  ++c->launches;
+  for (int pass = 0; pass < np; ++pass) {
     const bool cl = pass >= 8;
     const int shift = cl ? 8 * (pass - 8) : 8 * pass;
     const int32_t *so = cl ? c->seg.seg_of : nullptr;
-    k_rs_hist<<<ntiles, kRsThreads, 0, c->stream>>>(ka, va, n, shift, so, t.hist, ntiles);
-    ++c->launches;
-    int rc = exclusive_scan(c, t.hist, (int64_t)256 * ntiles, nullptr);
-    if (rc) return rc;
-    k_rs_scatter<<<ntiles, kRsThreads, 0, c->stream>>>(ka, va, kb, vb, n, shift, so, t.hist, ntiles);
+    k_rs_sweep<<<ntiles, kRsThreads, 0, c->stream>>>(ka, va, kb, vb, n, shift, so,
+                                                     ghist + 256 * pass,
+                                                     status + (int64_t)pass * ntiles * 256,
+                                                     counters + pass, ntiles, c->d_status);
     ++c->launches;
     uint64_t *tk = ka; ka = kb; kb = tk;
     uint32_t *tv = va; va = vb; vb = tv;
   }
-  if ((8 + cloud_passes) % 2) {               // odd pass count: move the result back
+  if (np % 2) {                               // odd pass count: move the result back
     GRAV_CUDA_TRY(cudaMemcpyAsync(t.keys, ka, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, c->stream));
     GRAV_CUDA_TRY(cudaMemcpyAsync(t.idx, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, c->stream));
   }
@@ -747,41 +867,69 @@ __global__ void k_leaf_moments(MomArgs A) {
 }
 
 // Internal nodes of one depth (bucket); their children are deeper, hence done.
-__global__ void k_level_moments(MomArgs A, int bucket) {
-  const uint32_t b0 = A.boff[bucket], b1 = A.boff[bucket + 1];
-  const int nn = min(*A.nnodes, A.cap_nodes);
-  for (uint32_t k = b0 + blockIdx.x * blockDim.x + threadIdx.x; k < b1;
-       k += gridDim.x * blockDim.x) {
-    const int id = A.nlist[k];
-    const int4 tp = A.topo[id];
-    if (tp.x <= 0 || tp.x + tp.y > nn) { latch_error(A.status, kErrTree); continue; }
-    double pm = 0.0, px = 0.0, py = 0.0, pz = 0.0;
-    for (int c = tp.x; c < tp.x + tp.y; ++c) {
-      const double mc = A.nmass[c];
-      pm = da(pm, mc);
-      px = da(px, dm(A.ncom[3 * c], mc));
-      py = da(py, dm(A.ncom[3 * c + 1], mc));
-      pz = da(pz, dm(A.ncom[3 * c + 2], mc));
+// All children's values are loaded up front (at most 8 children: independent loads
+// in flight together), then combined in octant order as before.
+__device__ void internal_node(const MomArgs &A, int id, int nn) {
+  const int4 tp = A.topo[id];
+  if (tp.x <= 0 || tp.y > 8 || tp.x + tp.y > nn) { latch_error(A.status, kErrTree); return; }
+  double cm[8], cx[8], cy[8], cz[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const bool in = j < tp.y;
+    const int c = in ? tp.x + j : tp.x;
+    cm[j] = in ? A.nmass[c] : 0.0;
+    cx[j] = A.ncom[3 * c]; cy[j] = A.ncom[3 * c + 1]; cz[j] = A.ncom[3 * c + 2];
+  }
+  double pm = 0.0, px = 0.0, py = 0.0, pz = 0.0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    if (j < tp.y) {
+      pm = da(pm, cm[j]);
+      px = da(px, dm(cx[j], cm[j]));
+      py = da(py, dm(cy[j], cm[j]));
+      pz = da(pz, dm(cz[j], cm[j]));
     }
-    const double pc[3] = {__ddiv_rn(px, pm), __ddiv_rn(py, pm), __ddiv_rn(pz, pm)};
-    double T[6] = {0, 0, 0, 0, 0, 0};
-    if (A.order >= 2) {
-      for (int c = tp.x; c < tp.x + tp.y; ++c) {
-        const double mc = A.nmass[c];
-        const double d0 = A.ncom[3 * c] - pc[0], d1 = A.ncom[3 * c + 1] - pc[1],
-                     d2 = A.ncom[3 * c + 2] - pc[2];
-        const double m0 = mc * d0, m1 = mc * d1, m2 = mc * d2;
-        const double *Tc = &A.nsec[6 * c];
-        T[0] += fma(m0, d0, Tc[0]); T[1] += fma(m1, d1, Tc[1]); T[2] += fma(m2, d2, Tc[2]);
-        T[3] += fma(m0, d1, Tc[3]); T[4] += fma(m0, d2, Tc[4]); T[5] += fma(m1, d2, Tc[5]);
+  }
+  const double pc[3] = {__ddiv_rn(px, pm), __ddiv_rn(py, pm), __ddiv_rn(pz, pm)};
+  double T[6] = {0, 0, 0, 0, 0, 0};
+  if (A.order >= 2) {
+#pragma unroll
+    for (int h = 0; h < 8; h += 4) {
+      double Tc[4][6];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = (h + j < tp.y) ? tp.x + h + j : tp.x;
+#pragma unroll
+        for (int a = 0; a < 6; ++a) Tc[j][a] = A.nsec[6 * c + a];
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (h + j < tp.y) {
+          const double mc = cm[h + j];
+          const double d0 = cx[h + j] - pc[0], d1 = cy[h + j] - pc[1], d2 = cz[h + j] - pc[2];
+          const double m0 = mc * d0, m1 = mc * d1, m2 = mc * d2;
+          T[0] += fma(m0, d0, Tc[j][0]); T[1] += fma(m1, d1, Tc[j][1]);
+          T[2] += fma(m2, d2, Tc[j][2]); T[3] += fma(m0, d1, Tc[j][3]);
+          T[4] += fma(m0, d2, Tc[j][4]); T[5] += fma(m1, d2, Tc[j][5]);
+        }
       }
     }
-    A.nmass[id] = pm;
-    for (int a = 0; a < 3; ++a) A.ncom[3 * id + a] = pc[a];
-    if (A.order >= 2)
-      for (int a = 0; a < 6; ++a) A.nsec[6 * id + a] = T[a];
-    write_records(A, id, pm, pc, T, false);
   }
+  A.nmass[id] = pm;
+  for (int a = 0; a < 3; ++a) A.ncom[3 * id + a] = pc[a];
+  if (A.order >= 2)
+    for (int a = 0; a < 6; ++a) A.nsec[6 * id + a] = T[a];
+  write_records(A, id, pm, pc, T, false);
+}
+
+// Internal nodes of one depth, one node per thread.
+__global__ void __launch_bounds__(128) k_level_moments(MomArgs A, int bucket) {
+  const uint32_t b0 = A.boff[bucket], b1 = A.boff[bucket + 1];
+  if (b0 >= b1) return;
+  const int nn = min(*A.nnodes, A.cap_nodes);
+  for (uint32_t k = b0 + blockIdx.x * blockDim.x + threadIdx.x; k < b1;
+       k += gridDim.x * blockDim.x)
+    internal_node(A, A.nlist[k], nn);
 }
 
 // Cloud id of every body (caller order), one block per cloud.
