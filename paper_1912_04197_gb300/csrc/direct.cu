@@ -31,6 +31,7 @@ __device__ __forceinline__ void two_sum_add(float &hi, float &lo, float p) {
   lo += err;
 }
 
+template <bool EPS0>
 __global__ void __launch_bounds__(kDirThreads)
 k_direct(const float4 *__restrict__ hi, const float4 *__restrict__ lo, int64_t n, float eps2,
          double G, double *__restrict__ acc) {
@@ -55,7 +56,7 @@ k_direct(const float4 *__restrict__ hi, const float4 *__restrict__ lo, int64_t n
     float px[P], py[P], pz[P];
 #pragma unroll
     for (int p = 0; p < P; ++p) px[p] = py[p] = pz[p] = 0.f;
-#pragma unroll 8
+#pragma unroll 4
     for (int k = 0; k < kDirThreads; ++k) {
       const float4 a = sh[k], b = sl[k];
 #pragma unroll
@@ -65,7 +66,9 @@ k_direct(const float4 *__restrict__ hi, const float4 *__restrict__ lo, int64_t n
         float dz = (a.z - zh[p]) + (b.z - zl[p]);
         float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
         float inv = rsqrtf(r2);
-        inv = r2 > 0.f ? inv : 0.f;
+        // with eps > 0, r^2 >= eps^2 > 0 and the self pair (d = 0) adds m * 0;
+        // with eps = 0 a pair at r^2 = 0 must add nothing
+        if (EPS0) inv = r2 > 0.f ? inv : 0.f;
         float s = a.w * (inv * inv * inv);
         px[p] = fmaf(s, dx, px[p]);
         py[p] = fmaf(s, dy, py[p]);
@@ -187,8 +190,12 @@ int direct_forces(Ctx *c, int64_t n, const double *pos, const double *mass, doub
   k_split<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(pos, mass, n, c->dir_hi, c->dir_lo);
   ++c->launches;
   const int64_t per_block = (int64_t)kDirThreads * kDirPerThread;
-  k_direct<<<(unsigned)((n + per_block - 1) / per_block), kDirThreads, 0, c->stream>>>(
-      c->dir_hi, c->dir_lo, n, (float)(eps * eps), G, acc);
+  const unsigned blocks = (unsigned)((n + per_block - 1) / per_block);
+  const float eps2 = (float)(eps * eps);
+  if (eps2 > 0.f)
+    k_direct<false><<<blocks, kDirThreads, 0, c->stream>>>(c->dir_hi, c->dir_lo, n, eps2, G, acc);
+  else
+    k_direct<true><<<blocks, kDirThreads, 0, c->stream>>>(c->dir_hi, c->dir_lo, n, eps2, G, acc);
   ++c->launches;
   return cuda_status(cudaGetLastError());
 }
@@ -281,7 +288,9 @@ extern "C" int gravity_direct_noalloc(int64_t n, const double *pos, const double
   // every staging entry the sum reads (j < n) is written first by k_split in this call
   k_split<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pos, mass, n, hi, lo);
   const int64_t per_block = (int64_t)kDirThreads * kDirPerThread;
-  k_direct<<<(unsigned)((n + per_block - 1) / per_block), kDirThreads, 0, s>>>(
-      hi, lo, n, (float)(eps * eps), G, acc);
+  const unsigned blocks = (unsigned)((n + per_block - 1) / per_block);
+  const float eps2 = (float)(eps * eps);
+  if (eps2 > 0.f) k_direct<false><<<blocks, kDirThreads, 0, s>>>(hi, lo, n, eps2, G, acc);
+  else k_direct<true><<<blocks, kDirThreads, 0, s>>>(hi, lo, n, eps2, G, acc);
   return cuda_status(cudaGetLastError());
 }
