@@ -25,7 +25,12 @@
 //   * each flushed list's partial sum enters a (hi, lo) two-sum accumulator (or an
 //     FP64 one).
 // The kernel is persistent: each warp takes 32-body tasks from an atomic counter,
-// and owns an overflow area in global memory for the deep part of its stack.
+// and owns an overflow area in global memory for the deep part of its stack.  When
+// there are too few tasks to fill the GPU (small N), each task is split in two: two
+// warps walk the same 32 bodies, each from one half of the root's children (the root
+// contains every body, so the guard opens it for all of them), and add their partial
+// sums to the zeroed output with FP64 atomics (two addends: the result does not
+// depend on their order).
 #include <type_traits>
 
 #include "internal.cuh"
@@ -100,7 +105,8 @@ struct WalkArgs {
   const uint32_t *perm;
   const int32_t *nnodes;
   int n;
-  int ntasks;
+  int ntasks;                     // tasks after splitting (base tasks x split)
+  int split;                      // 1, or 2: two warps per base task (see above)
   float theta2f;
   double theta2d;
   float eps2;
@@ -415,9 +421,24 @@ k_walk(WalkArgs A) {
     if (task < 0) break;
 
     // task: up to 32 consecutive bodies of one cloud; the walk starts at the cloud root
+    const int part = A.split > 1 ? task % A.split : 0;
+    task = A.split > 1 ? task / A.split : task;
     const int wbeg = A.task_begin ? A.task_begin[task] : task * 32;
     const int wend = min(A.task_begin ? A.task_end[task] : n, wbeg + 32);
     const int root = A.task_seg ? A.task_seg[task] : 0;
+    // first stack entry: the root, or (split) this part's half of the root's children
+    uint32_t first_entry = (uint32_t)root;
+    if (A.split > 1) {
+      const int4 rt = A.topo[root];
+      if (rt.x < 0) {                           // a one-leaf tree: part 0 takes it whole
+        if (part != 0) continue;
+      } else {
+        const int h = (rt.y + 1) / 2;
+        const int cnt = min(h, rt.y - part * h);
+        if (cnt <= 0) continue;
+        first_entry = (uint32_t)(rt.x + part * h) | ((uint32_t)(cnt - 1) << kCntShift);
+      }
+    }
     const double side = A.geom[8 * root + 3];
     const int gi = wbeg + lane;
     const bool valid = gi < wend;
@@ -471,7 +492,7 @@ k_walk(WalkArgs A) {
     bool abort = false;
     {
       const unsigned vm = __ballot_sync(0xffffffffu, valid);
-      if (lane == 0) st.set(0, (uint32_t)root, vm);   // root node, count 1, kind node
+      if (lane == 0) st.set(0, first_entry, vm);      // root (or half of its children)
     }
     __syncwarp();
 
@@ -788,11 +809,30 @@ k_walk(WalkArgs A) {
     if (VJP && valid) {                         // own-term gradient, sorted order
       double gx, gy, gz;
       acc.get(acc64, gx, gy, gz);
-      A.g_own[3 * gi] = -gx;
-      A.g_own[3 * gi + 1] = -gy;
-      A.g_own[3 * gi + 2] = -gz;
+      if (A.split > 1) {
+        atomicAdd(&A.g_own[3 * gi], -gx);
+        atomicAdd(&A.g_own[3 * gi + 1], -gy);
+        atomicAdd(&A.g_own[3 * gi + 2], -gz);
+      } else {
+        A.g_own[3 * gi] = -gx;
+        A.g_own[3 * gi + 1] = -gy;
+        A.g_own[3 * gi + 2] = -gz;
+      }
     }
-    if (!VJP && valid) {
+    if (!VJP && valid && A.split > 1) {         // partial sums of a split task
+      double ax, ay, az;
+      acc.get(acc64, ax, ay, az);
+      const int64_t ci = A.perm[gi];
+      atomicAdd(&A.acc[3 * ci], ax * A.G);
+      atomicAdd(&A.acc[3 * ci + 1], ay * A.G);
+      atomicAdd(&A.acc[3 * ci + 2], az * A.G);
+      if (COUNT) {
+        atomicAdd(&A.counts[3 * ci], c_m2p);
+        atomicAdd(&A.counts[3 * ci + 1], c_p2p);
+        atomicAdd(&A.counts[3 * ci + 2], c_tests);
+      }
+    }
+    if (!VJP && valid && A.split == 1) {
       double ax, ay, az;
       acc.get(acc64, ax, ay, az);
       ax *= A.G; ay *= A.G; az *= A.G;
@@ -844,6 +884,22 @@ int launch_walk(Ctx *c, WalkArgs A) {
   int bps = blocks_per_sm[dev] - shape.blocks_less;
   if (bps < 1) bps = 1;
   int blocks = bps * c->num_sms;
+  // split tasks when there are no more of them than resident warps
+  const int base_tasks = A.ntasks;
+  A.split = (A.mac_guard && base_tasks <= blocks * kWalkWarps) ? 2 : 1;
+  A.ntasks = base_tasks * A.split;
+  if (A.split > 1) {
+    const size_t n3 = 3 * (size_t)A.n;
+    if (MODE == kModeVjp) {
+      GRAV_CUDA_TRY(cudaMemsetAsync(A.g_own, 0, sizeof(double) * n3, c->stream));
+    } else {
+      GRAV_CUDA_TRY(cudaMemsetAsync(A.acc, 0, sizeof(double) * n3, c->stream));
+      if (MODE == kModeCount)
+        GRAV_CUDA_TRY(cudaMemsetAsync(A.counts, 0, sizeof(int32_t) * n3, c->stream));
+    }
+  }
+  double *kick_vel = A.vel;                 // the fused kick needs the whole sum
+  if (A.split > 1) A.vel = nullptr;
   const int need = (A.ntasks + kWalkWarps - 1) / kWalkWarps;
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
@@ -860,7 +916,9 @@ int launch_walk(Ctx *c, WalkArgs A) {
   GRAV_CUDA_TRY(cudaMemsetAsync(A.task_counter, 0, sizeof(unsigned) * A.nqueues, c->stream));
   kern<<<blocks, 32 * kWalkWarps, smem, c->stream>>>(A);
   ++c->launches;
-  return cuda_status(cudaGetLastError());
+  GRAV_CUDA_TRY(cudaGetLastError());
+  if (A.split > 1 && kick_vel) return launch_kick(c, A.n, kick_vel, A.acc, A.kick);
+  return GRAVITY_OK;
 }
 
 }  // namespace
