@@ -134,6 +134,22 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- CPU oracle
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """Largest x over all ranks: one all-reduce (the identity on a single rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(n_per_rank: int, world: int, t_max_ms: float) -> float:
+    """Body-forces/s of the whole job: every rank's bodies over the slowest rank's time."""
+    return world * n_per_rank / (t_max_ms * 1e-3)
+
+
 def oracle_eval(pos, m, args, ntarg):
     """Oracle tree build (all bodies) + walk of ntarg seeded targets; returns the
     extrapolated body-forces/s of a full evaluation and the times."""
@@ -278,12 +294,8 @@ def run_ours(args, rank, world, local_rank):
     t_build = sum(e0.elapsed_time(e1) for e0, e1, _ in ev) / args.steps
     t_walk = sum(e1.elapsed_time(e2) for _, e1, e2 in ev) / args.steps
     t_step = t_build + t_walk
-    t_max = t_step
-    if world > 1:
-        t = torch.tensor([t_step], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * n / (t_max * 1e-3)
+    t_max = max_over_ranks(t_step, world, dev)
+    value = whole_job_value(n, world, t_max)
 
     # error against the direct sum, and the direct-sum throughput on the same GPU
     extra = {}
@@ -335,13 +347,10 @@ def run_ours(args, rank, world, local_rank):
         t0 = time.perf_counter()
         for _ in range(ke):
             g.gravity_forces_host(ctx, ph, mh, args.theta, args.eps, p, ah)
-        te = (time.perf_counter() - t0) / ke
-        tt = torch.tensor([te], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * n / float(tt.item()), "unit": UNIT,
+        te = max_over_ranks((time.perf_counter() - t0) / ke, world, dev)
+        e2e = {"value": whole_job_value(n, world, 1e3 * te), "unit": UNIT,
                "h2d_bytes_per_step": int(ph.nbytes + mh.nbytes), "d2h_bytes_per_step": int(ah.nbytes),
-               "ms_per_step": 1e3 * float(tt.item()),
+               "ms_per_step": 1e3 * te,
                "api": "gravity_forces_host (pinned host buffers, copies + build + walk + sync)"}
 
     ens = None if args.no_ensemble else ensemble_leg(args, g, dev, rank)
