@@ -39,7 +39,7 @@ def _rank_main(rank, world, port, out):
 
 def test_max_over_ranks_and_whole_job_value_two_ranks():
     world = 2
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.spawn(_rank_main, args=(world, _free_port(), out), nprocs=world, join=True)
         res = dict(out)
