@@ -472,20 +472,41 @@ def gradient_leg(args, g, dev, rank):
         return float(axis_ratio_loss(P, M))
 
     rng = np.random.default_rng(args.seed + 201)
-    gn = np.sqrt((gx * gx).sum() + (gv * gv).sum())
-    gmax = max(np.abs(gx).max(), np.abs(gv).max())
-    dirs = [("gradient", gx / gmax, gv / gmax)]
-    for k in range(4):
-        dirs.append((f"random{k}", rng.standard_normal(pos.shape), rng.standard_normal(pos.shape)))
-    fd_dirs = []
-    for h in (1e-3, 1e-4):
+    unit = [(f"random{k}", rng.standard_normal(pos.shape), rng.standard_normal(pos.shape))
+            for k in range(4)]
+    # random affine fields (x -> A x, v -> B x): smooth directions that move neighbours
+    # together, so close pairs do not dominate the differences
+    affine = [(f"affine{k}", pos @ rng.standard_normal((3, 3)).T, pos @ rng.standard_normal((3, 3)).T)
+              for k in range(4)]
+
+    def fd_check(th, gx_, gv_, dirs, hs, richardson=False):
+        """Central differences of the loss of the same GPU forward along each direction,
+        for each step h; with richardson, (4 D(h/2) - D(h)) / 3 cancels the h^2 term."""
+        gn = np.sqrt((gx_ * gx_).sum() + (gv_ * gv_).sum())
+        out = []
         for name, dx, dv in dirs:
-            fd = (loss_at(pos + h * dx, vel + h * dv) - loss_at(pos - h * dx, vel - h * dv)) / (2 * h)
-            ad = float((gx * dx).sum() + (gv * dv).sum())
+            def cd(hh):
+                return (loss_at(pos + hh * dx, vel + hh * dv, th) -
+                        loss_at(pos - hh * dx, vel - hh * dv, th)) / (2 * hh)
+            ad = float((gx_ * dx).sum() + (gv_ * dv).sum())
             cs = gn * float(np.sqrt((dx * dx).sum() + (dv * dv).sum()))
-            fd_dirs.append({"direction": name, "h": h, "fd": fd, "adjoint": ad,
+            for h in hs:
+                fd = cd(h)
+                if richardson:
+                    fd = (4.0 * cd(0.5 * h) - fd) / 3.0
+                out.append({"direction": name, "theta": th, "h": h, "richardson": richardson,
+                            "fd": fd, "adjoint": ad,
                             "rel_err": abs(fd - ad) / abs(ad) if ad else None,
                             "err_over_norm_bound": abs(fd - ad) / cs})
+        return out
+
+    # The loss depends on the eigenvalues of S, which are nearly degenerate for a sphere
+    # (gaps ~ N^-1/2): an affine step moves them by O(h), so central differences converge
+    # to the derivative only once h is well below the gaps (O(h^2) error, seen below).
+    gmax = max(np.abs(gx).max(), np.abs(gv).max())
+    fd_dirs = fd_check(theta, gx, gv, [("gradient", gx / gmax, gv / gmax)], (1e-3,))
+    fd_dirs += fd_check(theta, gx, gv, affine, (1e-3, 1e-4, 1e-5))
+    fd_dirs += fd_check(theta, gx, gv, unit, (4e-3,), richardson=True)
     coords = rng.choice(3 * n, size=32, replace=False)
     coord_rel, h_c = [], 1e-3
     for c in coords:
@@ -495,11 +516,14 @@ def gradient_leg(args, g, dev, rank):
         fd = (loss_at(pos + h_c * dx, vel) - loss_at(pos - h_c * dx, vel)) / (2 * h_c)
         coord_rel.append(abs(fd - gx[i, a]) / (abs(gx[i, a]) + 1e-300))
 
-    # gradient of the exact sum: the same pipeline at theta = 0
+    # gradient of the exact sum: the same pipeline at theta = 0 (no opening decisions,
+    # so its differences carry FP32 rounding only)
     _, gx0, gv0, t_fwd0, t_bwd0 = run(0.0)
     d_exact = {"rel_l2_x": float(np.linalg.norm(gx - gx0) / np.linalg.norm(gx0)),
                "rel_l2_v": float(np.linalg.norm(gv - gv0) / np.linalg.norm(gv0)),
                "fwd_ms_theta0": t_fwd0, "bwd_ms_theta0": t_bwd0}
+    fd_dirs += fd_check(0.0, gx0, gv0, affine[:2], (1e-3, 1e-4, 1e-5))
+    fd_dirs += fd_check(0.0, gx0, gv0, unit[:2], (1e-3, 1e-4))
 
     # the vector-Jacobian-product kernel alone, on the tree of the initial positions
     P0 = torch.tensor(pos, device=dev)

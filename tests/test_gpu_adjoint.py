@@ -162,6 +162,14 @@ def _loss_fd(g, pos, vel, m, dt, nsteps, theta, eps, leaf_max, directions, h):
 
 @pytest.mark.parametrize("theta", [0.0, 0.5])
 def test_loss_gradient_vs_finite_differences(gpu, theta):
+    """The loss is a function of the eigenvalues of S, nearly degenerate for a round cloud,
+    so a central difference converges to the derivative only for steps well below the
+    eigenvalue gaps (an O(h^2) error that is large at h = 1e-3 along affine directions).
+    theta = 0 (the exact sum) is smooth: smooth (affine) directions at h = 1e-5 must agree
+    to 1e-4 relative.  At theta = 0.5 the forward map is only piecewise smooth (opening
+    decisions flip under the perturbation); the adjoint is the derivative with the
+    decisions frozen, checked against differences relative to the largest derivative a
+    direction of that norm can have."""
     from paper_1912_04197_gb300.adjoint import leapfrog
     from paper_1912_04197_gb300.loss import axis_ratio_loss
     pos, vel, m = inputs.rubble_pile(4096, seed=41)
@@ -175,14 +183,21 @@ def test_loss_gradient_vs_finite_differences(gpu, theta):
     gx, gv = torch.autograd.grad(L, (x0, v0))
     gx, gv = gx.cpu().numpy(), gv.cpu().numpy()
     rng = np.random.default_rng(42)
-    dirs = []
-    for _ in range(3):                         # random directions over all coordinates
-        dirs.append((rng.standard_normal(pos.shape), rng.standard_normal(pos.shape)))
-    dirs.append((gx / np.abs(gx).max(), gv / np.abs(gx).max()))   # along the gradient
-    fd = _loss_fd(gpu, pos, vel, m, dt, nsteps, theta, eps, leaf, dirs, h=1e-4)
-    ad = np.array([(gx * dx).sum() + (gv * dv).sum() for dx, dv in dirs])
-    # relative to the largest derivative a direction of that norm can have
     gnorm = np.sqrt((gx * gx).sum() + (gv * gv).sum())
-    scale = np.array([gnorm * np.sqrt((dx * dx).sum() + (dv * dv).sum()) for dx, dv in dirs])
-    rel = np.abs(fd - ad) / scale
-    assert np.all(rel <= 1e-4), (rel, fd, ad)
+    if theta == 0.0:
+        dirs = [(pos @ rng.standard_normal((3, 3)).T, pos @ rng.standard_normal((3, 3)).T)
+                for _ in range(3)]
+        fd = _loss_fd(gpu, pos, vel, m, dt, nsteps, theta, eps, leaf, dirs, h=1e-5)
+        ad = np.array([(gx * dx).sum() + (gv * dv).sum() for dx, dv in dirs])
+        rel = np.abs(fd - ad) / np.abs(ad)
+        assert np.all(rel <= 1e-4), (rel, fd, ad)
+    else:
+        dirs = [(rng.standard_normal(pos.shape), rng.standard_normal(pos.shape))
+                for _ in range(3)]
+        dirs.append((gx / np.abs(gx).max(), gv / np.abs(gx).max()))   # along the gradient
+        fd = _loss_fd(gpu, pos, vel, m, dt, nsteps, theta, eps, leaf, dirs, h=1e-4)
+        ad = np.array([(gx * dx).sum() + (gv * dv).sum() for dx, dv in dirs])
+        scale = np.array([gnorm * np.sqrt((dx * dx).sum() + (dv * dv).sum()) for dx, dv in dirs])
+        rel = np.abs(fd - ad) / scale
+        assert np.all(rel <= 1e-4), (rel, fd, ad)
+        assert abs(fd[-1] - ad[-1]) <= 1e-3 * abs(ad[-1])   # along the gradient, plain relative
