@@ -1,7 +1,7 @@
 """GPU walk (kernel 5, Sec. 2.1), direct sum (Eq. Newton) and stepping (Sec. 2.3)
 against the FP64 oracle on the same seeded inputs.
 
-Tolerances (derived from the FP32 pair arithmetic, see DESIGN.md "Tolerances"):
+Tolerances (derived from the FP32 pair arithmetic):
   * decision counts (node terms, body terms) per body: exact;
   * tree and direct accelerations: |a - a_oracle| <= 1e-6 * sum_k |term_k| for every
     body (FP32 terms with hi/lo differences carry ~2^-22 relative error each, and
