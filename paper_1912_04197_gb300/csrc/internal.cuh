@@ -153,6 +153,12 @@ __device__ __forceinline__ void latch_error(unsigned *status, unsigned bit) {
   atomicOr(status, bit);
 }
 
+// 2^-d as a double, built from its exponent bits (0 <= d <= 1022): side * pow2_neg(d)
+// equals ldexp(side, -d) exactly while the product stays normal.
+__device__ __forceinline__ double pow2_neg(int d) {
+  return __longlong_as_double((long long)(1023 - d) << 52);
+}
+
 // hi/lo split of an FP64 value into two FP32 values with hi + lo ~ x to ~2^-48.
 __device__ __forceinline__ void split_df(double x, float &hi, float &lo) {
   hi = __double2float_rn(x);

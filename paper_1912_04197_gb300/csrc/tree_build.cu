@@ -810,7 +810,7 @@ __device__ void write_records(const MomArgs &A, int id, double m, const double *
   for (int a = 0; a < 3; ++a) split_df(com[a], h[a], lo[a]);
   const int4 t = A.topo[id];
   const double side = A.geom[8 * (A.seg_sorted ? A.seg_sorted[t.z] : 0) + 3];
-  double l = ldexp(side, -A.ndepth[id]);
+  double l = __dmul_rn(side, pow2_neg(A.ndepth[id]));
   float l2 = single_body ? -1.0f : __double2float_rn(dm(l, l));
   A.rec0[id] = make_float4(h[0], h[1], h[2], __double2float_rn(m));
   A.rec1[id] = make_float4(lo[0], lo[1], lo[2], l2);

@@ -624,7 +624,7 @@ k_walk(WalkArgs A) {
               const double ddx = __dsub_rn(X, x), ddy = __dsub_rn(Y, y), ddz = __dsub_rn(Z, z);
               const double D2d = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)),
                                            __dmul_rn(ddz, ddz));
-              const double l = ldexp(side, -A.ndepth[node]);
+              const double l = __dmul_rn(side, pow2_neg(A.ndepth[node]));
               a_i = __dmul_rn(l, l) < __dmul_rn(A.theta2d, D2d);
               if (COUNT) atomicAdd(&A.stats[kStatFp64], 1ull);
             } else {
