@@ -536,26 +536,40 @@ def gradient_leg(args, g, dev, rank):
 
     # the vector-Jacobian-product kernel alone, on the tree of the initial positions
     P0 = torch.tensor(pos, device=dev)
-    lam = torch.tensor(rng.standard_normal(pos.shape), device=dev)
-    out = torch.empty_like(P0)
-    cnt = torch.empty((n, 3), dtype=torch.int32, device=dev)
-    g.gravity_tree_build(ctx, P0, M, p)
-    g.gravity_forces_counted(ctx, theta, eps, out, cnt)
-    c = cnt.to(torch.int64).sum(0).cpu().numpy()
-    terms, tests = int(c[0] + c[1]), int(c[2])
-    for _ in range(3):
-        g.gravity_forces_vjp(ctx, theta, eps, lam, out)
-    reps = 20
-    v0e, v1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    v0e.record(stream)
-    for _ in range(reps):
-        g.gravity_forces_vjp(ctx, theta, eps, lam, out)
-    v1e.record(stream)
-    torch.cuda.synchronize(dev)
-    g.gravity_sync(ctx)
-    t_vjp = v0e.elapsed_time(v1e) / reps
     props = torch.cuda.get_device_properties(dev)
-    flops = terms * FLOP_VJP + tests * FLOP_MAC
+    fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * 2070e6
+
+    def time_vjp(P_, M_, p_, th, ep):
+        """Average time of one vector-Jacobian product on the tree of P_ (and its FLOP)."""
+        lam_ = torch.tensor(rng.standard_normal(tuple(P_.shape)), device=dev)
+        out_ = torch.empty_like(P_)
+        cnt_ = torch.empty((P_.shape[0], 3), dtype=torch.int32, device=dev)
+        g.gravity_tree_build(ctx, P_, M_, p_)
+        g.gravity_forces_counted(ctx, th, ep, out_, cnt_)
+        c_ = cnt_.to(torch.int64).sum(0).cpu().numpy()
+        for _ in range(3):
+            g.gravity_forces_vjp(ctx, th, ep, lam_, out_)
+        reps = 20
+        e0_, e1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0_.record(stream)
+        for _ in range(reps):
+            g.gravity_forces_vjp(ctx, th, ep, lam_, out_)
+        e1_.record(stream)
+        torch.cuda.synchronize(dev)
+        g.gravity_sync(ctx)
+        ms = e0_.elapsed_time(e1_) / reps
+        fl = int(c_[0] + c_[1]) * FLOP_VJP + int(c_[2]) * FLOP_MAC
+        return {"ms": ms, "terms": int(c_[0] + c_[1]), "opening_tests": int(c_[2]),
+                "flop_per_term": FLOP_VJP, "achieved_tflops": fl / (ms * 1e-3) / 1e12,
+                "frac_of_fp32_peak_at_max_clock": fl / (ms * 1e-3) / fp32_peak,
+                "includes": "VJP walk + leaf-chain finishing pass + 2 memsets"}
+
+    vjp = time_vjp(P0, M, p, theta, eps)
+    # the same kernel on the headline workload (monopole: the product covers order 0)
+    hpos, _, hm = inputs.clumpy_plummer(1_048_576, seed=args.seed)
+    vjp_1m = time_vjp(torch.tensor(hpos, device=dev), torch.tensor(hm, device=dev),
+                      g.params(order=0, leaf_max=16), theta, 1e-3)
+    vjp_1m["workload"] = "clumpy aggregate, 1,048,576 bodies, theta 0.5, monopole, leaf 16"
     return {"workload": f"N={n} uniform sphere at rest, m=1/N, eps={eps}, {nsteps} KDK steps "
                         f"dt={dt}, theta={theta} monopole, leaf 1, checkpoints every {every}; "
                         "loss (rho2-0.8)^2+(rho3-0.6)^2 of the final second-moment tensor",
@@ -566,12 +580,7 @@ def gradient_leg(args, g, dev, rank):
                                                       "median_rel_err": float(np.median(coord_rel)),
                                                       "max_rel_err": float(np.max(coord_rel))}},
             "vs_exact_sum_gradient": d_exact,
-            "vjp_kernel": {"ms": t_vjp, "terms": terms, "opening_tests": tests,
-                           "flop_per_term": FLOP_VJP, "achieved_tflops": flops / (t_vjp * 1e-3) / 1e12,
-                           "frac_of_fp32_peak_at_max_clock":
-                               flops / (t_vjp * 1e-3) /
-                               (props.multi_processor_count * FP32_LANES_PER_SM * 2 * 2070e6),
-                           "includes": "VJP walk + leaf-chain finishing pass + 2 memsets"}}
+            "vjp_kernel": vjp, "vjp_kernel_1M": vjp_1m}
 
 
 def experiment_accuracy(args):
