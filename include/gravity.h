@@ -48,6 +48,13 @@ enum gravity_status {
 
 typedef struct gravity_ctx gravity_ctx;
 
+/* Caller-supplied device allocator (see gravity_set_allocator).  alloc stores a device
+ * pointer of at least `bytes` bytes (aligned to 256 bytes) in *ptr and returns 0, or
+ * returns non-zero on failure; release frees a pointer alloc returned.  `user` is passed
+ * through unchanged. */
+typedef int (*gravity_alloc_fn)(void **ptr, size_t bytes, void *user);
+typedef void (*gravity_free_fn)(void *ptr, void *user);
+
 /* Tunables.  Fill with gravity_params_default() and change what you need. */
 typedef struct gravity_params {
   double G;            /* gravitational constant of Eq. (Newton); default 1.0 */
@@ -80,6 +87,17 @@ int gravity_destroy(gravity_ctx *ctx);
 
 /* Change the stream later calls are enqueued on. */
 int gravity_set_stream(gravity_ctx *ctx, void *cuda_stream);
+
+/* Route every device allocation of the context through the caller's allocator (for
+ * instance an application's memory pool); alloc = release = NULL restores
+ * cudaMalloc/cudaFree.  Synchronises the context's stream, then releases ALL of the
+ * context's device memory (the tree, the cloud segmentation, every scratch buffer) with
+ * the allocator that made it and re-creates the small fixed buffers with the new one: the
+ * context is left as after gravity_create (no tree, one cloud).  An allocation the
+ * allocator refuses makes the call that needed it return GRAVITY_E_NOMEM, with no buffer
+ * left half-made; the context stays usable. */
+int gravity_set_allocator(gravity_ctx *ctx, gravity_alloc_fn alloc, gravity_free_fn release,
+                          void *user);
 
 /* Kernels 1-4 of the paper's five-kernel list (Sec. 2.1, "CUDA implementation"):
  * bounding cube of all bodies (the root), octree construction (63-bit Morton keys,
@@ -266,6 +284,13 @@ enum gravity_debug_item {
   GRAVITY_DBG_WALKSTATS = 10
 };
 int gravity_debug_export(gravity_ctx *ctx, int what, void *host_dst, size_t bytes);
+
+/* Settings for failure testing.  GRAVITY_DBGSET_STACK_CAP: largest number of walk stack
+ * entries a warp may hold (1 .. the built-in capacity; 0 restores the full capacity); a
+ * walk that needs more latches GRAVITY_E_INTERNAL (reported by gravity_sync) instead of
+ * growing, as an exhausted stack does.  GRAVITY_E_ARG for an unknown item or value. */
+enum gravity_debug_setting { GRAVITY_DBGSET_STACK_CAP = 1 };
+int gravity_debug_set(gravity_ctx *ctx, int what, int64_t value);
 
 /* Number of kernels this context has enqueued since it was created (host-side
  * counter, no synchronisation). */

@@ -39,28 +39,38 @@ int integrate_one(Ctx &c, int64_t n, double *pos, double *vel, const double *mas
   return walk_forces(&c, theta, eps, acc, nullptr, kdk ? vel : nullptr, kdk ? h_kick : 0.0);
 }
 
+int ctx_malloc(Ctx *c, void **p, size_t bytes) {
+  *p = nullptr;
+  if (c->user_alloc) {
+    if (c->user_alloc(p, bytes, c->alloc_user) != 0 || !*p) {
+      *p = nullptr;
+      return GRAVITY_E_NOMEM;
+    }
+    return GRAVITY_OK;
+  }
+  return cuda_status(cudaMalloc(p, bytes));
+}
+
+void ctx_free(Ctx *c, void *p) {
+  if (!p) return;
+  if (c->user_free) c->user_free(p, c->alloc_user);
+  else cudaFree(p);
+}
+
 namespace {
 
-template <typename T>
-void free_ptr(T *&p) {
-  if (p) cudaFree(p);
-  p = nullptr;
-}
-
-void free_tree(Tree &t) {
-  free_ptr(t.keys); free_ptr(t.keys_alt); free_ptr(t.idx); free_ptr(t.idx_alt);
-  free_ptr(t.hist); free_ptr(t.scan_aux); free_ptr(t.bbox_part);
-  free_ptr(t.pos_s); free_ptr(t.mass_s); free_ptr(t.body_hi); free_ptr(t.body_lo);
-  free_ptr(t.bchild); free_ptr(t.bparent); free_ptr(t.bfirst); free_ptr(t.blast);
-  free_ptr(t.bplen); free_ptr(t.bnchild); free_ptr(t.bbase);
-  free_ptr(t.topo); free_ptr(t.nparent); free_ptr(t.ndepth); free_ptr(t.nlist);
-  free_ptr(t.nmass); free_ptr(t.ncom); free_ptr(t.nquad); free_ptr(t.nrec0); free_ptr(t.nrec1);
-  free_ptr(t.nquadf);
-}
-
-template <typename T>
-cudaError_t alloc(T *&p, int64_t count) {
-  return cudaMalloc(reinterpret_cast<void **>(&p), sizeof(T) * (size_t)(count > 0 ? count : 1));
+void free_tree(Ctx *c) {
+  Tree &t = c->t;
+  ctx_release(c, t.keys); ctx_release(c, t.keys_alt); ctx_release(c, t.idx);
+  ctx_release(c, t.idx_alt); ctx_release(c, t.hist); ctx_release(c, t.scan_aux);
+  ctx_release(c, t.bbox_part); ctx_release(c, t.pos_s); ctx_release(c, t.mass_s);
+  ctx_release(c, t.body_hi); ctx_release(c, t.body_lo); ctx_release(c, t.bchild);
+  ctx_release(c, t.bparent); ctx_release(c, t.bfirst); ctx_release(c, t.blast);
+  ctx_release(c, t.bplen); ctx_release(c, t.bnchild); ctx_release(c, t.bbase);
+  ctx_release(c, t.topo); ctx_release(c, t.nparent); ctx_release(c, t.ndepth);
+  ctx_release(c, t.nlist); ctx_release(c, t.nmass); ctx_release(c, t.ncom);
+  ctx_release(c, t.nquad); ctx_release(c, t.nrec0); ctx_release(c, t.nrec1);
+  ctx_release(c, t.nquadf);
 }
 
 int check_params(const gravity_params *p) {
@@ -83,7 +93,7 @@ int ensure_capacity(Ctx *c, int64_t n) {
   if (n <= c->cap) return GRAVITY_OK;
   GRAV_CUDA_TRY(cudaStreamSynchronize(c->stream));
   Tree &t = c->t;
-  free_tree(t);
+  free_tree(c);
   c->cap = 0;
   int64_t cap = n + n / 8;
   if (cap < 1024) cap = 1024;
@@ -91,8 +101,8 @@ int ensure_capacity(Ctx *c, int64_t n) {
   const int64_t ntiles = (cap + 2047) / 2048;
   const int64_t scan_n = (256 * ntiles > cap ? 256 * ntiles : cap);
   const int64_t nodes = 2 * cap;
-  cudaError_t e = cudaSuccess;
-#define GRAV_ALLOC(p, cnt) if (e == cudaSuccess) e = alloc(p, cnt)
+  int rc = GRAVITY_OK;
+#define GRAV_ALLOC(p, cnt) if (rc == GRAVITY_OK) rc = ctx_alloc(c, p, cnt)
   GRAV_ALLOC(t.keys, cap); GRAV_ALLOC(t.keys_alt, cap);
   GRAV_ALLOC(t.idx, cap); GRAV_ALLOC(t.idx_alt, cap);
   GRAV_ALLOC(t.hist, 257 * 10 + 10 * 256 * ntiles);   // radix sort: counts + tile states
@@ -108,18 +118,19 @@ int ensure_capacity(Ctx *c, int64_t n) {
   GRAV_ALLOC(t.nmass, nodes); GRAV_ALLOC(t.ncom, 3 * nodes); GRAV_ALLOC(t.nquad, 6 * nodes);
   GRAV_ALLOC(t.nrec0, nodes); GRAV_ALLOC(t.nrec1, nodes); GRAV_ALLOC(t.nquadf, 2 * nodes);
 #undef GRAV_ALLOC
-  if (e != cudaSuccess) {
-    free_tree(t);
-    return cuda_status(e);
+  if (rc != GRAVITY_OK) {
+    free_tree(c);
+    return rc;
   }
   c->cap = cap;
   return GRAVITY_OK;
 }
 
 namespace {
-void free_segments(Segs &sg) {
-  free_ptr(sg.off); free_ptr(sg.seg_of); free_ptr(sg.seg_sorted);
-  free_ptr(sg.task_begin); free_ptr(sg.task_end); free_ptr(sg.task_seg);
+void free_segments(Ctx *c) {
+  Segs &sg = c->seg;
+  ctx_release(c, sg.off); ctx_release(c, sg.seg_of); ctx_release(c, sg.seg_sorted);
+  ctx_release(c, sg.task_begin); ctx_release(c, sg.task_end); ctx_release(c, sg.task_seg);
   sg = Segs{};
 }
 }  // namespace
@@ -129,14 +140,14 @@ void free_segments(Segs &sg) {
 // task list (32 consecutive bodies of one cloud per task) and the geometry array.
 int set_segments(Ctx *c, int nseg, const int64_t *off) {
   GRAV_CUDA_TRY(cudaStreamSynchronize(c->stream));
-  free_segments(c->seg);
+  free_segments(c);
   if (nseg <= 1) return GRAVITY_OK;
   if (!off || off[0] != 0 || nseg > 65536) return GRAVITY_E_ARG;
   for (int k = 0; k < nseg; ++k)
     if (off[k + 1] <= off[k]) return GRAVITY_E_ARG;
   const int64_t n = off[nseg];
   if (n > kMaxBodies) return GRAVITY_E_ARG;
-  Segs sg;
+  Segs &sg = c->seg;
   sg.nseg = nseg;
   sg.cbits = 0;
   while ((1 << sg.cbits) < nseg) ++sg.cbits;
@@ -149,26 +160,74 @@ int set_segments(Ctx *c, int nseg, const int64_t *off) {
       ts.push_back(k);
     }
   sg.ntasks = (int)tb.size();
-  cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = alloc(sg.off, nseg + 1);
-  if (e == cudaSuccess) e = alloc(sg.seg_of, n);
-  if (e == cudaSuccess) e = alloc(sg.seg_sorted, n);
-  if (e == cudaSuccess) e = alloc(sg.task_begin, sg.ntasks);
-  if (e == cudaSuccess) e = alloc(sg.task_end, sg.ntasks);
-  if (e == cudaSuccess) e = alloc(sg.task_seg, sg.ntasks);
-  if (e == cudaSuccess) e = cudaMemcpy(sg.off, off, sizeof(int64_t) * (nseg + 1), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(sg.task_begin, tb.data(), sizeof(int32_t) * sg.ntasks, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(sg.task_end, te.data(), sizeof(int32_t) * sg.ntasks, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(sg.task_seg, ts.data(), sizeof(int32_t) * sg.ntasks, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && c->t.geom_cap < nseg) {
-    free_ptr(c->t.geom);
-    c->t.geom_cap = 0;
-    e = alloc(c->t.geom, 8 * (int64_t)nseg);
-    if (e == cudaSuccess) c->t.geom_cap = nseg;
+  int rc = GRAVITY_OK;
+  if (rc == GRAVITY_OK) rc = ctx_alloc(c, sg.off, nseg + 1);
+  if (rc == GRAVITY_OK) rc = ctx_alloc(c, sg.seg_of, n);
+  if (rc == GRAVITY_OK) rc = ctx_alloc(c, sg.seg_sorted, n);
+  if (rc == GRAVITY_OK) rc = ctx_alloc(c, sg.task_begin, sg.ntasks);
+  if (rc == GRAVITY_OK) rc = ctx_alloc(c, sg.task_end, sg.ntasks);
+  if (rc == GRAVITY_OK) rc = ctx_alloc(c, sg.task_seg, sg.ntasks);
+  if (rc == GRAVITY_OK)
+    rc = cuda_status(cudaMemcpy(sg.off, off, sizeof(int64_t) * (nseg + 1), cudaMemcpyHostToDevice));
+  if (rc == GRAVITY_OK)
+    rc = cuda_status(cudaMemcpy(sg.task_begin, tb.data(), sizeof(int32_t) * sg.ntasks, cudaMemcpyHostToDevice));
+  if (rc == GRAVITY_OK)
+    rc = cuda_status(cudaMemcpy(sg.task_end, te.data(), sizeof(int32_t) * sg.ntasks, cudaMemcpyHostToDevice));
+  if (rc == GRAVITY_OK)
+    rc = cuda_status(cudaMemcpy(sg.task_seg, ts.data(), sizeof(int32_t) * sg.ntasks, cudaMemcpyHostToDevice));
+  if (rc == GRAVITY_OK && c->t.geom_cap < nseg) {
+    double *g = nullptr;
+    rc = ctx_alloc(c, g, 8 * (int64_t)nseg);
+    if (rc == GRAVITY_OK) {
+      ctx_release(c, c->t.geom);
+      c->t.geom = g;
+      c->t.geom_cap = nseg;
+    }
   }
-  c->seg = sg;
-  if (e != cudaSuccess) { free_segments(c->seg); return cuda_status(e); }
+  if (rc != GRAVITY_OK) { free_segments(c); return rc; }
   return fill_segment_ids(c);
+}
+
+// The small fixed buffers every context holds (status word, one cloud's geometry,
+// counters); and the release of everything the context owns.
+int alloc_base(Ctx *c) {
+  int rc = GRAVITY_OK;
+  if (rc == GRAVITY_OK) rc = ctx_alloc(c, c->d_status, 1);
+  if (rc == GRAVITY_OK) rc = ctx_alloc(c, c->t.geom, 8);
+  if (rc == GRAVITY_OK) c->t.geom_cap = 1;
+  if (rc == GRAVITY_OK) rc = ctx_alloc(c, c->t.bbox_ticket, 1);
+  if (rc == GRAVITY_OK) rc = ctx_alloc(c, c->t.nnodes, 1);
+  if (rc == GRAVITY_OK) rc = ctx_alloc(c, c->t.scalars, 128);
+  if (rc == GRAVITY_OK) rc = ctx_alloc(c, c->walk_stats, 16);
+  if (rc == GRAVITY_OK) rc = ctx_alloc(c, c->walk_queues, c->num_sms + 1);
+  if (rc == GRAVITY_OK) rc = cuda_status(cudaMemset(c->walk_stats, 0, 16 * sizeof(unsigned long long)));
+  if (rc == GRAVITY_OK) rc = cuda_status(cudaMemset(c->d_status, 0, sizeof(unsigned)));
+  if (rc == GRAVITY_OK) rc = cuda_status(cudaMemset(c->t.bbox_ticket, 0, sizeof(unsigned)));
+  if (rc == GRAVITY_OK) rc = cuda_status(cudaMemset(c->t.nnodes, 0, sizeof(int32_t)));
+  return rc;
+}
+
+void free_all(Ctx *c) {
+  free_tree(c);
+  free_segments(c);
+  c->cap = 0;
+  c->n = 0;
+  c->have_tree = false;
+  ctx_release(c, c->t.geom); c->t.geom_cap = 0;
+  ctx_release(c, c->t.bbox_ticket); ctx_release(c, c->t.nnodes); ctx_release(c, c->t.scalars);
+  ctx_release(c, c->walk_stats); ctx_release(c, c->walk_queues);
+  ctx_release(c, c->walk_gstack); c->walk_gstack_cap = 0;
+  ctx_release(c, c->vjp_own); ctx_release(c, c->vjp_body); ctx_release(c, c->vjp_node);
+  c->vjp_cap = 0;
+  ctx_release(c, c->adj_levels); ctx_release(c, c->adj_work);
+  c->adj_levels_cap = c->adj_work_cap = 0;
+  ctx_release(c, c->dir_hi); ctx_release(c, c->dir_lo); c->dir_cap = 0;
+  ctx_release(c, c->diag_buf); c->diag_cap = 0;
+  ctx_release(c, c->h2d_pos); ctx_release(c, c->h2d_mass); ctx_release(c, c->h2d_acc);
+  c->h2d_cap = 0;
+  if (c->graph.exec) cudaGraphExecDestroy(c->graph.exec);
+  c->graph = StepGraph{};
+  ctx_release(c, c->d_status);
 }
 
 }  // namespace grav
@@ -204,18 +263,7 @@ int gravity_create(gravity_ctx **out, int device, void *cuda_stream) {
   gravity_params_default(&c.params);
   int rc = grav::set_device(c);
   if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, device));
-  if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMalloc(&c.d_status, sizeof(unsigned)));
-  if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMalloc(&c.t.geom, 8 * sizeof(double)));
-  if (rc == GRAVITY_OK) c.t.geom_cap = 1;
-  if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMalloc(&c.t.bbox_ticket, sizeof(unsigned)));
-  if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMalloc(&c.t.nnodes, sizeof(int32_t)));
-  if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMalloc(&c.t.scalars, 128 * sizeof(uint32_t)));
-  if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMalloc(&c.walk_stats, 16 * sizeof(unsigned long long)));
-  if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMalloc(&c.walk_queues, sizeof(unsigned) * (c.num_sms + 1)));
-  if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMemset(c.walk_stats, 0, 16 * sizeof(unsigned long long)));
-  if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMemset(c.d_status, 0, sizeof(unsigned)));
-  if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMemset(c.t.bbox_ticket, 0, sizeof(unsigned)));
-  if (rc == GRAVITY_OK) rc = grav::cuda_status(cudaMemset(c.t.nnodes, 0, sizeof(int32_t)));
+  if (rc == GRAVITY_OK) rc = grav::alloc_base(&c);
   if (rc != GRAVITY_OK) {
     gravity_destroy(h);
     return rc;
@@ -229,22 +277,48 @@ int gravity_destroy(gravity_ctx *h) {
   Ctx &c = h->c;
   cudaSetDevice(c.device);
   cudaStreamSynchronize(c.stream);
-  grav::free_tree(c.t);
-  grav::free_segments(c.seg);
-  grav::free_ptr(c.t.geom); grav::free_ptr(c.t.bbox_ticket); grav::free_ptr(c.t.nnodes);
-  grav::free_ptr(c.t.scalars);
-  grav::free_ptr(c.walk_stats);
-  grav::free_ptr(c.walk_gstack);
-  grav::free_ptr(c.walk_queues);
-  grav::free_ptr(c.vjp_own); grav::free_ptr(c.vjp_body); grav::free_ptr(c.vjp_node);
-  grav::free_ptr(c.adj_levels); grav::free_ptr(c.adj_work);
-  if (c.graph.exec) cudaGraphExecDestroy(c.graph.exec);
-  grav::free_ptr(c.d_status);
-  grav::free_ptr(c.dir_hi); grav::free_ptr(c.dir_lo); grav::free_ptr(c.diag_buf);
-  grav::free_ptr(c.h2d_pos); grav::free_ptr(c.h2d_mass); grav::free_ptr(c.h2d_acc);
+  grav::free_all(&c);
   cudaGetLastError();
   delete h;
   return GRAVITY_OK;
+}
+
+int gravity_set_allocator(gravity_ctx *h, gravity_alloc_fn alloc, gravity_free_fn release,
+                          void *user) {
+  if (!h || (alloc == nullptr) != (release == nullptr)) return GRAVITY_E_ARG;
+  Ctx &c = h->c;
+  int rc = grav::set_device(c);
+  if (rc) return rc;
+  GRAV_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  grav::free_all(&c);                       // with the allocator that made each buffer
+  const gravity_alloc_fn old_alloc = c.user_alloc;
+  const gravity_free_fn old_free = c.user_free;
+  void *const old_user = c.alloc_user;
+  c.user_alloc = alloc;
+  c.user_free = release;
+  c.alloc_user = user;
+  rc = grav::alloc_base(&c);
+  if (rc != GRAVITY_OK) {                   // keep a usable context on the previous allocator
+    grav::free_all(&c);
+    c.user_alloc = old_alloc;
+    c.user_free = old_free;
+    c.alloc_user = old_user;
+    const int rc2 = grav::alloc_base(&c);
+    return rc2 != GRAVITY_OK ? rc2 : rc;
+  }
+  return GRAVITY_OK;
+}
+
+int gravity_debug_set(gravity_ctx *h, int what, int64_t value) {
+  if (!h) return GRAVITY_E_ARG;
+  switch (what) {
+    case GRAVITY_DBGSET_STACK_CAP:
+      if (value < 0 || value > grav::walk_stack_capacity()) return GRAVITY_E_ARG;
+      h->c.stack_cap = (int)value;
+      return GRAVITY_OK;
+    default:
+      return GRAVITY_E_ARG;
+  }
 }
 
 int gravity_set_stream(gravity_ctx *h, void *cuda_stream) {
@@ -419,15 +493,15 @@ int leapfrog_adjoint(gravity_ctx *h, int64_t n, const double *pos0, const double
   if (c.adj_levels_cap < lev_need || c.adj_work_cap < 3 * n3) {
     GRAV_CUDA_TRY(cudaStreamSynchronize(c.stream));
     if (c.adj_levels_cap < lev_need) {
-      grav::free_ptr(c.adj_levels);
+      grav::ctx_release(&c, c.adj_levels);
       c.adj_levels_cap = 0;
-      GRAV_CUDA_TRY(cudaMalloc(&c.adj_levels, sizeof(double) * lev_need));
+      if ((rc = grav::ctx_alloc(&c, c.adj_levels, lev_need))) return rc;
       c.adj_levels_cap = lev_need;
     }
     if (c.adj_work_cap < 3 * n3) {
-      grav::free_ptr(c.adj_work);
+      grav::ctx_release(&c, c.adj_work);
       c.adj_work_cap = 0;
-      GRAV_CUDA_TRY(cudaMalloc(&c.adj_work, sizeof(double) * 3 * n3));
+      if ((rc = grav::ctx_alloc(&c, c.adj_work, 3 * n3))) return rc;
       c.adj_work_cap = 3 * n3;
     }
   }
@@ -517,11 +591,12 @@ int gravity_forces_host(gravity_ctx *h, int64_t n, const double *pos_host, const
   if ((rc = grav::set_device(c))) return rc;
   if (n > c.h2d_cap) {
     GRAV_CUDA_TRY(cudaStreamSynchronize(c.stream));
-    grav::free_ptr(c.h2d_pos); grav::free_ptr(c.h2d_mass); grav::free_ptr(c.h2d_acc);
+    grav::ctx_release(&c, c.h2d_pos); grav::ctx_release(&c, c.h2d_mass);
+    grav::ctx_release(&c, c.h2d_acc);
     c.h2d_cap = 0;
-    GRAV_CUDA_TRY(cudaMalloc(&c.h2d_pos, sizeof(double) * 3 * n));
-    GRAV_CUDA_TRY(cudaMalloc(&c.h2d_mass, sizeof(double) * n));
-    GRAV_CUDA_TRY(cudaMalloc(&c.h2d_acc, sizeof(double) * 3 * n));
+    if ((rc = grav::ctx_alloc(&c, c.h2d_pos, 3 * n))) return rc;
+    if ((rc = grav::ctx_alloc(&c, c.h2d_mass, n))) return rc;
+    if ((rc = grav::ctx_alloc(&c, c.h2d_acc, 3 * n))) return rc;
     c.h2d_cap = n;
   }
   if (n > 0) {

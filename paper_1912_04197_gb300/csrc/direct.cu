@@ -179,12 +179,13 @@ __global__ void k_diag_final(const double *__restrict__ part, double G, double *
 int direct_forces(Ctx *c, int64_t n, const double *pos, const double *mass, double eps, double G,
                   double *acc) {
   if (n > c->dir_cap) {
-    if (c->dir_hi) cudaFree(c->dir_hi);
-    if (c->dir_lo) cudaFree(c->dir_lo);
-    c->dir_hi = c->dir_lo = nullptr;
+    GRAV_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    ctx_release(c, c->dir_hi);
+    ctx_release(c, c->dir_lo);
     c->dir_cap = 0;
-    GRAV_CUDA_TRY(cudaMalloc(&c->dir_hi, sizeof(float4) * n));
-    GRAV_CUDA_TRY(cudaMalloc(&c->dir_lo, sizeof(float4) * n));
+    int rc = ctx_alloc(c, c->dir_hi, n);
+    if (rc == GRAVITY_OK) rc = ctx_alloc(c, c->dir_lo, n);
+    if (rc) return rc;
     c->dir_cap = n;
   }
   k_split<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(pos, mass, n, c->dir_hi, c->dir_lo);
@@ -203,19 +204,21 @@ int direct_forces(Ctx *c, int64_t n, const double *pos, const double *mass, doub
 int diagnostics(Ctx *c, int64_t n, const double *pos, const double *vel, const double *mass,
                 double eps, double G, double *out_dev) {
   if (n > c->dir_cap) {
-    if (c->dir_hi) cudaFree(c->dir_hi);
-    if (c->dir_lo) cudaFree(c->dir_lo);
-    c->dir_hi = c->dir_lo = nullptr;
+    GRAV_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    ctx_release(c, c->dir_hi);
+    ctx_release(c, c->dir_lo);
     c->dir_cap = 0;
-    GRAV_CUDA_TRY(cudaMalloc(&c->dir_hi, sizeof(float4) * n));
-    GRAV_CUDA_TRY(cudaMalloc(&c->dir_lo, sizeof(float4) * n));
+    int rc = ctx_alloc(c, c->dir_hi, n);
+    if (rc == GRAVITY_OK) rc = ctx_alloc(c, c->dir_lo, n);
+    if (rc) return rc;
     c->dir_cap = n;
   }
   if (n > c->diag_cap) {
-    if (c->diag_buf) cudaFree(c->diag_buf);
-    c->diag_buf = nullptr;
+    GRAV_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    ctx_release(c, c->diag_buf);
     c->diag_cap = 0;
-    GRAV_CUDA_TRY(cudaMalloc(&c->diag_buf, sizeof(double) * (n + 8 * kDiagBlocks + 8)));
+    const int rc = ctx_alloc(c, c->diag_buf, n + 8 * kDiagBlocks + 8);
+    if (rc) return rc;
     c->diag_cap = n;
   }
   double *mphi = c->diag_buf, *part = c->diag_buf + n;

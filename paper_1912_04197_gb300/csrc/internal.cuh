@@ -89,6 +89,11 @@ struct StepGraph {
 
 struct Ctx {
   int device = 0;
+  // device memory of the context: cudaMalloc/cudaFree, or the caller's allocator
+  gravity_alloc_fn user_alloc = nullptr;
+  gravity_free_fn user_free = nullptr;
+  void *alloc_user = nullptr;
+  int stack_cap = 0;           // walk stack entries allowed (0 = all); failure testing
   cudaStream_t stream = nullptr;
   int num_sms = 0;
   int64_t cap = 0;             // body capacity of the buffers
@@ -128,6 +133,7 @@ int tree_build(Ctx *c, int64_t n, const double *pos, const double *mass);
 int walk_forces(Ctx *c, double theta, double eps, double *acc, int32_t *counts,
                 double *vel, double kick);
 int walk_vjp(Ctx *c, double theta, double eps, const double *lambda, double *grad);
+int walk_stack_capacity();
 // ---- launchers (direct.cu)
 int direct_forces(Ctx *c, int64_t n, const double *pos, const double *mass, double eps,
                   double G, double *acc);
@@ -144,6 +150,23 @@ int launch_adjoint_kick_drift(Ctx *c, int64_t n, double *xbar, double *vbar, con
 int probe_fp32(Ctx *c, int64_t iters, double *ms, double *flops);
 
 int ensure_capacity(Ctx *c, int64_t n);
+int alloc_base(Ctx *c);
+void free_all(Ctx *c);
+// Context-owned device memory (through the caller's allocator when one is set).
+int ctx_malloc(Ctx *c, void **p, size_t bytes);
+void ctx_free(Ctx *c, void *p);
+template <typename T>
+int ctx_alloc(Ctx *c, T *&p, int64_t count) {
+  void *q = nullptr;
+  const int rc = ctx_malloc(c, &q, sizeof(T) * (size_t)(count > 0 ? count : 1));
+  p = static_cast<T *>(q);
+  return rc;
+}
+template <typename T>
+void ctx_release(Ctx *c, T *&p) {
+  if (p) ctx_free(c, p);
+  p = nullptr;
+}
 int set_segments(Ctx *c, int nseg, const int64_t *off_host);
 int fill_segment_ids(Ctx *c);
 int cuda_status(cudaError_t e);

@@ -25,7 +25,8 @@ __global__ void __launch_bounds__(256) k_ffma(int64_t iters, float seed, float *
 
 int probe_fp32(Ctx *c, int64_t iters, double *ms, double *flops) {
   float *sink = nullptr;
-  GRAV_CUDA_TRY(cudaMalloc(&sink, 256 * sizeof(float)));
+  const int rc = ctx_alloc(c, sink, 256);
+  if (rc) return rc;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -41,7 +42,7 @@ int probe_fp32(Ctx *c, int64_t iters, double *ms, double *flops) {
   cudaEventElapsedTime(&t, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  cudaFree(sink);
+  ctx_release(c, sink);
   if (err != cudaSuccess) return cuda_status(err);
   *ms = t;
   *flops = 2.0 * 8 * 16 * (double)iters * blocks * 256 / (t * 1e-3);

@@ -122,6 +122,7 @@ struct WalkArgs {
   unsigned *task_counter;         // [nqueues] per-queue counters, zeroed before the launch
   int nqueues;
   int flush_at;
+  int stack_cap;                  // stack entries allowed (<= kStackCap)
   uint2 *gstack;                  // [persistent warps][kGlobStack] (first|cnt|kind, mask)
   const int32_t *task_begin;      // several clouds: per task first body, cloud end, cloud id
   const int32_t *task_end;
@@ -697,7 +698,7 @@ k_walk(WalkArgs A) {
         pincl = warp_incl_scan_i(npush, lane);
         ptotal = __shfl_sync(0xffffffffu, pincl, 31);
       }
-      if (sp + ptotal > kStackCap) {
+      if (sp + ptotal > A.stack_cap) {
         if (lane == 0) latch_error(A.status, kErrStack);
         abort = true;
         break;
@@ -881,6 +882,7 @@ int launch_walk(Ctx *c, WalkArgs A) {
   }
   const WalkShape shape = walk_shape(c->params.walk_cfg);
   A.flush_at = shape.flush_at;
+  A.stack_cap = (c->stack_cap > 0 && c->stack_cap < kStackCap) ? c->stack_cap : kStackCap;
   int bps = blocks_per_sm[dev] - shape.blocks_less;
   if (bps < 1) bps = 1;
   int blocks = bps * c->num_sms;
@@ -905,10 +907,13 @@ int launch_walk(Ctx *c, WalkArgs A) {
   if (blocks < 1) blocks = 1;
   const size_t gneed = (size_t)blocks * kWalkWarps * kGlobStack;
   if (gneed > c->walk_gstack_cap) {
-    if (c->walk_gstack) cudaFree(c->walk_gstack);
-    c->walk_gstack = nullptr;
+    GRAV_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    ctx_release(c, c->walk_gstack);
     c->walk_gstack_cap = 0;
-    GRAV_CUDA_TRY(cudaMalloc(&c->walk_gstack, gneed * sizeof(uint2)));
+    void *gs = nullptr;
+    const int rc = ctx_malloc(c, &gs, gneed * sizeof(uint2));
+    if (rc) return rc;
+    c->walk_gstack = gs;
     c->walk_gstack_cap = gneed;
   }
   A.gstack = reinterpret_cast<uint2 *>(c->walk_gstack);
@@ -922,6 +927,8 @@ int launch_walk(Ctx *c, WalkArgs A) {
 }
 
 }  // namespace
+
+int walk_stack_capacity() { return kStackCap; }
 
 int walk_forces(Ctx *c, double theta, double eps, double *acc, int32_t *counts, double *vel,
                 double kick) {
@@ -1011,14 +1018,14 @@ int walk_vjp(Ctx *c, double theta, double eps, const double *lambda, double *gra
   const int64_t node_cap = 2 * c->cap;
   if (c->vjp_cap < c->cap) {
     GRAV_CUDA_TRY(cudaStreamSynchronize(c->stream));
-    if (c->vjp_own) cudaFree(c->vjp_own);
-    if (c->vjp_body) cudaFree(c->vjp_body);
-    if (c->vjp_node) cudaFree(c->vjp_node);
-    c->vjp_own = c->vjp_body = c->vjp_node = nullptr;
+    ctx_release(c, c->vjp_own);
+    ctx_release(c, c->vjp_body);
+    ctx_release(c, c->vjp_node);
     c->vjp_cap = 0;
-    GRAV_CUDA_TRY(cudaMalloc(&c->vjp_own, sizeof(double) * 3 * c->cap));
-    GRAV_CUDA_TRY(cudaMalloc(&c->vjp_body, sizeof(double) * 3 * c->cap));
-    GRAV_CUDA_TRY(cudaMalloc(&c->vjp_node, sizeof(double) * 3 * node_cap));
+    int rc = ctx_alloc(c, c->vjp_own, 3 * c->cap);
+    if (rc == GRAVITY_OK) rc = ctx_alloc(c, c->vjp_body, 3 * c->cap);
+    if (rc == GRAVITY_OK) rc = ctx_alloc(c, c->vjp_node, 3 * node_cap);
+    if (rc) return rc;
     c->vjp_cap = c->cap;
   }
   GRAV_CUDA_TRY(cudaMemsetAsync(c->vjp_body, 0, sizeof(double) * 3 * n, c->stream));

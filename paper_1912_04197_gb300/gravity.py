@@ -25,6 +25,12 @@ GRAVITY_E_INTERNAL = -6
 GRAVITY_E_NOTREE = -7
 GRAVITY_ADJ_END = 1
 GRAVITY_ADJ_START = 2
+GRAVITY_DBGSET_STACK_CAP = 1
+
+# gravity_alloc_fn / gravity_free_fn
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(ctypes.c_void_p), ctypes.c_size_t,
+                            ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
 DBG_ROOT, DBG_KEYS, DBG_PERM, DBG_NNODES, DBG_TOPO, DBG_DEPTH, DBG_PARENT, DBG_MASS, DBG_COM, \
     DBG_QUAD, DBG_WALKSTATS = range(11)
@@ -55,6 +61,8 @@ def _load() -> ctypes.CDLL:
         "gravity_create": (I, [ctypes.POINTER(P), I, P]),
         "gravity_destroy": (I, [P]),
         "gravity_set_stream": (I, [P, P]),
+        "gravity_set_allocator": (I, [P, ALLOC_FN, FREE_FN, P]),
+        "gravity_debug_set": (I, [P, I, I64]),
         "gravity_tree_build": (I, [P, I64, P, P, PP]),
         "gravity_forces": (I, [P, D, D, P]),
         "gravity_forces_counted": (I, [P, D, D, P, P]),
@@ -139,12 +147,55 @@ class Context:
         if getattr(self, "_h", None) is not None:
             _lib.gravity_destroy(self._h)
             self._h = None
+        self._alloc_keep = None
 
     def __del__(self):
         try:
             self.close()
         except Exception:
             pass
+
+
+def gravity_set_allocator(ctx: Context, alloc=None, release=None):
+    """Route the context's device memory through Python callables alloc(nbytes) -> int
+    device pointer (0 on failure) and release(ptr); both None restores cudaMalloc/cudaFree.
+    The context's tree and scratch are released (see gravity.h)."""
+    if (alloc is None) != (release is None):
+        raise ValueError("give both alloc and release, or neither")
+    if alloc is None:
+        fa, ff = ALLOC_FN(), FREE_FN()
+    else:
+        def _a(pp, nbytes, _user):
+            try:
+                ptr = int(alloc(int(nbytes)))
+            except Exception:
+                return 1
+            if not ptr:
+                return 1
+            pp[0] = ptr
+            return 0
+
+        def _f(ptr, _user):
+            release(int(ptr))
+        fa, ff = ALLOC_FN(_a), FREE_FN(_f)
+    h = ctx.handle
+    keep_old = getattr(ctx, "_alloc_keep", None)   # old callbacks stay alive for the release
+    ctx._alloc_keep = (fa, ff)
+    rc = _lib.gravity_set_allocator(h, fa, ff, None)
+    if rc != GRAVITY_OK and keep_old is not None:
+        ctx._alloc_keep = keep_old
+    _check(rc, "gravity_set_allocator")
+
+
+def use_torch_allocator(ctx: Context):
+    """Give the context's device memory to PyTorch's caching allocator (one pool)."""
+    dev, stream = ctx.device, torch.cuda.current_stream(ctx.device)
+    gravity_set_allocator(ctx, lambda nbytes: torch.cuda.caching_allocator_alloc(nbytes, dev, stream),
+                          torch.cuda.caching_allocator_delete)
+
+
+def gravity_debug_set(ctx: Context, what: int, value: int):
+    _check(_lib.gravity_debug_set(ctx.handle, int(what), int(value)), "gravity_debug_set")
 
 
 def gravity_create(device=None) -> Context:
