@@ -268,7 +268,7 @@ int gravity_sync(gravity_ctx *ctx);
  *                         entries, deepest stack, terms evaluated by active lanes, lockstep
  *                         iterations of lists split by 16 / 8 / 1 lanes, full-mask entries,
  *                         far-list entries, mixed nodes that all tested lanes decided alike,
- *                         2 reserved
+ *                         lockstep iterations of the point list split by 1 lane, 1 reserved
  * bytes must be at least the size listed; otherwise GRAVITY_E_ARG. */
 enum gravity_debug_item {
   GRAVITY_DBG_ROOT = 0,

@@ -67,7 +67,7 @@ enum { kModeForce = 0, kModeCount = 1, kModeVjp = 2 };
 
 enum { kStatBatches, kStatItems, kStatMixed, kStatFp64, kStatMono, kStatQuad, kStatMaxSp,
        kStatLaneTerms, kStatSplit2, kStatSplit4, kStatSplit32, kStatFull, kStatFar,
-       kStatMixedUnanimous, kStatCount = 16 };
+       kStatMixedUnanimous, kStatPointLane, kStatCount = 16 };
 
 struct WarpSmem {
   uint32_t st_a[kSmemStack];      // first | (count-1) << 25 | kind
@@ -487,6 +487,7 @@ k_walk(WalkArgs A) {
     int c_m2p = 0, c_p2p = 0, c_tests = 0;
     unsigned long long w_batches = 0, w_items = 0, w_mixed = 0, w_mono = 0, w_quad = 0, w_far = 0;
     unsigned long long w_split[4] = {0, 0, 0, 0};
+    unsigned long long w_psplit[4] = {0, 0, 0, 0};   // the point list alone
     int w_maxsp = 0;
     int npt = 0, nfar = 0, nnear = 0;
     int sp = 1;
@@ -720,7 +721,11 @@ k_walk(WalkArgs A) {
 
       // ---- evaluate full lists
       if (npt >= A.flush_at) {
-        if (COUNT) { w_mono += npt; split_costs(M.lb, 3, npt, lane, w_split); }
+        if (COUNT) {
+          w_mono += npt;
+          split_costs(M.lb, 3, npt, lane, w_split);
+          split_costs(M.lb, 3, npt, lane, w_psplit);
+        }
         float px, py, pz;
         if constexpr (VJP)
           flush_vjp<false, EPS0>(S, npt, lane, xh, yh, zh, xl, yl, zl, xr, yr, zr, eps2, ux, uy, uz,
@@ -759,7 +764,10 @@ k_walk(WalkArgs A) {
     if (!abort) {
       if (COUNT) {
         w_mono += npt; w_quad += nfar + nnear;
-        if (npt > 0) split_costs(M.lb, 3, npt, lane, w_split);
+        if (npt > 0) {
+          split_costs(M.lb, 3, npt, lane, w_split);
+          split_costs(M.lb, 3, npt, lane, w_psplit);
+        }
         if (nfar > 0) split_costs(M.fc, 2, nfar, lane, w_split);
         if constexpr (ORDER == 2) { if (nnear > 0) split_costs(S.qb, 3, nnear, lane, w_split); }
       }
@@ -805,6 +813,7 @@ k_walk(WalkArgs A) {
         atomicAdd(&A.stats[kStatSplit32], w_split[2]);
         atomicAdd(&A.stats[kStatFull], w_split[3]);
         atomicAdd(&A.stats[kStatFar], w_far);
+        atomicAdd(&A.stats[kStatPointLane], w_psplit[2]);
       }
     }
     if (VJP && valid) {                         // own-term gradient, sorted order
