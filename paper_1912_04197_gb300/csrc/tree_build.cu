@@ -284,7 +284,7 @@ int exclusive_scan(Ctx *c, uint32_t *data, int64_t n, uint32_t *total_out) {
 constexpr int kRsMaxPasses = 10;                 // 8 key passes + up to 2 cloud-id passes
 constexpr uint32_t kRsFlagAgg = 1u << 30, kRsFlagPre = 2u << 30, kRsValue = (1u << 30) - 1;
 constexpr int kRsSpin = 1 << 22;
-constexpr int kRsLook = 32;                      // predecessor tiles read per look-back round
+constexpr int kRsLook = 8;                       // predecessor tiles read per look-back round
 
 __device__ __forceinline__ unsigned rs_digit(uint64_t key, uint32_t val, int shift,
                                              const int32_t *__restrict__ seg_of) {
@@ -334,7 +334,8 @@ __device__ __forceinline__ uint32_t block_excl_scan256(uint32_t v, uint32_t *s_t
   return ex;
 }
 
-__global__ void __launch_bounds__(kRsThreads)
+// 4 blocks per SM (64 registers): every 2048-key tile of a 1M-key pass is resident at once
+__global__ void __launch_bounds__(kRsThreads, 4)
 k_rs_sweep(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
            uint64_t *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n, int shift,
            const int32_t *__restrict__ seg_of, const uint32_t *__restrict__ ghist,
