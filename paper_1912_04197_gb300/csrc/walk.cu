@@ -15,13 +15,14 @@
 //     the oracle does, so every decision equals the FP64 one;
 //   * accepted terms go to shared-memory lists that all lanes evaluate with the
 //     softened r of Eq. (Force_rComp); inactive lanes add zero.  Three lists:
-//       point  - body-to-body terms (Eq. Force_leaf), d = (c_hi - x_hi) + (c_lo - x_lo);
+//       point  - body-to-body terms (Eq. Force_leaf), and with monopoles only the
+//                node terms not in the far list, d = (c_hi - x_hi) + (c_lo - x_lo);
 //       far    - node terms (Eq. Force_thetaTrue; + quadrupole) of cells at least
 //                theta R_w / 2 wide (R_w = extent of the warp's bodies), on FP32
 //                coordinates relative to the warp's first body: every accepting
 //                body is then more than R_w / 2 away, which bounds the error of
 //                d = c_rel - x_rel by 5.5 * 2^-23 |d| (2^-23 (1.5 |d| + 2 R_w));
-//       near   - the other node terms, on hi/lo coordinates as the point list;
+//       near   - (quadrupole) the other node terms, on hi/lo coordinates;
 //   * each flushed list's partial sum enters a (hi, lo) two-sum accumulator (or an
 //     FP64 one).
 // The kernel is persistent: each warp takes 32-body tasks from an atomic counter,
@@ -31,6 +32,9 @@
 // contains every body, so the guard opens it for all of them), and add their partial
 // sums to the zeroed output with FP64 atomics (two addends: the result does not
 // depend on their order).
+// A second mode computes the vector-Jacobian product of the accelerations on the
+// same decisions (see flush_vjp and k_vjp_finish); a third counts decisions and
+// collects walk statistics.
 #include <type_traits>
 
 #include "internal.cuh"
@@ -59,12 +63,14 @@ constexpr uint32_t kKindBody = 0x80000000u;
 constexpr uint32_t kFirstMask = 0x01FFFFFFu;   // 25-bit first index
 constexpr int kCntShift = 25;                  // 6-bit (count - 1)
 
+enum { kModeForce = 0, kModeCount = 1, kModeVjp = 2 };
+
 // Walk statistics accumulated by the counted variant (introspection, not used on
 // the timed path): batches, items, mixed nodes, FP64 decisions, point-list entries,
 // node-term entries, deepest stack, lane-terms evaluated by active lanes, lockstep
-// iterations of lists split by 16 / 8 / 1 lanes, full-mask entries, far entries.
-enum { kModeForce = 0, kModeCount = 1, kModeVjp = 2 };
-
+// iterations of lists split by 16 / 8 / 1 lanes, full-mask entries, far entries,
+// mixed nodes every tested lane decided alike, per-lane lockstep iterations of the
+// point list.
 enum { kStatBatches, kStatItems, kStatMixed, kStatFp64, kStatMono, kStatQuad, kStatMaxSp,
        kStatLaneTerms, kStatSplit2, kStatSplit4, kStatSplit32, kStatFull, kStatFar,
        kStatMixedUnanimous, kStatPointLane, kStatCount = 16 };
