@@ -216,20 +216,29 @@ def run_reference(args, rank, world):
 
 
 # ----------------------------------------------------------------------------- GPU arm
+def walk_code_hash() -> str:
+    """Hash of the walk source without comments and blank space: a change of the code
+    (not of its comments) makes the recorded DRAM traffic stale."""
+    import re
+    src = open(os.path.join(ROOT, "paper_1912_04197_gb300", "csrc", "walk.cu")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    src = re.sub(r"\s+", " ", src)
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
+
+
 def walk_traffic(order):
-    """DRAM bytes per walk launch from the committed ncu summary, if the walk source
-    has not changed since it was captured (else None)."""
+    """DRAM bytes per walk launch from the committed ncu summary, if the walk code has
+    not changed since it was captured (else None)."""
     path = os.path.join(ROOT, "profiles", "walk_ncu_clumpy1M.txt")
-    src = os.path.join(ROOT, "paper_1912_04197_gb300", "csrc", "walk.cu")
     if not os.path.exists(path):
         return None
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     vals = {}
     for line in open(path):
         if ":" in line and not line.startswith("#"):
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("walk_source_sha256_16") != h:
+    if vals.get("walk_code_sha256_16") != walk_code_hash():
         return None
     key = f"dram_bytes_per_launch_order{order}"
     return float(vals[key]) if key in vals else None
