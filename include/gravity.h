@@ -165,8 +165,11 @@ int gravity_forces_vjp(gravity_ctx *ctx, double theta, double eps, const double 
  * place.  With GRAVITY_ADJ_START they end as the cotangents of (pos0, vel0);
  * without it the reverse of the drift that produced pos0 is applied too, which is
  * where the preceding segment's call continues.  p: order 0 and scheme 0 only
- * (GRAVITY_E_ARG otherwise).  Allocates (nsteps + 1) * 24 bytes per body for the
- * levels on first use (synchronises then); leaves the tree of pos0 in the context. */
+ * (GRAVITY_E_ARG otherwise).  Allocates on first use (synchronising then)
+ * (nsteps + 1) * 24 bytes per body for the positions and, when it can, about
+ * (nsteps + 1) * 250 bytes per body to keep each level's tree for the reverse pass (else
+ * the trees are built again); leaves the tree of the last recomputed level in the
+ * context. */
 enum gravity_adjoint_flags { GRAVITY_ADJ_END = 1, GRAVITY_ADJ_START = 2 };
 int leapfrog_adjoint(gravity_ctx *ctx, int64_t n, const double *pos0, const double *vel0,
                      const double *mass, double dt, int nsteps, double theta, double eps,

@@ -188,6 +188,66 @@ int set_segments(Ctx *c, int nseg, const int64_t *off) {
   return fill_segment_ids(c);
 }
 
+// A saved copy of the tree arrays the vector-Jacobian product reads (the adjoint
+// keeps one per recomputed level instead of building the tree again in reverse).
+struct TreeSlot {
+  size_t bhi, blo, pos, mass, idx, topo, rec0, rec1, depth, parent, nmass, ncom, geom, nnodes;
+  size_t bytes;
+};
+
+TreeSlot tree_slot_layout(int64_t n, int ngeom) {
+  TreeSlot L{};
+  size_t o = 0;
+  auto take = [&](size_t b) { const size_t r = o; o += (b + 255) & ~(size_t)255; return r; };
+  const size_t nodes = 2 * (size_t)n;
+  L.bhi = take(sizeof(float4) * n); L.blo = take(sizeof(float4) * n);
+  L.pos = take(sizeof(double) * 3 * n); L.mass = take(sizeof(double) * n);
+  L.idx = take(sizeof(uint32_t) * n);
+  L.topo = take(sizeof(int4) * nodes); L.rec0 = take(sizeof(float4) * nodes);
+  L.rec1 = take(sizeof(float4) * nodes); L.depth = take(sizeof(int32_t) * nodes);
+  L.parent = take(sizeof(int32_t) * nodes); L.nmass = take(sizeof(double) * nodes);
+  L.ncom = take(sizeof(double) * 3 * nodes); L.geom = take(sizeof(double) * 8 * ngeom);
+  L.nnodes = take(sizeof(int32_t));
+  L.bytes = o;
+  return L;
+}
+
+Tree tree_slot_view(unsigned char *b, const TreeSlot &L) {
+  Tree v{};
+  v.body_hi = reinterpret_cast<float4 *>(b + L.bhi);
+  v.body_lo = reinterpret_cast<float4 *>(b + L.blo);
+  v.pos_s = reinterpret_cast<double *>(b + L.pos);
+  v.mass_s = reinterpret_cast<double *>(b + L.mass);
+  v.idx = reinterpret_cast<uint32_t *>(b + L.idx);
+  v.topo = reinterpret_cast<int4 *>(b + L.topo);
+  v.nrec0 = reinterpret_cast<float4 *>(b + L.rec0);
+  v.nrec1 = reinterpret_cast<float4 *>(b + L.rec1);
+  v.ndepth = reinterpret_cast<int32_t *>(b + L.depth);
+  v.nparent = reinterpret_cast<int32_t *>(b + L.parent);
+  v.nmass = reinterpret_cast<double *>(b + L.nmass);
+  v.ncom = reinterpret_cast<double *>(b + L.ncom);
+  v.geom = reinterpret_cast<double *>(b + L.geom);
+  v.nnodes = reinterpret_cast<int32_t *>(b + L.nnodes);
+  return v;
+}
+
+int tree_slot_save(Ctx *c, unsigned char *b, const TreeSlot &L, int64_t n, int ngeom) {
+  const Tree v = tree_slot_view(b, L);
+  const Tree &t = c->t;
+  const size_t nodes = 2 * (size_t)n;
+  struct { void *dst; const void *src; size_t bytes; } cp[] = {
+      {v.body_hi, t.body_hi, sizeof(float4) * n}, {v.body_lo, t.body_lo, sizeof(float4) * n},
+      {v.pos_s, t.pos_s, sizeof(double) * 3 * n}, {v.mass_s, t.mass_s, sizeof(double) * n},
+      {v.idx, t.idx, sizeof(uint32_t) * n}, {v.topo, t.topo, sizeof(int4) * nodes},
+      {v.nrec0, t.nrec0, sizeof(float4) * nodes}, {v.nrec1, t.nrec1, sizeof(float4) * nodes},
+      {v.ndepth, t.ndepth, sizeof(int32_t) * nodes}, {v.nparent, t.nparent, sizeof(int32_t) * nodes},
+      {v.nmass, t.nmass, sizeof(double) * nodes}, {v.ncom, t.ncom, sizeof(double) * 3 * nodes},
+      {v.geom, t.geom, sizeof(double) * 8 * ngeom}, {v.nnodes, t.nnodes, sizeof(int32_t)}};
+  for (const auto &e : cp)
+    GRAV_CUDA_TRY(cudaMemcpyAsync(e.dst, e.src, e.bytes, cudaMemcpyDeviceToDevice, c->stream));
+  return GRAVITY_OK;
+}
+
 // The small fixed buffers every context holds (status word, one cloud's geometry,
 // counters); and the release of everything the context owns.
 int alloc_base(Ctx *c) {
@@ -221,6 +281,7 @@ void free_all(Ctx *c) {
   c->vjp_cap = 0;
   ctx_release(c, c->adj_levels); ctx_release(c, c->adj_work);
   c->adj_levels_cap = c->adj_work_cap = 0;
+  ctx_release(c, c->adj_bank); c->adj_bank_cap = 0;
   ctx_release(c, c->dir_hi); ctx_release(c, c->dir_lo); c->dir_cap = 0;
   ctx_release(c, c->diag_buf); c->diag_cap = 0;
   ctx_release(c, c->h2d_pos); ctx_release(c, c->h2d_mass); ctx_release(c, c->h2d_acc);
@@ -507,6 +568,29 @@ int leapfrog_adjoint(gravity_ctx *h, int64_t n, const double *pos0, const double
   }
   double *vel = c.adj_work, *acc = c.adj_work + n3, *g = c.adj_work + 2 * n3;
   auto level = [&](int k) { return c.adj_levels + n3 * (int64_t)k; };
+  const int last = (flags & GRAVITY_ADJ_END) ? nsteps : nsteps - 1;
+  // keep each recomputed level's tree (the arrays the product reads) when that fits,
+  // so the reverse pass needs no second build; else build again in reverse
+  const int ngeom = c.seg.nseg > 1 ? c.seg.nseg : 1;
+  const grav::TreeSlot L = grav::tree_slot_layout(n, ngeom);
+  const size_t bank_need = L.bytes * (size_t)(last + 1);
+  bool banked = false;
+  if (bank_need <= ((size_t)64 << 30)) {
+    if (c.adj_bank_cap >= bank_need) {
+      banked = true;
+    } else {
+      GRAV_CUDA_TRY(cudaStreamSynchronize(c.stream));
+      grav::ctx_release(&c, c.adj_bank);
+      c.adj_bank_cap = 0;
+      if (grav::ctx_alloc(&c, c.adj_bank, (int64_t)bank_need) == GRAVITY_OK) {
+        c.adj_bank_cap = bank_need;
+        banked = true;
+      } else {
+        cudaGetLastError();                  // not enough memory: rebuild in reverse
+      }
+    }
+  }
+  auto slot = [&](int k) { return c.adj_bank + L.bytes * (size_t)k; };
   // recompute the segment's levels from the checkpoint with the forward kernels
   GRAV_CUDA_TRY(cudaMemcpyAsync(level(0), pos0, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c.stream));
   GRAV_CUDA_TRY(cudaMemcpyAsync(vel, vel0, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c.stream));
@@ -514,23 +598,29 @@ int leapfrog_adjoint(gravity_ctx *h, int64_t n, const double *pos0, const double
   if ((rc = grav::tree_build(&c, n, level(0), mass))) return rc;
   c.have_tree = true;
   if ((rc = grav::walk_forces(&c, theta, eps, acc, nullptr, nullptr, 0.0))) return rc;
-  const int last = (flags & GRAVITY_ADJ_END) ? nsteps : nsteps - 1;
+  if (banked && (rc = grav::tree_slot_save(&c, slot(0), L, n, ngeom))) return rc;
   for (int k = 0; k < last; ++k) {
     GRAV_CUDA_TRY(cudaMemcpyAsync(level(k + 1), level(k), sizeof(double) * n3,
                                   cudaMemcpyDeviceToDevice, c.stream));
     if ((rc = grav::integrate_one(c, n, level(k + 1), vel, mass, acc, dt, theta, eps))) return rc;
+    if (banked && (rc = grav::tree_slot_save(&c, slot(k + 1), L, n, ngeom))) return rc;
   }
   // reverse: level k takes xbar += c_k J(x_k)^T vbar, then the drift before it
   const double hk = 0.5 * dt;
   for (int k = last; k >= 0; --k) {
     const bool top = k == nsteps;                    // only with GRAVITY_ADJ_END
     const bool first = k == 0 && (flags & GRAVITY_ADJ_START);
-    if (k != last) {                                 // the tree is at level `last` already
-      c.n = n;
-      if ((rc = grav::tree_build(&c, n, level(k), mass))) return rc;
-      c.have_tree = true;
+    if (banked) {
+      rc = grav::walk_vjp_tree(&c, grav::tree_slot_view(slot(k), L), theta, eps, vbar, g);
+    } else {
+      if (k != last) {                               // the tree is at level `last` already
+        c.n = n;
+        if ((rc = grav::tree_build(&c, n, level(k), mass))) return rc;
+        c.have_tree = true;
+      }
+      rc = grav::walk_vjp(&c, theta, eps, vbar, g);
     }
-    if ((rc = grav::walk_vjp(&c, theta, eps, vbar, g))) return rc;
+    if (rc) return rc;
     const double coef = (top || first) ? hk : dt;
     if ((rc = grav::launch_adjoint_kick_drift(&c, n, xbar, vbar, g, coef, dt, !first))) return rc;
   }

@@ -115,6 +115,8 @@ struct Ctx {
   // and product work arrays
   double *adj_levels = nullptr, *adj_work = nullptr;
   int64_t adj_levels_cap = 0, adj_work_cap = 0;   // in doubles
+  unsigned char *adj_bank = nullptr;              // saved trees of the recomputed levels
+  size_t adj_bank_cap = 0;                        // in bytes
   Tree t;
   // direct-sum staging (caller order hi/lo)
   float4 *dir_hi = nullptr, *dir_lo = nullptr;
@@ -133,6 +135,9 @@ int tree_build(Ctx *c, int64_t n, const double *pos, const double *mass);
 int walk_forces(Ctx *c, double theta, double eps, double *acc, int32_t *counts,
                 double *vel, double kick);
 int walk_vjp(Ctx *c, double theta, double eps, const double *lambda, double *grad);
+// The same on a tree held elsewhere (a saved copy of the arrays the product reads).
+int walk_vjp_tree(Ctx *c, const Tree &t, double theta, double eps, const double *lambda,
+                  double *grad);
 int walk_stack_capacity();
 // ---- launchers (direct.cu)
 int direct_forces(Ctx *c, int64_t n, const double *pos, const double *mass, double eps,

@@ -1028,7 +1028,11 @@ __global__ void k_vjp_finish(const int4 *__restrict__ topo, const int32_t *__res
 }  // namespace
 
 int walk_vjp(Ctx *c, double theta, double eps, const double *lambda, double *grad) {
-  Tree &t = c->t;
+  return walk_vjp_tree(c, c->t, theta, eps, lambda, grad);
+}
+
+int walk_vjp_tree(Ctx *c, const Tree &t, double theta, double eps, const double *lambda,
+                  double *grad) {
   const int64_t n = c->n;
   const int64_t node_cap = 2 * c->cap;
   if (c->vjp_cap < c->cap) {
