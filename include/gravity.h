@@ -192,7 +192,11 @@ int gravity_batch_tree_build(gravity_ctx *ctx, int32_t nclouds, const int64_t *o
 
 /* Eq. (Newton) with the softening of Eq. (Force_rComp), all N(N-1) pairs:
  * acc_i = G sum_{j != i} m_j (R_j - R_i) / (|R_j - R_i|^2 + eps^2)^{3/2}.
- * FP32 pair terms on hi/lo split coordinates, compensated accumulation, FP64 out. */
+ * FP32 pair terms, compensated accumulation, FP64 out.  The bodies are put in Morton
+ * order first (the context's own buffers; its tree is untouched) so that each source
+ * tile far from a block of targets is evaluated on FP32 coordinates relative to the
+ * block, the others on hi/lo split coordinates; every term's error stays a few 2^-24 of
+ * its size. */
 int gravity_direct(gravity_ctx *ctx, int64_t n, const double *pos, const double *mass,
                    double eps, double G, double *acc);
 
@@ -200,8 +204,10 @@ int gravity_direct(gravity_ctx *ctx, int64_t n, const double *pos, const double 
  * service).  For callers that cannot call cudaMalloc - an application that owns
  * all device memory (fixed-budget pool, plugin host forbidding allocations after
  * start-up), or a latency-critical loop that cannot afford the implicit device
- * synchronisation of cudaMalloc/cudaFree.  Same result as gravity_direct (same
- * kernels), but needs no context and allocates nothing: the hi/lo staging of the
+ * synchronisation of cudaMalloc/cudaFree.  The same sum as gravity_direct (equal to
+ * rounding: it keeps the caller's order and hi/lo coordinates for every pair, where
+ * gravity_direct sorts the bodies first), but needs no context and allocates nothing:
+ * the hi/lo staging of the
  * bodies lives in a file-scope __device__ array of 2 MiB, sized for at most
  * 65536 bodies, which every GPU that loads the library holds until the process
  * exits.

@@ -105,7 +105,7 @@ int ensure_capacity(Ctx *c, int64_t n) {
 #define GRAV_ALLOC(p, cnt) if (rc == GRAVITY_OK) rc = ctx_alloc(c, p, cnt)
   GRAV_ALLOC(t.keys, cap); GRAV_ALLOC(t.keys_alt, cap);
   GRAV_ALLOC(t.idx, cap); GRAV_ALLOC(t.idx_alt, cap);
-  GRAV_ALLOC(t.hist, 257 * 10 + 10 * 256 * ntiles);   // radix sort: counts + tile states
+  GRAV_ALLOC(t.hist, radix_hist_words(cap));         // radix sort: counts + tile states
   GRAV_ALLOC(t.scan_aux, scan_n / 4096 + 64);
   GRAV_ALLOC(t.bbox_part, 6 * (4 * (int64_t)c->num_sms + 3));
   GRAV_ALLOC(t.pos_s, 3 * cap); GRAV_ALLOC(t.mass_s, cap);
@@ -283,6 +283,10 @@ void free_all(Ctx *c) {
   c->adj_levels_cap = c->adj_work_cap = 0;
   ctx_release(c, c->adj_bank); c->adj_bank_cap = 0;
   ctx_release(c, c->dir_hi); ctx_release(c, c->dir_lo); c->dir_cap = 0;
+  ctx_release(c, c->ds_keys); ctx_release(c, c->ds_keys_alt); ctx_release(c, c->ds_idx);
+  ctx_release(c, c->ds_idx_alt); ctx_release(c, c->ds_hist); ctx_release(c, c->ds_geom);
+  ctx_release(c, c->ds_part); ctx_release(c, c->ds_ticket); ctx_release(c, c->ds_hi);
+  ctx_release(c, c->ds_lo); ctx_release(c, c->ds_box); c->ds_cap = 0;
   ctx_release(c, c->diag_buf); c->diag_cap = 0;
   ctx_release(c, c->h2d_pos); ctx_release(c, c->h2d_mass); ctx_release(c, c->h2d_acc);
   c->h2d_cap = 0;

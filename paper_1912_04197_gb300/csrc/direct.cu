@@ -1,8 +1,14 @@
 // Direct N^2 gravity, Eq. (Newton) (Sec. 2.1), with the softened distance of
 // Eq. (Force_rComp): a_i = G sum_{j != i} m_j d_ij / (|d_ij|^2 + eps^2)^{3/2}.
-// FP32 pair terms on hi/lo split coordinates (d = (x_j,hi - x_i,hi) + (x_j,lo - x_i,lo)),
-// source tiles staged in shared memory, each tile's partial sum added to a
-// (hi, lo) two-sum accumulator.  The self term has d = 0 and adds zero.
+// FP32 pair terms, source tiles staged in shared memory, each tile's partial sum added
+// to a (hi, lo) two-sum accumulator.  The self term has d = 0 and adds zero.
+// gravity_direct first puts the bodies in Morton order, so that a block's 512 bodies
+// and a 256-body source tile are each compact: a tile away from the block (gap between
+// their boxes at least half the block's diagonal w) is evaluated on FP32 coordinates
+// relative to the block's first body, d = s_rel - x_rel, whose error is then below
+// 2^-24 (2 |d| + 2 w) <= 6 * 2^-24 |d|; nearer tiles use hi/lo split coordinates,
+// d = (x_j,hi - x_i,hi) + (x_j,lo - x_i,lo).  The allocation-free entry point keeps
+// the caller's order and the hi/lo form throughout.
 #include "internal.cuh"
 
 namespace grav {
@@ -94,6 +100,166 @@ k_direct(const float4 *__restrict__ hi, const float4 *__restrict__ lo, int64_t n
   }
 }
 
+// Sorted hi/lo bodies (Morton order) and the box of each 256-body tile (hi parts).
+__global__ void k_split_sorted(const double *__restrict__ pos, const double *__restrict__ mass,
+                               const uint32_t *__restrict__ perm, int64_t n,
+                               float4 *__restrict__ hi, float4 *__restrict__ lo) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t j = perm[i];
+  float xh, xl, yh, yl, zh, zl;
+  split_df(pos[3 * j], xh, xl);
+  split_df(pos[3 * j + 1], yh, yl);
+  split_df(pos[3 * j + 2], zh, zl);
+  hi[i] = make_float4(xh, yh, zh, __double2float_rn(mass[j]));
+  lo[i] = make_float4(xl, yl, zl, 0.f);
+}
+
+__global__ void __launch_bounds__(kDirThreads)
+k_tile_box(const float4 *__restrict__ hi, int64_t n, float4 *__restrict__ box) {
+  const int64_t i = blockIdx.x * (int64_t)kDirThreads + threadIdx.x;
+  const bool v = i < n;
+  const float4 h = v ? hi[i] : make_float4(0, 0, 0, 0);
+  float lx = v ? h.x : INFINITY, ly = v ? h.y : INFINITY, lz = v ? h.z : INFINITY;
+  float ux = v ? h.x : -INFINITY, uy = v ? h.y : -INFINITY, uz = v ? h.z : -INFINITY;
+  for (int o = 16; o > 0; o >>= 1) {
+    lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
+    ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
+    lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
+    ux = fmaxf(ux, __shfl_xor_sync(0xffffffffu, ux, o));
+    uy = fmaxf(uy, __shfl_xor_sync(0xffffffffu, uy, o));
+    uz = fmaxf(uz, __shfl_xor_sync(0xffffffffu, uz, o));
+  }
+  __shared__ float s[kDirThreads / 32][6];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { s[w][0] = lx; s[w][1] = ly; s[w][2] = lz; s[w][3] = ux; s[w][4] = uy; s[w][5] = uz; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < kDirThreads / 32; ++k) {
+      lx = fminf(lx, s[k][0]); ly = fminf(ly, s[k][1]); lz = fminf(lz, s[k][2]);
+      ux = fmaxf(ux, s[k][3]); uy = fmaxf(uy, s[k][4]); uz = fmaxf(uz, s[k][5]);
+    }
+    box[2 * blockIdx.x] = make_float4(lx, ly, lz, 0.f);
+    box[2 * blockIdx.x + 1] = make_float4(ux, uy, uz, 0.f);
+  }
+}
+
+// One block: 512 Morton-consecutive bodies (2 per thread) against every 256-body tile.
+template <bool EPS0>
+__global__ void __launch_bounds__(kDirThreads)
+k_direct_sorted(const float4 *__restrict__ hi, const float4 *__restrict__ lo,
+                const float4 *__restrict__ box, const uint32_t *__restrict__ perm, int64_t n,
+                float eps2, double G, double *__restrict__ acc) {
+  __shared__ float4 sh[kDirThreads], sl[kDirThreads];
+  constexpr int P = kDirPerThread;
+  const int64_t b0 = blockIdx.x * (int64_t)kDirThreads * P;
+  const int64_t ntiles = (n + kDirThreads - 1) / kDirThreads;
+  // origin (the block's first body) and the block's box from its tiles' boxes
+  const float4 oh = hi[b0], ol = lo[b0];
+  float bl[3] = {INFINITY, INFINITY, INFINITY}, bu[3] = {-INFINITY, -INFINITY, -INFINITY};
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const int64_t t = b0 / kDirThreads + p;
+    if (t < ntiles) {
+      const float4 a = box[2 * t], c = box[2 * t + 1];
+      bl[0] = fminf(bl[0], a.x); bl[1] = fminf(bl[1], a.y); bl[2] = fminf(bl[2], a.z);
+      bu[0] = fmaxf(bu[0], c.x); bu[1] = fmaxf(bu[1], c.y); bu[2] = fmaxf(bu[2], c.z);
+    }
+  }
+  const float ex = bu[0] - bl[0], ey = bu[1] - bl[1], ez = bu[2] - bl[2];
+  const float C = fmaxf(fmaxf(fabsf(bl[0]), fabsf(bu[0])),
+                        fmaxf(fmaxf(fabsf(bl[1]), fabsf(bu[1])), fmaxf(fabsf(bl[2]), fabsf(bu[2]))));
+  // far: gap >= diag / 2 (the hi parts' rounding is taken off the gap below)
+  const float far2 = 0.25f * fmaf(ex, ex, fmaf(ey, ey, ez * ez)) * 1.01f + 1e-30f;
+  const float slack = C * 2.4e-7f;            // 2^-22 |x|: hi parts are within 2^-24 |x|
+  float xh[P], yh[P], zh[P], xl[P], yl[P], zl[P], xr[P], yr[P], zr[P];
+  float ahx[P], ahy[P], ahz[P], alx[P], aly[P], alz[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const int64_t i = b0 + threadIdx.x + p * kDirThreads;
+    const float4 h = i < n ? hi[i] : oh;
+    const float4 l = i < n ? lo[i] : ol;
+    xh[p] = h.x; yh[p] = h.y; zh[p] = h.z; xl[p] = l.x; yl[p] = l.y; zl[p] = l.z;
+    xr[p] = (h.x - oh.x) + (l.x - ol.x);
+    yr[p] = (h.y - oh.y) + (l.y - ol.y);
+    zr[p] = (h.z - oh.z) + (l.z - ol.z);
+    ahx[p] = ahy[p] = ahz[p] = alx[p] = aly[p] = alz[p] = 0.f;
+  }
+  for (int64_t t = 0; t < ntiles; ++t) {
+    const float4 a0 = box[2 * t], a1 = box[2 * t + 1];
+    float gx = fmaxf(fmaxf(a0.x - bu[0], bl[0] - a1.x) - slack, 0.f);
+    float gy = fmaxf(fmaxf(a0.y - bu[1], bl[1] - a1.y) - slack, 0.f);
+    float gz = fmaxf(fmaxf(a0.z - bu[2], bl[2] - a1.z) - slack, 0.f);
+    const bool far = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) >= far2;     // block-uniform
+    const int64_t j = t * kDirThreads + threadIdx.x;
+    const float4 h = j < n ? hi[j] : make_float4(0, 0, 0, 0);
+    const float4 l = j < n ? lo[j] : make_float4(0, 0, 0, 0);
+    if (far) {   // sources relative to the origin; past the end: massless and very far
+      sh[threadIdx.x] = j < n ? make_float4((h.x - oh.x) + (l.x - ol.x), (h.y - oh.y) + (l.y - ol.y),
+                                            (h.z - oh.z) + (l.z - ol.z), h.w)
+                              : make_float4(1e30f, 1e30f, 1e30f, 0.f);
+    } else {
+      sh[threadIdx.x] = h;
+      sl[threadIdx.x] = l;
+    }
+    __syncthreads();
+    float px[P], py[P], pz[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) px[p] = py[p] = pz[p] = 0.f;
+    if (far) {
+#pragma unroll 4
+      for (int k = 0; k < kDirThreads; ++k) {
+        const float4 a = sh[k];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          const float dx = a.x - xr[p], dy = a.y - yr[p], dz = a.z - zr[p];
+          const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+          const float inv = rsqrtf(r2);           // r2 > 0: the tile is away from the block
+          const float sc = a.w * (inv * inv * inv);
+          px[p] = fmaf(sc, dx, px[p]);
+          py[p] = fmaf(sc, dy, py[p]);
+          pz[p] = fmaf(sc, dz, pz[p]);
+        }
+      }
+    } else {
+#pragma unroll 4
+      for (int k = 0; k < kDirThreads; ++k) {
+        const float4 a = sh[k], b = sl[k];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          const float dx = (a.x - xh[p]) + (b.x - xl[p]);
+          const float dy = (a.y - yh[p]) + (b.y - yl[p]);
+          const float dz = (a.z - zh[p]) + (b.z - zl[p]);
+          const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+          float inv = rsqrtf(r2);
+          if (EPS0) inv = r2 > 0.f ? inv : 0.f;
+          const float sc = a.w * (inv * inv * inv);
+          px[p] = fmaf(sc, dx, px[p]);
+          py[p] = fmaf(sc, dy, py[p]);
+          pz[p] = fmaf(sc, dz, pz[p]);
+        }
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      two_sum_add(ahx[p], alx[p], px[p]);
+      two_sum_add(ahy[p], aly[p], py[p]);
+      two_sum_add(ahz[p], alz[p], pz[p]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const int64_t i = b0 + threadIdx.x + p * kDirThreads;
+    if (i < n) {
+      const int64_t ci = perm[i];
+      acc[3 * ci] = G * ((double)ahx[p] + (double)alx[p]);
+      acc[3 * ci + 1] = G * ((double)ahy[p] + (double)aly[p]);
+      acc[3 * ci + 2] = G * ((double)ahz[p] + (double)alz[p]);
+    }
+  }
+}
+
 // Softened potential of every body, phi_i = sum_{j != i} m_j / sqrt(|d_ij|^2 + eps^2)
 // (the Plummer potential consistent with the softened force; Sec. 3.1's energy),
 // same tiling and arithmetic as k_direct; the self pair is excluded by index and a
@@ -178,26 +344,47 @@ __global__ void k_diag_final(const double *__restrict__ part, double G, double *
 
 int direct_forces(Ctx *c, int64_t n, const double *pos, const double *mass, double eps, double G,
                   double *acc) {
-  if (n > c->dir_cap) {
+  if (n > c->ds_cap) {
     GRAV_CUDA_TRY(cudaStreamSynchronize(c->stream));
-    ctx_release(c, c->dir_hi);
-    ctx_release(c, c->dir_lo);
-    c->dir_cap = 0;
-    int rc = ctx_alloc(c, c->dir_hi, n);
-    if (rc == GRAVITY_OK) rc = ctx_alloc(c, c->dir_lo, n);
+    ctx_release(c, c->ds_keys); ctx_release(c, c->ds_keys_alt); ctx_release(c, c->ds_idx);
+    ctx_release(c, c->ds_idx_alt); ctx_release(c, c->ds_hist); ctx_release(c, c->ds_geom);
+    ctx_release(c, c->ds_part); ctx_release(c, c->ds_ticket); ctx_release(c, c->ds_hi);
+    ctx_release(c, c->ds_lo); ctx_release(c, c->ds_box);
+    c->ds_cap = 0;
+    const int64_t ntiles = (n + kDirThreads - 1) / kDirThreads;
+    int rc = ctx_alloc(c, c->ds_keys, n);
+    if (rc == GRAVITY_OK) rc = ctx_alloc(c, c->ds_keys_alt, n);
+    if (rc == GRAVITY_OK) rc = ctx_alloc(c, c->ds_idx, n);
+    if (rc == GRAVITY_OK) rc = ctx_alloc(c, c->ds_idx_alt, n);
+    if (rc == GRAVITY_OK) rc = ctx_alloc(c, c->ds_hist, radix_hist_words(n));
+    if (rc == GRAVITY_OK) rc = ctx_alloc(c, c->ds_geom, 8);
+    if (rc == GRAVITY_OK) rc = ctx_alloc(c, c->ds_part, 6 * (4 * (int64_t)c->num_sms + 3));
+    if (rc == GRAVITY_OK) rc = ctx_alloc(c, c->ds_ticket, 1);
+    if (rc == GRAVITY_OK) rc = ctx_alloc(c, c->ds_hi, n);
+    if (rc == GRAVITY_OK) rc = ctx_alloc(c, c->ds_lo, n);
+    if (rc == GRAVITY_OK) rc = ctx_alloc(c, c->ds_box, 2 * ntiles);
+    if (rc == GRAVITY_OK) rc = cuda_status(cudaMemset(c->ds_ticket, 0, sizeof(unsigned)));
     if (rc) return rc;
-    c->dir_cap = n;
+    c->ds_cap = n;
   }
-  k_split<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(pos, mass, n, c->dir_hi, c->dir_lo);
-  ++c->launches;
+  const MortonBuffers b{c->ds_keys, c->ds_keys_alt, c->ds_idx, c->ds_idx_alt, c->ds_hist,
+                        c->ds_geom, c->ds_part, c->ds_ticket};
+  int rc = morton_order(c, n, pos, b);
+  if (rc) return rc;
+  k_split_sorted<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(pos, mass, c->ds_idx, n,
+                                                                    c->ds_hi, c->ds_lo);
+  const int64_t ntiles = (n + kDirThreads - 1) / kDirThreads;
+  k_tile_box<<<(unsigned)ntiles, kDirThreads, 0, c->stream>>>(c->ds_hi, n, c->ds_box);
   const int64_t per_block = (int64_t)kDirThreads * kDirPerThread;
   const unsigned blocks = (unsigned)((n + per_block - 1) / per_block);
   const float eps2 = (float)(eps * eps);
   if (eps2 > 0.f)
-    k_direct<false><<<blocks, kDirThreads, 0, c->stream>>>(c->dir_hi, c->dir_lo, n, eps2, G, acc);
+    k_direct_sorted<false><<<blocks, kDirThreads, 0, c->stream>>>(c->ds_hi, c->ds_lo, c->ds_box,
+                                                                 c->ds_idx, n, eps2, G, acc);
   else
-    k_direct<true><<<blocks, kDirThreads, 0, c->stream>>>(c->dir_hi, c->dir_lo, n, eps2, G, acc);
-  ++c->launches;
+    k_direct_sorted<true><<<blocks, kDirThreads, 0, c->stream>>>(c->ds_hi, c->ds_lo, c->ds_box,
+                                                                c->ds_idx, n, eps2, G, acc);
+  c->launches += 3;
   return cuda_status(cudaGetLastError());
 }
 

@@ -121,6 +121,14 @@ struct Ctx {
   // direct-sum staging (caller order hi/lo)
   float4 *dir_hi = nullptr, *dir_lo = nullptr;
   int64_t dir_cap = 0;
+  // direct sum on Morton-sorted tiles: order, sorted hi/lo bodies, tile boxes
+  uint64_t *ds_keys = nullptr, *ds_keys_alt = nullptr;
+  uint32_t *ds_idx = nullptr, *ds_idx_alt = nullptr, *ds_hist = nullptr;
+  double *ds_geom = nullptr;
+  unsigned long long *ds_part = nullptr;
+  unsigned *ds_ticket = nullptr;
+  float4 *ds_hi = nullptr, *ds_lo = nullptr, *ds_box = nullptr;
+  int64_t ds_cap = 0;
   // diagnostics: m phi per body, block partials, result (nodes of 8 doubles)
   double *diag_buf = nullptr;
   int64_t diag_cap = 0;
@@ -131,6 +139,16 @@ struct Ctx {
 
 // ---- launchers (tree_build.cu)
 int tree_build(Ctx *c, int64_t n, const double *pos, const double *mass);
+struct MortonBuffers {
+  uint64_t *keys, *keys_alt;
+  uint32_t *idx, *idx_alt;
+  uint32_t *hist;                 // radix sort counts and tile states
+  double *geom;                   // 8 doubles: root cube of the bodies
+  unsigned long long *part;       // bounding-box partials, 6 per block
+  unsigned *ticket;               // zero before the first use; left zero
+};
+int morton_order(Ctx *c, int64_t n, const double *pos, const MortonBuffers &b);
+int64_t radix_hist_words(int64_t n);
 // ---- launchers (walk.cu)
 int walk_forces(Ctx *c, double theta, double eps, double *acc, int32_t *counts,
                 double *vel, double kick);

@@ -447,29 +447,31 @@ k_rs_sweep(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
 }
 
 // 8 passes over the 63-bit keys, then (several clouds) stable passes over the cloud
-// ids, so the order is by cloud, then key, then caller index.
-int radix_sort(Ctx *c, int64_t n) {
-  Tree &t = c->t;
+// ids, so the order is by cloud, then key, then caller index.  Sorts (keys, idx) in
+// place; keys_alt / idx_alt are the other halves of the ping-pong, hist the counts
+// and tile states (257 * kRsMaxPasses + passes * tiles * 256 words).
+int radix_sort_buffers(Ctx *c, int64_t n, uint64_t *keys, uint64_t *keys_alt, uint32_t *idx,
+                       uint32_t *idx_alt, uint32_t *hist, int cloud_passes,
+                       const int32_t *seg_of) {
   const int ntiles = (int)((n + kRsTile - 1) / kRsTile);
-  uint64_t *ka = t.keys, *kb = t.keys_alt;
-  uint32_t *va = t.idx, *vb = t.idx_alt;
-  const int cloud_passes = c->seg.nseg > 1 ? (c->seg.cbits + 7) / 8 : 0;
+  uint64_t *ka = keys, *kb = keys_alt;
+  uint32_t *va = idx, *vb = idx_alt;
   const int np = 8 + cloud_passes;
-  // t.hist: [kRsMaxPasses][256] digit counts, [kRsMaxPasses] tile counters,
+  // hist: [kRsMaxPasses][256] digit counts, [kRsMaxPasses] tile counters,
   // then [kRsMaxPasses][ntiles][256] published tile counts
-  uint32_t *ghist = t.hist, *counters = t.hist + 256 * kRsMaxPasses;
+  uint32_t *ghist = hist, *counters = hist + 256 * kRsMaxPasses;
   uint32_t *status = counters + kRsMaxPasses;
-  GRAV_CUDA_TRY(cudaMemsetAsync(t.hist, 0,
+  GRAV_CUDA_TRY(cudaMemsetAsync(hist, 0,
                                 sizeof(uint32_t) * ((size_t)(256 + 1) * kRsMaxPasses +
                                                     (size_t)np * ntiles * 256), c->stream));
   int cb = (int)((n + kRsThreads - 1) / kRsThreads);
   if (cb > 2 * c->num_sms) cb = 2 * c->num_sms;
-  k_rs_count<<<cb, kRsThreads, 0, c->stream>>>(t.keys, n, 8, cloud_passes, c->seg.seg_of, ghist);
+  k_rs_count<<<cb, kRsThreads, 0, c->stream>>>(keys, n, 8, cloud_passes, seg_of, ghist);
   ++c->launches;
   for (int pass = 0; pass < np; ++pass) {
     const bool cl = pass >= 8;
     const int shift = cl ? 8 * (pass - 8) : 8 * pass;
-    const int32_t *so = cl ? c->seg.seg_of : nullptr;
+    const int32_t *so = cl ? seg_of : nullptr;
     k_rs_sweep<<<ntiles, kRsThreads, 0, c->stream>>>(ka, va, kb, vb, n, shift, so,
                                                      ghist + 256 * pass,
                                                      status + (int64_t)pass * ntiles * 256,
@@ -479,10 +481,29 @@ int radix_sort(Ctx *c, int64_t n) {
     uint32_t *tv = va; va = vb; vb = tv;
   }
   if (np % 2) {                               // odd pass count: move the result back
-    GRAV_CUDA_TRY(cudaMemcpyAsync(t.keys, ka, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, c->stream));
-    GRAV_CUDA_TRY(cudaMemcpyAsync(t.idx, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, c->stream));
+    GRAV_CUDA_TRY(cudaMemcpyAsync(keys, ka, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, c->stream));
+    GRAV_CUDA_TRY(cudaMemcpyAsync(idx, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, c->stream));
   }
   return cuda_status(cudaGetLastError());
+}
+
+int radix_sort(Ctx *c, int64_t n) {
+  Tree &t = c->t;
+  const int cloud_passes = c->seg.nseg > 1 ? (c->seg.cbits + 7) / 8 : 0;
+  return radix_sort_buffers(c, n, t.keys, t.keys_alt, t.idx, t.idx_alt, t.hist, cloud_passes,
+                            c->seg.seg_of);
+}
+
+// Launch of k_bbox over one cloud of n bodies (grid a multiple of 3, see k_bbox).
+void launch_bbox(Ctx *c, const double *pos, int64_t n, unsigned long long *part,
+                 unsigned *ticket, double *geom) {
+  int64_t nb64 = (3 * n + 4 * kBBoxThreads - 1) / (4 * kBBoxThreads);
+  if (nb64 > 4 * (int64_t)c->num_sms) nb64 = 4 * (int64_t)c->num_sms;
+  nb64 = (nb64 + 2) / 3 * 3;
+  int nb = (int)nb64;
+  if (nb < 1) nb = 1;
+  k_bbox<<<nb, kBBoxThreads, 0, c->stream>>>(pos, n, part, ticket, geom, c->d_status);
+  ++c->launches;
 }
 
 // ------------------------------------------------------------------ a4: gather
@@ -967,17 +988,12 @@ int tree_build(Ctx *c, int64_t n, const double *pos, const double *mass) {
   const bool multi = sg.nseg > 1;
   // a1: root cube of each cloud (also validates the coordinates)
   if (!multi) {
-    int64_t nb64 = (3 * n + 4 * kBBoxThreads - 1) / (4 * kBBoxThreads);
-    if (nb64 > 4 * (int64_t)c->num_sms) nb64 = 4 * (int64_t)c->num_sms;
-    nb64 = (nb64 + 2) / 3 * 3;               // stride multiple of 3 (see k_bbox)
-    int nb = (int)nb64;
-    if (nb < 1) nb = 1;
-    k_bbox<<<nb, kBBoxThreads, 0, s>>>(pos, n, reinterpret_cast<unsigned long long *>(t.bbox_part),
-                                       t.bbox_ticket, t.geom, c->d_status);
+    launch_bbox(c, pos, n, reinterpret_cast<unsigned long long *>(t.bbox_part), t.bbox_ticket,
+                t.geom);
   } else {
     k_bbox_seg<<<sg.nseg, kBBoxThreads, 0, s>>>(pos, sg.off, t.geom, c->d_status);
+    ++c->launches;
   }
-  ++c->launches;
   // a2: keys
   k_keys<<<blocks_for(n, 256), 256, 0, s>>>(pos, n, t.geom, multi ? sg.seg_of : nullptr, t.keys,
                                              t.idx);
@@ -1040,6 +1056,21 @@ int tree_build(Ctx *c, int64_t n, const double *pos, const double *mass) {
     ++c->launches;
   }
   return cuda_status(cudaGetLastError());
+}
+
+// Morton order of n bodies of one cloud (for the direct sum's tiling): root cube,
+// keys and the radix sort into caller-provided buffers; idx ends as the permutation
+// (sorted position -> caller index).
+int64_t radix_hist_words(int64_t n) {
+  const int64_t ntiles = (n + kRsTile - 1) / kRsTile;
+  return (int64_t)257 * kRsMaxPasses + (int64_t)kRsMaxPasses * 256 * ntiles;
+}
+
+int morton_order(Ctx *c, int64_t n, const double *pos, const MortonBuffers &b) {
+  launch_bbox(c, pos, n, b.part, b.ticket, b.geom);
+  k_keys<<<blocks_for(n, 256), 256, 0, c->stream>>>(pos, n, b.geom, nullptr, b.keys, b.idx);
+  ++c->launches;
+  return radix_sort_buffers(c, n, b.keys, b.keys_alt, b.idx, b.idx_alt, b.hist, 0, nullptr);
 }
 
 }  // namespace grav
