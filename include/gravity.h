@@ -192,8 +192,9 @@ int gravity_batch_tree_build(gravity_ctx *ctx, int32_t nclouds, const int64_t *o
 
 /* Eq. (Newton) with the softening of Eq. (Force_rComp), all N(N-1) pairs:
  * acc_i = G sum_{j != i} m_j (R_j - R_i) / (|R_j - R_i|^2 + eps^2)^{3/2}.
- * FP32 pair terms, compensated accumulation, FP64 out.  The bodies are put in Morton
- * order first (the context's own buffers; its tree is untouched) so that each source
+ * FP32 pair terms, compensated accumulation, FP64 out.  From 32768 bodies on, the
+ * bodies are put in Morton order first (the context's own buffers; its tree is
+ * untouched) so that each source
  * tile far from a block of targets is evaluated on FP32 coordinates relative to the
  * block, the others on hi/lo split coordinates; every term's error stays a few 2^-24 of
  * its size. */

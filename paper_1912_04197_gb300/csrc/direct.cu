@@ -2,13 +2,13 @@
 // Eq. (Force_rComp): a_i = G sum_{j != i} m_j d_ij / (|d_ij|^2 + eps^2)^{3/2}.
 // FP32 pair terms, source tiles staged in shared memory, each tile's partial sum added
 // to a (hi, lo) two-sum accumulator.  The self term has d = 0 and adds zero.
-// gravity_direct first puts the bodies in Morton order, so that a block's 512 bodies
-// and a 256-body source tile are each compact: a tile away from the block (gap between
-// their boxes at least half the block's diagonal w) is evaluated on FP32 coordinates
-// relative to the block's first body, d = s_rel - x_rel, whose error is then below
-// 2^-24 (2 |d| + 2 w) <= 6 * 2^-24 |d|; nearer tiles use hi/lo split coordinates,
-// d = (x_j,hi - x_i,hi) + (x_j,lo - x_i,lo).  The allocation-free entry point keeps
-// the caller's order and the hi/lo form throughout.
+// From 32768 bodies on, gravity_direct first puts the bodies in Morton order, so that a
+// block's 512 bodies and a 256-body source tile are each compact: a tile away from the
+// block (gap between their boxes at least half the block's diagonal w) is evaluated on
+// FP32 coordinates relative to the block's first body, d = s_rel - x_rel, whose error is
+// then below 2^-24 (2 |d| + 2 w) <= 6 * 2^-24 |d|; nearer tiles use hi/lo split
+// coordinates, d = (x_j,hi - x_i,hi) + (x_j,lo - x_i,lo).  Smaller sums, and the
+// allocation-free entry point, keep the caller's order and the hi/lo form throughout.
 #include "internal.cuh"
 
 namespace grav {
@@ -342,8 +342,33 @@ __global__ void k_diag_final(const double *__restrict__ part, double G, double *
 
 }  // namespace
 
+// Below this many bodies the Morton order costs more than the far tiles save.
+constexpr int64_t kDirSortMin = 32768;
+
 int direct_forces(Ctx *c, int64_t n, const double *pos, const double *mass, double eps, double G,
                   double *acc) {
+  if (n < kDirSortMin) {                       // caller order, hi/lo for every pair
+    if (n > c->dir_cap) {
+      GRAV_CUDA_TRY(cudaStreamSynchronize(c->stream));
+      ctx_release(c, c->dir_hi);
+      ctx_release(c, c->dir_lo);
+      c->dir_cap = 0;
+      int rc = ctx_alloc(c, c->dir_hi, n);
+      if (rc == GRAVITY_OK) rc = ctx_alloc(c, c->dir_lo, n);
+      if (rc) return rc;
+      c->dir_cap = n;
+    }
+    k_split<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(pos, mass, n, c->dir_hi, c->dir_lo);
+    const int64_t per_block = (int64_t)kDirThreads * kDirPerThread;
+    const unsigned blocks = (unsigned)((n + per_block - 1) / per_block);
+    const float eps2 = (float)(eps * eps);
+    if (eps2 > 0.f)
+      k_direct<false><<<blocks, kDirThreads, 0, c->stream>>>(c->dir_hi, c->dir_lo, n, eps2, G, acc);
+    else
+      k_direct<true><<<blocks, kDirThreads, 0, c->stream>>>(c->dir_hi, c->dir_lo, n, eps2, G, acc);
+    c->launches += 2;
+    return cuda_status(cudaGetLastError());
+  }
   if (n > c->ds_cap) {
     GRAV_CUDA_TRY(cudaStreamSynchronize(c->stream));
     ctx_release(c, c->ds_keys); ctx_release(c, c->ds_keys_alt); ctx_release(c, c->ds_idx);

@@ -74,6 +74,29 @@ def test_tree_forces_vs_oracle(gpu, case, theta, leaf_max, order):
     assert np.array_equal(a, a2)
 
 
+@pytest.mark.parametrize("kind,n,eps,G", [("clumpy", 70_001, 1e-3, 1.0), ("sphere", 40_000, 0.0, 1.7)])
+def test_direct_sorted_tiles_vs_oracle(gpu, kind, n, eps, G):
+    # from 32768 bodies on the direct sum runs on Morton-sorted tiles (block-relative
+    # coordinates for tiles away from a block, hi/lo for the others): sampled bodies
+    # against the oracle's FP64 sum, a coincident pair included (eps = 0: adds nothing)
+    if kind == "clumpy":
+        pos, _, m = inputs.clumpy_plummer(n, seed=31, nclusters=8)
+    else:
+        pos, _, m = inputs.uniform_sphere(n, seed=32)
+        pos[17] = pos[12345]
+    ctx = gpu.Context(0)
+    P = torch.tensor(pos, device="cuda")
+    M = torch.tensor(m, device="cuda")
+    acc = torch.empty_like(P)
+    gpu.gravity_direct(ctx, P, M, eps, G, acc)
+    gpu.gravity_sync(ctx)
+    idx = np.union1d(inputs.subset(n, 2048, seed=33), [17, 12345, 0, n - 1])
+    ref, absum = oracle.direct(pos, m, eps, G, targets=idx)
+    a = acc.cpu().numpy()
+    assert np.all(np.isfinite(a))
+    _check(a[idx], ref, absum)
+
+
 @pytest.mark.parametrize("mac_guard,accum,eps", [(0, 0, 1e-3), (1, 1, 1e-3), (1, 0, 0.0)])
 def test_tree_variants(gpu, mac_guard, accum, eps):
     pos, _, m = inputs.clumpy_plummer(20_000, seed=7, nclusters=4)
