@@ -5,6 +5,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.cuh"
 
 struct gravity_ctx {
@@ -12,6 +14,15 @@ struct gravity_ctx {
 };
 
 namespace grav {
+
+// A named range around each entry point, visible to a profiler (NVTX; no cost when none
+// is attached).
+struct Range {
+  explicit Range(const char *name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range &) = delete;
+  Range &operator=(const Range &) = delete;
+};
 
 // Largest body count: octree node indices (< 2n) must fit the walk's 25-bit fields.
 constexpr int64_t kMaxBodies = (int64_t)1 << 24;
@@ -394,6 +405,7 @@ int gravity_set_stream(gravity_ctx *h, void *cuda_stream) {
 
 int gravity_tree_build(gravity_ctx *h, int64_t n, const double *pos, const double *mass,
                        const gravity_params *p) {
+  grav::Range range_("gravity_tree_build");
   if (!h || n < 0 || n > grav::kMaxBodies) return GRAVITY_E_ARG;
   if (n > 0 && (!pos || !mass)) return GRAVITY_E_ARG;
   int rc = grav::check_params(p);
@@ -412,6 +424,7 @@ int gravity_tree_build(gravity_ctx *h, int64_t n, const double *pos, const doubl
 }
 
 static int forces_common(gravity_ctx *h, double theta, double eps, double *acc, int32_t *counts) {
+  grav::Range range_("gravity_forces");
   if (!h || !(theta >= 0.0) || !(eps >= 0.0) || !std::isfinite(theta) || !std::isfinite(eps))
     return GRAVITY_E_ARG;
   Ctx &c = h->c;
@@ -435,6 +448,7 @@ int gravity_forces_counted(gravity_ctx *h, double theta, double eps, double *acc
 
 int gravity_forces_vjp(gravity_ctx *h, double theta, double eps, const double *lambda,
                        double *grad_pos) {
+  grav::Range range_("gravity_forces_vjp");
   if (!h || !(theta >= 0.0) || !(eps >= 0.0) || !std::isfinite(theta) || !std::isfinite(eps))
     return GRAVITY_E_ARG;
   Ctx &c = h->c;
@@ -449,6 +463,7 @@ int gravity_forces_vjp(gravity_ctx *h, double theta, double eps, const double *l
 
 int gravity_direct(gravity_ctx *h, int64_t n, const double *pos, const double *mass, double eps,
                    double G, double *acc) {
+  grav::Range range_("gravity_direct");
   if (!h || n < 0 || !(eps >= 0.0) || !std::isfinite(eps) || !std::isfinite(G))
     return GRAVITY_E_ARG;
   if (n == 0) return GRAVITY_OK;
@@ -460,6 +475,7 @@ int gravity_direct(gravity_ctx *h, int64_t n, const double *pos, const double *m
 
 int gravity_diagnostics(gravity_ctx *h, int64_t n, const double *pos, const double *vel,
                         const double *mass, double eps, double G, double *out) {
+  grav::Range range_("gravity_diagnostics");
   if (!h || n < 0 || !(eps >= 0.0) || !std::isfinite(eps) || !std::isfinite(G) || !out)
     return GRAVITY_E_ARG;
   if (n > 0 && (!pos || !vel || !mass)) return GRAVITY_E_ARG;
@@ -476,6 +492,7 @@ int gravity_diagnostics(gravity_ctx *h, int64_t n, const double *pos, const doub
 int leapfrog_step(gravity_ctx *h, int64_t n, double *pos, double *vel, const double *mass,
                   double *acc_cache, double dt, int nsteps, double theta, double eps,
                   const gravity_params *p) {
+  grav::Range range_("leapfrog_step");
   if (!h || n < 0 || n > grav::kMaxBodies || nsteps < 0 || !std::isfinite(dt)) return GRAVITY_E_ARG;
   if (!(theta >= 0.0) || !(eps >= 0.0) || !std::isfinite(theta) || !std::isfinite(eps))
     return GRAVITY_E_ARG;
@@ -537,6 +554,7 @@ int leapfrog_step(gravity_ctx *h, int64_t n, double *pos, double *vel, const dou
 int leapfrog_adjoint(gravity_ctx *h, int64_t n, const double *pos0, const double *vel0,
                      const double *mass, double dt, int nsteps, double theta, double eps,
                      const gravity_params *p, int flags, double *xbar, double *vbar) {
+  grav::Range range_("leapfrog_adjoint");
   if (!h || n < 0 || n > grav::kMaxBodies || nsteps < 0 || !std::isfinite(dt)) return GRAVITY_E_ARG;
   if (!(theta >= 0.0) || !(eps >= 0.0) || !std::isfinite(theta) || !std::isfinite(eps))
     return GRAVITY_E_ARG;
@@ -632,6 +650,7 @@ int leapfrog_adjoint(gravity_ctx *h, int64_t n, const double *pos0, const double
 }
 
 int gravity_set_clouds(gravity_ctx *h, int32_t nclouds, const int64_t *offsets_host) {
+  grav::Range range_("gravity_set_clouds");
   if (!h || nclouds < 0) return GRAVITY_E_ARG;
   if (nclouds > 1 && !offsets_host) return GRAVITY_E_ARG;
   if (offsets_host && nclouds >= 1) {          // off[0] = 0, strictly increasing
@@ -675,6 +694,7 @@ int gravity_sync(gravity_ctx *h) {
 
 int gravity_forces_host(gravity_ctx *h, int64_t n, const double *pos_host, const double *mass_host,
                         double theta, double eps, const gravity_params *p, double *acc_host) {
+  grav::Range range_("gravity_forces_host");
   if (!h || n < 0 || n > grav::kMaxBodies) return GRAVITY_E_ARG;
   if (n > 0 && (!pos_host || !mass_host || !acc_host)) return GRAVITY_E_ARG;
   if (!(theta >= 0.0) || !(eps >= 0.0) || !std::isfinite(theta) || !std::isfinite(eps))
