@@ -109,3 +109,21 @@ def test_allocator_refusing_the_fixed_buffers_keeps_the_previous_one(gpu):
     assert e.value.code == gpu.GRAVITY_E_NOMEM
     pos, _, m = inputs.uniform_sphere(3000, seed=6)
     assert np.isfinite(_forces(gpu, ctx, pos, m)).all()
+
+
+def test_torch_pool_allocator_helper(gpu):
+    # the binding's helper hands the context's memory to PyTorch's caching allocator
+    pos, _, m = inputs.clumpy_plummer(40_000, seed=7, nclusters=4)
+    ref = _forces(gpu, gpu.Context(0), pos, m, order=2, leaf_max=16)
+    ctx = gpu.Context(0)
+    before = torch.cuda.memory_allocated(0)
+    gpu.use_torch_allocator(ctx)
+    got = _forces(gpu, ctx, pos, m, order=2, leaf_max=16)
+    held = torch.cuda.memory_allocated(0) - before
+    assert np.array_equal(got, ref)
+    assert held > 0                            # the tree lives in the torch pool now
+    ctx.close()
+    assert torch.cuda.memory_allocated(0) - before <= 0
+    with pytest.raises(gpu.GravityError) as e:
+        gpu.gravity_debug_set(gpu.Context(0), 99, 0)
+    assert e.value.code == gpu.GRAVITY_E_ARG
