@@ -83,6 +83,7 @@ struct WarpSmem {
   float4 fa[kListCap];            // far list:   (c_rel xyz, m)
   float4 fc[kListCap];            //             (q_xz, q_yz, lane mask bits, 0)
   int32_t ltag[kListCap];         // counting / VJP: -(node+1) node term, else sorted body index
+  float4 org_h, org_l;            // the warp origin (lane 0's body), hi and lo parts
 };
 
 // Vector-Jacobian product (order 0): far-list sources and the lane-to-source
@@ -156,15 +157,25 @@ __device__ __forceinline__ void two_sum_add(float &hi, float &lo, float p) {
   lo += err;
 }
 
+// Per-body accumulator: a (hi, lo) two-sum pair per component, or (accum = 1) an FP64
+// sum whose bits live in the same two 32-bit registers (hi word, lo word).
+__device__ __forceinline__ void add64(float &h, float &l, float p) {
+  const double d = __hiloint2double(__float_as_int(h), __float_as_int(l)) + (double)p;
+  h = __int_as_float(__double2hiint(d));
+  l = __int_as_float(__double2loint(d));
+}
+__device__ __forceinline__ double get64(float h, float l) {
+  return __hiloint2double(__float_as_int(h), __float_as_int(l));
+}
+
 struct Accum {
-  float hx = 0, hy = 0, hz = 0, lx = 0, ly = 0, lz = 0;
-  double dx = 0, dy = 0, dz = 0;
+  float hx = 0, hy = 0, hz = 0, lx = 0, ly = 0, lz = 0;   // all-zero bits = 0.0 as FP64 too
   __device__ __forceinline__ void add(bool acc64, float px, float py, float pz) {
-    if (acc64) { dx += (double)px; dy += (double)py; dz += (double)pz; }
+    if (acc64) { add64(hx, lx, px); add64(hy, ly, py); add64(hz, lz, pz); }
     else { two_sum_add(hx, lx, px); two_sum_add(hy, ly, py); two_sum_add(hz, lz, pz); }
   }
   __device__ __forceinline__ void get(bool acc64, double &x, double &y, double &z) const {
-    if (acc64) { x = dx; y = dy; z = dz; }
+    if (acc64) { x = get64(hx, lx); y = get64(hy, ly); z = get64(hz, lz); }
     else { x = (double)hx + (double)lx; y = (double)hy + (double)ly; z = (double)hz + (double)lz; }
   }
 };
@@ -383,8 +394,11 @@ struct Stack {
   }
 };
 
+// Force and VJP modes are held to 6 (quadrupole: 80 registers; the shared memory of its
+// lists allows no more) or 7 (monopole: 72 registers) resident blocks of 4 warps per SM;
+// the counted mode is not held to either.
 template <int ORDER, bool EPS0, int MODE>
-__global__ void __launch_bounds__(32 * kWalkWarps)
+__global__ void __launch_bounds__(32 * kWalkWarps, MODE == kModeCount ? 1 : (ORDER == 2 ? 6 : 7))
 k_walk(WalkArgs A) {
   constexpr bool COUNT = MODE == kModeCount;
   constexpr bool VJP = MODE == kModeVjp;
@@ -446,7 +460,6 @@ k_walk(WalkArgs A) {
         first_entry = (uint32_t)(rt.x + part * h) | ((uint32_t)(cnt - 1) << kCntShift);
       }
     }
-    const double side = A.geom[8 * root + 3];
     const int gi = wbeg + lane;
     const bool valid = gi < wend;
 
@@ -466,6 +479,10 @@ k_walk(WalkArgs A) {
     const float ohx = __shfl_sync(0xffffffffu, xh, 0), ohy = __shfl_sync(0xffffffffu, yh, 0),
                 ohz = __shfl_sync(0xffffffffu, zh, 0), olx = __shfl_sync(0xffffffffu, xl, 0),
                 oly = __shfl_sync(0xffffffffu, yl, 0), olz = __shfl_sync(0xffffffffu, zl, 0);
+    if (lane == 0) {                            // kept in shared memory for the far appends
+      M.org_h = make_float4(ohx, ohy, ohz, 0.f);
+      M.org_l = make_float4(olx, oly, olz, 0.f);
+    }
     const float xr = valid ? (xh - ohx) + (xl - olx) : 0.f;
     const float yr = valid ? (yh - ohy) + (yl - oly) : 0.f;
     const float zr = valid ? (zh - ohz) + (zl - olz) : 0.f;
@@ -632,7 +649,7 @@ k_walk(WalkArgs A) {
               const double ddx = __dsub_rn(X, x), ddy = __dsub_rn(Y, y), ddz = __dsub_rn(Z, z);
               const double D2d = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)),
                                            __dmul_rn(ddz, ddz));
-              const double l = __dmul_rn(side, pow2_neg(A.ndepth[node]));
+              const double l = __dmul_rn(A.geom[8 * root + 3], pow2_neg(A.ndepth[node]));
               a_i = __dmul_rn(l, l) < __dmul_rn(A.theta2d, D2d);
               if (COUNT) atomicAdd(&A.stats[kStatFp64], 1ull);
             } else {
@@ -666,9 +683,10 @@ k_walk(WalkArgs A) {
         const unsigned bf = __ballot_sync(0xffffffffu, to_far);
         if (to_far) {
           const int p = nfar + __popc(bf & ((1u << lane) - 1u));
-          const float cx = (r0.x - ohx) + (r1.x - olx);
-          const float cy = (r0.y - ohy) + (r1.y - oly);
-          const float cz = (r0.z - ohz) + (r1.z - olz);
+          const float4 oh = M.org_h, ol = M.org_l;
+          const float cx = (r0.x - oh.x) + (r1.x - ol.x);
+          const float cy = (r0.y - oh.y) + (r1.y - ol.y);
+          const float cz = (r0.z - oh.z) + (r1.z - ol.z);
           M.fa[p] = make_float4(cx, cy, cz, r0.w);
           if constexpr (VJP) S.ftag[p] = item;
           if constexpr (ORDER == 2) {
