@@ -84,6 +84,7 @@ struct WarpSmem {
   float4 fc[kListCap];            //             (q_xz, q_yz, lane mask bits, 0)
   int32_t ltag[kListCap];         // counting / VJP: -(node+1) node term, else sorted body index
   float4 org_h, org_l;            // the warp origin (lane 0's body), hi and lo parts
+  int32_t bitem[32];              // node id of each lane's item (mixed nodes' FP64 decisions)
 };
 
 // Vector-Jacobian product (order 0): far-list sources and the lane-to-source
@@ -196,11 +197,12 @@ __device__ __forceinline__ void flush_point(const WarpSmem &S, int cnt, int lane
                                             float eps2, float &px, float &py, float &pz,
                                             int gi, int &c_m2p, int &c_p2p) {
   px = py = pz = 0.f;
+  const unsigned lbit = 1u << lane;
 #pragma unroll 4
   for (int k = 0; k < cnt; ++k) {
     const float4 a = S.la[k];
     const float4 b = S.lb[k];
-    const bool act = (__float_as_uint(b.w) >> lane) & 1u;
+    const bool act = (__float_as_uint(b.w) & lbit) != 0u;
     const float dx = (a.x - xh) + (b.x - xl);
     const float dy = (a.y - yh) + (b.y - yl);
     const float dz = (a.z - zh) + (b.z - zl);
@@ -245,11 +247,12 @@ __device__ __forceinline__ void flush_far(const void *Sv, int cnt, int lane, flo
                                           int &c_m2p) {
   const WarpSmem &S = *reinterpret_cast<const WarpSmem *>(Sv);
   px = py = pz = 0.f;
+  const unsigned lbit = 1u << lane;
 #pragma unroll 2
   for (int k = 0; k < cnt; ++k) {
     const float4 a = S.fa[k];
     const float4 c = S.fc[k];
-    const bool act = (__float_as_uint(c.z) >> lane) & 1u;
+    const bool act = (__float_as_uint(c.z) & lbit) != 0u;
     const float dx = a.x - xr, dy = a.y - yr, dz = a.z - zr;
     const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
     const float inv = inv_r<EPS0>(r2, act);
@@ -273,10 +276,11 @@ __device__ __forceinline__ void flush_near(const WarpSmemQ &S, int cnt, int lane
                                            float eps2, float &px, float &py, float &pz,
                                            int &c_m2p) {
   px = py = pz = 0.f;
+  const unsigned lbit = 1u << lane;
 #pragma unroll 2
   for (int k = 0; k < cnt; ++k) {
     const float4 a = S.qa[k], b = S.qb[k], q0 = S.qc[k], q1 = S.qd[k];
-    const bool act = (__float_as_uint(b.w) >> lane) & 1u;
+    const bool act = (__float_as_uint(b.w) & lbit) != 0u;
     const float dx = (a.x - xh) + (b.x - xl);
     const float dy = (a.y - yh) + (b.y - yl);
     const float dz = (a.z - zh) + (b.z - zl);
@@ -549,8 +553,9 @@ k_walk(WalkArgs A) {
       }
       sp -= nfull;
       const unsigned starts = __reduce_or_sync(0xffffffffu, take > 0 ? (1u << excl) : 0u);
-      const int stpos = 31 - __clz(starts & (0xffffffffu >> (31 - lane)));
-      const int owner = __popc(starts & ((1u << stpos) - 1u));
+      const unsigned starts_le = starts & (0xffffffffu >> (31 - lane));
+      const int stpos = 31 - __clz(starts_le);
+      const int owner = __popc(starts_le) - 1;
       const uint32_t oa = __shfl_sync(0xffffffffu, ea, owner);
       const uint32_t omask = __shfl_sync(0xffffffffu, em, owner);
       const bool have = lane < nitems;
@@ -592,6 +597,7 @@ k_walk(WalkArgs A) {
         break;
       }
       unsigned accm = 0, openm = 0;
+      unsigned tmask = 0;                      // mixed node: the lanes that test it themselves
       bool mixed = false;
       if (have) {
         if (single) {
@@ -610,9 +616,19 @@ k_walk(WalkArgs A) {
           const float dmin2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
           const float dmax2 = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
           const bool guard_any = A.mac_guard && tp.z < wend && tp.w > wbeg;
-          if (!guard_any && l2 < theta2f * dmin2 * 0.999f) accm = omask;
-          else if (l2 > theta2f * dmax2 * 1.001f) openm = omask;
-          else mixed = true;
+          if (!guard_any && l2 < theta2f * dmin2 * 0.999f) {
+            accm = omask;
+          } else if (l2 > theta2f * dmax2 * 1.001f) {
+            openm = omask;
+          } else {
+            mixed = true;
+            unsigned gm = 0;                   // lanes whose body is in the node: opened
+            if (A.mac_guard) {
+              const int lo = min(max(tp.z - wbeg, 0), 32), hi = min(max(tp.w - wbeg, 0), 32);
+              gm = (unsigned)(((1ull << hi) - 1ull) & ~((1ull << lo) - 1ull));
+            }
+            tmask = omask & ~gm;
+          }
         }
       }
       if (COUNT) {                             // MAC tests per body (introspection only)
@@ -623,45 +639,51 @@ k_walk(WalkArgs A) {
           if (!sj && ((mj >> lane) & 1u) && !(A.mac_guard && bj <= gi && gi < ej)) ++c_tests;
         }
       }
-      // ---- exact per-lane test for mixed nodes (node record re-read from L1 by all lanes)
+      // ---- exact per-lane test for mixed nodes: the owner lane broadcasts the node's
+      // record and the mask of lanes that test it; every other lane of the node's mask
+      // has its body inside the node and opens it
       unsigned mixed_bits = __ballot_sync(0xffffffffu, mixed);
       if (COUNT) w_mixed += __popc(mixed_bits);
+      if (mixed_bits) {
+        if (mixed) M.bitem[lane] = item;
+        __syncwarp();
+      }
       while (mixed_bits) {
         const int j = __ffs(mixed_bits) - 1;
         mixed_bits &= mixed_bits - 1;
-        const int node = __shfl_sync(0xffffffffu, item, j);
-        const unsigned mk = __shfl_sync(0xffffffffu, omask, j);
-        bool a_i = false, o_i = false;
-        if ((mk >> lane) & 1u) {
-          const int4 tj = A.topo[node];
-          if (A.mac_guard && tj.z <= gi && gi < tj.w) {
-            o_i = true;
+        const unsigned tk = __shfl_sync(0xffffffffu, tmask, j);
+        float4 c0, c1;
+        c0.x = __shfl_sync(0xffffffffu, r0.x, j); c0.y = __shfl_sync(0xffffffffu, r0.y, j);
+        c0.z = __shfl_sync(0xffffffffu, r0.z, j); c1.x = __shfl_sync(0xffffffffu, r1.x, j);
+        c1.y = __shfl_sync(0xffffffffu, r1.y, j); c1.z = __shfl_sync(0xffffffffu, r1.z, j);
+        c1.w = __shfl_sync(0xffffffffu, r1.w, j);
+        bool a_i = false;
+        if (tk & (1u << lane)) {
+          const float dx = (c0.x - xh) + (c1.x - xl);
+          const float dy = (c0.y - yh) + (c1.y - yl);
+          const float dz = (c0.z - zh) + (c1.z - zl);
+          const float D2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          const float diff = c1.w - theta2f * D2;
+          if (fabsf(diff) <= 1.52587890625e-5f * c1.w) {    // 2^-16 band: decide in FP64
+            const int node = M.bitem[j];
+            const double X = A.ncom[3 * node], Y = A.ncom[3 * node + 1], Z = A.ncom[3 * node + 2];
+            const double x = A.pos_s[3 * gi], y = A.pos_s[3 * gi + 1], z = A.pos_s[3 * gi + 2];
+            const double ddx = __dsub_rn(X, x), ddy = __dsub_rn(Y, y), ddz = __dsub_rn(Z, z);
+            const double D2d = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)),
+                                         __dmul_rn(ddz, ddz));
+            const double l = __dmul_rn(A.geom[8 * root + 3], pow2_neg(A.ndepth[node]));
+            a_i = __dmul_rn(l, l) < __dmul_rn(A.theta2d, D2d);
+            if (COUNT) atomicAdd(&A.stats[kStatFp64], 1ull);
           } else {
-            const float4 c0 = A.rec0[node], c1 = A.rec1[node];
-            const float dx = (c0.x - xh) + (c1.x - xl);
-            const float dy = (c0.y - yh) + (c1.y - yl);
-            const float dz = (c0.z - zh) + (c1.z - zl);
-            const float D2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float diff = c1.w - theta2f * D2;
-            if (fabsf(diff) <= 1.52587890625e-5f * c1.w) {    // 2^-16 band: decide in FP64
-              const double X = A.ncom[3 * node], Y = A.ncom[3 * node + 1], Z = A.ncom[3 * node + 2];
-              const double x = A.pos_s[3 * gi], y = A.pos_s[3 * gi + 1], z = A.pos_s[3 * gi + 2];
-              const double ddx = __dsub_rn(X, x), ddy = __dsub_rn(Y, y), ddz = __dsub_rn(Z, z);
-              const double D2d = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)),
-                                           __dmul_rn(ddz, ddz));
-              const double l = __dmul_rn(A.geom[8 * root + 3], pow2_neg(A.ndepth[node]));
-              a_i = __dmul_rn(l, l) < __dmul_rn(A.theta2d, D2d);
-              if (COUNT) atomicAdd(&A.stats[kStatFp64], 1ull);
-            } else {
-              a_i = diff < 0.f;
-            }
-            o_i = !a_i;
+            a_i = diff < 0.f;
           }
         }
         const unsigned am = __ballot_sync(0xffffffffu, a_i);
-        const unsigned om = __ballot_sync(0xffffffffu, o_i);
-        if (lane == j) { accm = am; openm = om; }
-        if (COUNT && lane == 0 && (am == mk || om == mk)) atomicAdd(&A.stats[kStatMixedUnanimous], 1ull);
+        if (lane == j) { accm = am; openm = omask & ~am; }   // tested lanes accept or open
+        if (COUNT) {
+          const unsigned mk = __shfl_sync(0xffffffffu, omask, j);
+          if (lane == 0 && (am == mk || am == 0u)) atomicAdd(&A.stats[kStatMixedUnanimous], 1ull);
+        }
       }
 
       // ---- append accepted terms: point / far / near
