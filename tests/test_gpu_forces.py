@@ -205,3 +205,31 @@ def test_leapfrog_graph_replay_matches_eager(gpu, clouds):
         out.append((P.cpu().numpy(), V.cpu().numpy(), A.cpu().numpy()))
     for x, y in zip(out[0], out[1]):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("mac_guard", [1, 0])
+def test_opening_band_on_a_lattice(gpu, mac_guard):
+    # A 17^3 lattice on [0, 1]^3 (root side 1): depth-3 cells (side 1/8) hold 2x2x2 bodies
+    # with the COM at odd multiples of 1/32, so bodies at offsets (5, 3, 3)/32 see
+    # l^2 = theta^2 D^2 up to the rounding of theta^2 = 16/43 (Eq. accuracy at equality).
+    # These tests land in the kernel's FP32 uncertainty band and are taken in FP64; the
+    # decision counts must still equal the oracle's for every body.
+    k = np.arange(17) / 16.0
+    pos = np.stack(np.meshgrid(k, k, k, indexing="ij"), -1).reshape(-1, 3)
+    m = np.ones(len(pos))
+    theta = float(np.sqrt(16.0 / 43.0))
+    ctx = gpu.Context(0)
+    P = torch.tensor(pos, device="cuda")
+    M = torch.tensor(m, device="cuda")
+    gpu.gravity_tree_build(ctx, P, M, gpu.params(leaf_max=1, order=0, mac_guard=mac_guard))
+    acc = torch.empty_like(P)
+    cnt = torch.empty((len(pos), 3), dtype=torch.int32, device="cuda")
+    gpu.gravity_forces_counted(ctx, theta, 1e-3, acc, cnt)
+    gpu.gravity_sync(ctx)
+    fp64_decisions = int(gpu.gravity_debug_export(ctx, gpu.DBG_WALKSTATS, 16)[3])
+    assert fp64_decisions >= 1000, fp64_decisions
+    ref, absum, ocnt = oracle.Tree(pos, m, leaf_max=1).forces(theta, 1e-3, mac_guard=mac_guard)
+    c = cnt.cpu().numpy()
+    assert np.array_equal(c[:, 0], ocnt[:, 1]) and np.array_equal(c[:, 1], ocnt[:, 2])
+    assert np.array_equal(c[:, 2], ocnt[:, 0])
+    _check(acc.cpu().numpy(), ref, absum)
