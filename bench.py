@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="default walk shape, no autotuning")
     ap.add_argument("--ensemble-steps", type=int, default=50)
     ap.add_argument("--no-grad", action="store_true", help="skip the gradient (adjoint) leg")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the theta / accumulator sweep (runs with the direct-sum leg)")
     return ap.parse_args()
 
 
@@ -244,6 +246,53 @@ def walk_traffic(order):
     return float(vals[key]) if key in vals else None
 
 
+def theta_sweep_leg(args, g, ctx, P, M, accd, p, flush, stream):
+    """The same workload at theta 0.3 / 0.5 / 0.7 / 0.9, with the FP32 two-sum and the FP64
+    accumulator: walk time (CUDA events, L2 flushed), FLOP rate from the exact decision
+    counts, error against the direct sum, and the largest difference between the two
+    accumulators relative to the force."""
+    import torch
+    n = P.shape[0]
+    dev = P.device
+    f_node = FLOP_QUAD if args.order == 2 else FLOP_POINT
+    acc = torch.empty_like(P)
+    cnt = torch.empty((n, 3), dtype=torch.int32, device=dev)
+    res = {}
+    rows = []
+    for accum in (0, 1):
+        q = g.params(order=args.order, leaf_max=args.leaf_max, accum=accum, walk_cfg=p.walk_cfg)
+        g.gravity_tree_build(ctx, P, M, q)
+        for theta in (0.3, 0.5, 0.7, 0.9):
+            g.gravity_forces_counted(ctx, theta, args.eps, acc, cnt)
+            c = cnt.to(torch.int64).sum(0).cpu().numpy()
+            flops = int(c[0]) * f_node + int(c[1]) * FLOP_POINT + int(c[2]) * FLOP_MAC
+            ts = []
+            for k in range(5):
+                flush.fill_(float(k))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                g.gravity_forces(ctx, theta, args.eps, acc)
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            g.gravity_sync(ctx)
+            t = float(np.median(ts))
+            rel = (torch.linalg.norm(acc - accd, dim=1) / torch.linalg.norm(accd, dim=1)).cpu().numpy()
+            res[(accum, theta)] = acc.clone()
+            rows.append({"theta": theta, "accum": "fp32-two-sum" if accum == 0 else "fp64",
+                         "walk_ms": t, "tflops": flops / (t * 1e-3) / 1e12,
+                         "node_terms": int(c[0]), "body_terms": int(c[1]), "opening_tests": int(c[2]),
+                         "median_error": float(np.median(rel)),
+                         "p99_error": float(np.quantile(rel, 0.99))})
+    for r in rows:
+        if r["accum"] == "fp32-two-sum":
+            a32, a64 = res[(0, r["theta"])], res[(1, r["theta"])]
+            d = (torch.linalg.norm(a32 - a64, dim=1) / torch.linalg.norm(a64, dim=1)).max()
+            r["max_rel_diff_vs_fp64_accum"] = float(d)
+    return {"workload": "the headline aggregate, one tree build per accumulator, walk shape "
+                        "of the headline; errors against the GPU direct sum", "rows": rows}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -338,6 +387,8 @@ def run_ours(args, rank, world, local_rank):
                            "speedup_of_tree": (n / (t_step * 1e-3)) / (n / (t_dir * 1e-3)),
                            "interactions_per_s": n * (n - 1) / (t_dir * 1e-3),
                            "flops_per_s": FLOP_POINT * n * (n - 1) / (t_dir * 1e-3)}
+        if not args.no_sweep:
+            extra["theta_sweep"] = theta_sweep_leg(args, g, ctx, P, M, accd, p, flush, stream)
 
     # rooflines: the walk is FP32-ALU bound (no dense contraction, no tensor cores)
     sm_mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0

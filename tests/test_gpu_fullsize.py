@@ -5,7 +5,8 @@ by one.
   * clumpy aggregate, 1,048,576 bodies (the headline workload), theta 0.5, quadrupole,
     leaf 16: root cube, keys, order, topology, node mass and COM bit-exact against the
     oracle's tree of all bodies; forces and decision counts of 2048 seeded bodies against
-    the oracle's walk for them; the direct sum of 512 seeded bodies against the oracle's;
+    the oracle's walk for them (512 bodies at theta 0.3, 0.7, 0.9 and with the FP64
+    accumulator); the direct sum of 512 seeded bodies against the oracle's;
   * ensemble of 256 clouds (4.4 M bodies): six clouds, each against an oracle tree of
     that cloud alone, on up to 512 seeded bodies per cloud;
   * rubble pile, 100,000 bodies: one leapfrog step against the oracle's, and 100 steps
@@ -79,6 +80,37 @@ def test_headline_forces_sampled(gpu, head):
     rel, scale = force_errors(a_timed[idx], ref, absum)
     assert scale.max() <= 1e-6, scale.max()
     assert np.quantile(rel, 0.99) <= 1e-5, np.quantile(rel, 0.99)
+
+
+@pytest.fixture(scope="module")
+def head_oracle(head):
+    pos, m = head
+    return oracle.Tree(pos, m, leaf_max=16, order=2)
+
+
+@pytest.mark.parametrize("theta,accum", [(0.3, 0), (0.7, 0), (0.9, 0), (0.5, 1)])
+def test_headline_theta_sweep_sampled(gpu, head, head_oracle, theta, accum):
+    # the other opening angles of the sweep, and the FP64 accumulator: decision counts of
+    # 512 seeded bodies exact, forces within the parity tolerance
+    pos, m = head
+    ctx = gpu.Context(0)
+    P = torch.tensor(pos, device="cuda")
+    M = torch.tensor(m, device="cuda")
+    acc = torch.empty_like(P)
+    cnt = torch.empty((len(pos), 3), dtype=torch.int32, device="cuda")
+    gpu.gravity_tree_build(ctx, P, M, gpu.params(order=2, leaf_max=16, accum=accum))
+    gpu.gravity_forces(ctx, theta, 1e-3, acc)
+    a_timed = acc.cpu().numpy()
+    gpu.gravity_forces_counted(ctx, theta, 1e-3, acc, cnt)
+    gpu.gravity_sync(ctx)
+    assert np.array_equal(acc.cpu().numpy(), a_timed)
+    idx = inputs.subset(len(pos), 512, seed=int(100 * theta) + accum)
+    ref, absum, ocnt = head_oracle.forces(theta, 1e-3, targets=idx)
+    c = cnt.cpu().numpy()[idx]
+    assert np.array_equal(c[:, 0], ocnt[:, 1]) and np.array_equal(c[:, 1], ocnt[:, 2])
+    assert np.array_equal(c[:, 2], ocnt[:, 0])
+    _, scale = force_errors(a_timed[idx], ref, absum)
+    assert scale.max() <= 1e-6, scale.max()
 
 
 def test_headline_direct_sampled(gpu, head):
