@@ -4,8 +4,9 @@
 // neighbouring threads traverse similar sub-trees.  Here a warp owns 32 bodies
 // that are consecutive in Morton order and walks ONE shared stack for all of them,
 // while every decision stays per body:
-//   * stack entries are ranges of sibling nodes (children are contiguous) or of
-//     bucket bodies, each with the 32-bit mask of lanes that still need them;
+//   * stack entries are ranges of sibling nodes (children are contiguous), each with
+//     the 32-bit mask of lanes that still need them; the bodies of an opened leaf go
+//     straight to the body-term list instead;
 //   * up to 32 stacked items are taken at once, one per lane, and classified
 //     against the bounding box of the warp's bodies: "accepted by every lane",
 //     "opened by every lane" or "mixed";
@@ -59,7 +60,6 @@ inline WalkShape walk_shape(int cfg) {
   const int fl[3] = {16, 12, 8};
   return WalkShape{fl[cfg % 3], (cfg / 3) % 3, cfg / 9};
 }
-constexpr uint32_t kKindBody = 0x80000000u;
 constexpr uint32_t kFirstMask = 0x01FFFFFFu;   // 25-bit first index
 constexpr int kCntShift = 25;                  // 6-bit (count - 1)
 
@@ -76,8 +76,7 @@ enum { kStatBatches, kStatItems, kStatMixed, kStatFp64, kStatMono, kStatQuad, kS
        kStatMixedUnanimous, kStatPointLane, kStatCount = 16 };
 
 struct WarpSmem {
-  uint32_t st_a[kSmemStack];      // first | (count-1) << 25 | kind
-  uint32_t st_m[kSmemStack];      // lane mask
+  uint2 st[kSmemStack];           // (first | (count-1) << 25, lane mask)
   float4 la[kListCap];            // point list: (x_hi, y_hi, z_hi, m)
   float4 lb[kListCap];            //             (x_lo, y_lo, z_lo, lane mask bits)
   float4 fa[kListCap];            // far list:   (c_rel xyz, m)
@@ -85,6 +84,7 @@ struct WarpSmem {
   int32_t ltag[kListCap];         // counting / VJP: -(node+1) node term, else sorted body index
   float4 org_h, org_l;            // the warp origin (lane 0's body), hi and lo parts
   int32_t bitem[32];              // node id of each lane's item (mixed nodes' FP64 decisions)
+  int4 lfx[32];                   // opened leaves of a batch: first body, bodies, lane mask
 };
 
 // Vector-Jacobian product (order 0): far-list sources and the lane-to-source
@@ -131,7 +131,7 @@ struct WalkArgs {
   int nqueues;
   int flush_at;
   int stack_cap;                  // stack entries allowed (<= kStackCap)
-  uint2 *gstack;                  // [persistent warps][kGlobStack] (first|cnt|kind, mask)
+  uint2 *gstack;                  // [persistent warps][kGlobStack] (first|cnt, mask)
   const int32_t *task_begin;      // several clouds: per task first body, cloud end, cloud id
   const int32_t *task_end;
   const int32_t *task_seg;
@@ -382,18 +382,19 @@ __device__ __forceinline__ void split_costs(const float4 *m4, int comp, int cnt,
 // Stack slot access: [0, kSmemStack) in shared memory, the rest in the warp's
 // global overflow area.
 struct Stack {
-  uint32_t *sa, *sm;
-  uint2 *g;
+  uint2 *s, *g;
   __device__ __forceinline__ void get(int i, uint32_t &a, uint32_t &m) const {
-    if (i < kSmemStack) { a = sa[i]; m = sm[i]; }
-    else { uint2 v = g[i - kSmemStack]; a = v.x; m = v.y; }
+    uint2 v;
+    if (i < kSmemStack) v = s[i];
+    else v = g[i - kSmemStack];
+    a = v.x; m = v.y;
   }
   __device__ __forceinline__ void set(int i, uint32_t a, uint32_t m) const {
-    if (i < kSmemStack) { sa[i] = a; sm[i] = m; }
+    if (i < kSmemStack) s[i] = make_uint2(a, m);
     else g[i - kSmemStack] = make_uint2(a, m);
   }
   __device__ __forceinline__ void set_a(int i, uint32_t a) const {
-    if (i < kSmemStack) sa[i] = a;
+    if (i < kSmemStack) s[i].x = a;
     else g[i - kSmemStack].x = a;
   }
 };
@@ -414,7 +415,7 @@ k_walk(WalkArgs A) {
   const int wib = threadIdx.x >> 5;
   Smem &S = reinterpret_cast<Smem *>(smem_raw)[wib];
   WarpSmem &M = *reinterpret_cast<WarpSmem *>(&S);
-  const Stack st{M.st_a, M.st_m, A.gstack + (size_t)(blockIdx.x * kWalkWarps + wib) * kGlobStack};
+  const Stack st{M.st, A.gstack + (size_t)(blockIdx.x * kWalkWarps + wib) * kGlobStack};
 
   const int n = A.n;
   const int nn = *A.nnodes;
@@ -504,8 +505,20 @@ k_walk(WalkArgs A) {
       bmaxz = fmaxf(bmaxz, __shfl_xor_sync(0xffffffffu, bmaxz, o));
       rw2 = fmaxf(rw2, __shfl_xor_sync(0xffffffffu, rw2, o));
     }
-    const float bR = fmaxf(fmaxf(fmaxf(fabsf(bminx), fabsf(bmaxx)), fmaxf(fabsf(bminy), fabsf(bmaxy))),
-                           fmaxf(fabsf(bminz), fabsf(bmaxz)));
+    {
+      // widen the box by del = 2^-19 (R + C), R = the bodies' largest |coordinate| and C a
+      // bound of every node COM's (the root cube's largest |corner coordinate|): a bound on
+      // the hi/lo truncation and rounding of the box distances below
+      const double *gr = A.geom + 8 * root;
+      const float C = (float)fmax(fmax(fmax(fabs(gr[0]), fabs(gr[0] + gr[3])),
+                                       fmax(fabs(gr[1]), fabs(gr[1] + gr[3]))),
+                                  fmax(fabs(gr[2]), fabs(gr[2] + gr[3])));
+      const float bR = fmaxf(fmaxf(fmaxf(fabsf(bminx), fabsf(bmaxx)), fmaxf(fabsf(bminy), fabsf(bmaxy))),
+                             fmaxf(fabsf(bminz), fabsf(bmaxz)));
+      const float del = (bR + C) * 1.9073486e-6f;
+      bminx -= del; bminy -= del; bminz -= del;
+      bmaxx += del; bmaxy += del; bmaxz += del;
+    }
     // a node with l^2 >= farl2 is at least R_w / 2 from every body that accepts it
     // (D > l / theta), which bounds the far-path error of d by 5.5 * 2^-23 |d|
     const float farl2 = 0.25f * theta2f * rw2 * 1.01f;
@@ -525,6 +538,24 @@ k_walk(WalkArgs A) {
     }
     __syncwarp();
 
+    // evaluates the point list into the accumulator and empties it
+    auto flush_pt = [&]() {
+      if (COUNT) {
+        w_mono += npt;
+        split_costs(M.lb, 3, npt, lane, w_split);
+        split_costs(M.lb, 3, npt, lane, w_psplit);
+      }
+      float px, py, pz;
+      if constexpr (VJP)
+        flush_vjp<false, EPS0>(S, npt, lane, xh, yh, zh, xl, yl, zl, xr, yr, zr, eps2, ux, uy, uz,
+                               gi, px, py, pz, A.g_body, A.g_node);
+      else
+        flush_point<EPS0, COUNT>(M, npt, lane, xh, yh, zh, xl, yl, zl, eps2, px, py, pz, gi,
+                                 c_m2p, c_p2p);
+      acc.add(acc64, px, py, pz);
+      npt = 0;
+      __syncwarp();
+    };
     for (int iter = 0; sp > 0; ++iter) {
       if (iter > A.max_iter) {                  // cannot happen on a well-formed tree
         if (lane == 0) latch_error(A.status, kErrTree);
@@ -549,7 +580,7 @@ k_walk(WalkArgs A) {
       __syncwarp();
       if (take > 0 && take < ecnt) {           // the one partially consumed entry stays
         st.set_a(ke, (((ea & kFirstMask) + take) & kFirstMask) |
-                         ((uint32_t)(ecnt - take - 1) << kCntShift) | (ea & kKindBody));
+                         ((uint32_t)(ecnt - take - 1) << kCntShift));
       }
       sp -= nfull;
       const unsigned starts = __reduce_or_sync(0xffffffffu, take > 0 ? (1u << excl) : 0u);
@@ -560,35 +591,27 @@ k_walk(WalkArgs A) {
       const uint32_t omask = __shfl_sync(0xffffffffu, em, owner);
       const bool have = lane < nitems;
       if (COUNT) { ++w_batches; w_items += nitems; }
-      const bool kbody = (oa & kKindBody) != 0;
       const int item = (int)(oa & kFirstMask) + (lane - stpos);
 
       // ---- load and classify (lane = item)
       float4 r0 = make_float4(0, 0, 0, 0), r1 = make_float4(0, 0, 0, 0);
       float4 q0 = make_float4(0, 0, 0, 0), q1 = make_float4(0, 0, 0, 0);
       int4 tp = make_int4(-1, 0, 0, 0);
-      bool single = false;                     // a point term (body or one-body leaf)
+      bool single = false;                     // a one-body leaf: a point term
       bool bad = false;
       if (have) {
-        if (kbody) {
-          bad = item >= n;
-          if (!bad) { r0 = A.bhi[item]; r1 = A.blo[item]; }
-          tp = make_int4(-1, 0, item, item + 1);
-          single = true;
-        } else {
-          bad = item >= nn;
-          if (!bad) {
-            tp = A.topo[item];
-            r0 = A.rec0[item];
-            r1 = A.rec1[item];
-            if constexpr (ORDER == 2) {        // in flight during classification
-              q0 = A.quadf[2 * item];
-              q1 = A.quadf[2 * item + 1];
-            }
-            single = r1.w < 0.f;               // one-body leaf: record holds the body itself
-            bad = (tp.x >= 0 && (tp.x <= 0 || tp.x + tp.y > nn)) || tp.z < 0 || tp.w > n ||
-                  tp.z >= tp.w;
+        bad = item >= nn;
+        if (!bad) {
+          tp = A.topo[item];
+          r0 = A.rec0[item];
+          r1 = A.rec1[item];
+          if constexpr (ORDER == 2) {          // in flight during classification
+            q0 = A.quadf[2 * item];
+            q1 = A.quadf[2 * item + 1];
           }
+          single = r1.w < 0.f;                 // the record holds the body itself
+          bad = (tp.x >= 0 && (tp.x <= 0 || tp.x + tp.y > nn)) || tp.z < 0 || tp.w > n ||
+                tp.z >= tp.w;
         }
       }
       if (__any_sync(0xffffffffu, bad)) {
@@ -604,15 +627,12 @@ k_walk(WalkArgs A) {
           accm = omask;
         } else {
           const float cx = r0.x, cy = r0.y, cz = r0.z, l2 = r1.w;
-          const float C = fmaxf(fabsf(cx), fmaxf(fabsf(cy), fabsf(cz)));
-          const float del = (bR + C) * 1.9073486e-6f;    // 2^-19 (R + C): bound on hi/lo + rounding
-          float gx = fmaxf(fmaxf(bminx - cx, cx - bmaxx), 0.f);
-          float gy = fmaxf(fmaxf(bminy - cy, cy - bmaxy), 0.f);
-          float gz = fmaxf(fmaxf(bminz - cz, cz - bmaxz), 0.f);
-          gx = fmaxf(gx - del, 0.f); gy = fmaxf(gy - del, 0.f); gz = fmaxf(gz - del, 0.f);
-          const float fx = fmaxf(fabsf(cx - bminx), fabsf(cx - bmaxx)) + del;
-          const float fy = fmaxf(fabsf(cy - bminy), fabsf(cy - bmaxy)) + del;
-          const float fz = fmaxf(fabsf(cz - bminz), fabsf(cz - bmaxz)) + del;
+          const float gx = fmaxf(fmaxf(bminx - cx, cx - bmaxx), 0.f);    // widened box
+          const float gy = fmaxf(fmaxf(bminy - cy, cy - bmaxy), 0.f);
+          const float gz = fmaxf(fmaxf(bminz - cz, cz - bmaxz), 0.f);
+          const float fx = fmaxf(fabsf(cx - bminx), fabsf(cx - bmaxx));
+          const float fy = fmaxf(fabsf(cy - bminy), fabsf(cy - bmaxy));
+          const float fz = fmaxf(fabsf(cz - bminz), fabsf(cz - bmaxz));
           const float dmin2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
           const float dmax2 = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
           const bool guard_any = A.mac_guard && tp.z < wend && tp.w > wbeg;
@@ -733,56 +753,64 @@ k_walk(WalkArgs A) {
         nnear += __popc(bq);
       }
 
-      // ---- push opened nodes (children range) or bucket bodies (chunks of <= 32)
-      int npush = 0;
-      if (openm != 0) npush = (tp.x >= 0) ? 1 : (tp.w - tp.z + 31) / 32;
-      int pincl, ptotal;
-      if (__all_sync(0xffffffffu, npush <= 1)) {
-        const unsigned pb = __ballot_sync(0xffffffffu, npush == 1);
-        pincl = __popc(pb & (0xffffffffu >> (31 - lane)));
-        ptotal = __popc(pb);
-      } else {
-        pincl = warp_incl_scan_i(npush, lane);
-        ptotal = __shfl_sync(0xffffffffu, pincl, 31);
-      }
+      // ---- push opened internal nodes (their children range)
+      const bool push = openm != 0 && tp.x >= 0;
+      const unsigned pb = __ballot_sync(0xffffffffu, push);
+      const int ptotal = __popc(pb);
       if (sp + ptotal > A.stack_cap) {
         if (lane == 0) latch_error(A.status, kErrStack);
         abort = true;
         break;
       }
-      if (npush > 0) {
-        int p = sp + pincl - npush;
-        if (tp.x >= 0) {
-          st.set(p, (uint32_t)tp.x | ((uint32_t)(tp.y - 1) << kCntShift), openm);
-        } else {
-          for (int b = tp.z; b < tp.w; b += 32, ++p) {
-            const int c = min(32, tp.w - b);
-            st.set(p, (uint32_t)b | ((uint32_t)(c - 1) << kCntShift) | kKindBody, openm);
-          }
-        }
-      }
+      if (push)
+        st.set(sp + __popc(pb & ((1u << lane) - 1u)),
+               (uint32_t)tp.x | ((uint32_t)(tp.y - 1) << kCntShift), openm);
       sp += ptotal;
       if (COUNT) w_maxsp = max(w_maxsp, sp);
-      __syncwarp();
 
-      // ---- evaluate full lists
-      if (npt >= A.flush_at) {
-        if (COUNT) {
-          w_mono += npt;
-          split_costs(M.lb, 3, npt, lane, w_split);
-          split_costs(M.lb, 3, npt, lane, w_psplit);
+      // ---- opened leaves: their bodies go straight to the point list as body terms of
+      // the opening lanes, packed 32 to a round (leaves compacted in shared memory first);
+      // the point list is evaluated when a round might not fit, and when full at the end
+      const bool open_leaf = openm != 0 && tp.x < 0;
+      const unsigned lm = __ballot_sync(0xffffffffu, open_leaf);
+      int4 lf = make_int4(0, 0, 0, 0);
+      int lincl = 0, ltot = 0;
+      if (lm) {
+        if (open_leaf) M.lfx[__popc(lm & ((1u << lane) - 1u))] = make_int4(tp.z, tp.w - tp.z, (int)openm, 0);
+        __syncwarp();
+        if (lane < __popc(lm)) lf = M.lfx[lane];
+        lincl = warp_incl_scan_i(lf.y, lane);
+        ltot = __shfl_sync(0xffffffffu, lincl, 31);
+      }
+      __syncwarp();
+      for (int base = 0;; base += 32) {
+        const bool more = base < ltot;
+        if (more ? npt > kListCap - 32 : npt >= A.flush_at) flush_pt();
+        if (!more) break;
+        // round [base, base + 32): the leaves overlapping it are consecutive, from the
+        // first one not ended before it; slot base + lane belongs to the last of them
+        // starting at or before the slot
+        const int lexcl = lincl - lf.y;
+        const bool in_round = lf.y > 0 && lexcl < base + 32 && lincl > base;
+        const unsigned starts = __reduce_or_sync(0xffffffffu, in_round ? 1u << max(lexcl - base, 0) : 0u);
+        const int first = __popc(__ballot_sync(0xffffffffu, lf.y > 0 && lincl <= base));
+        const int li = first + __popc(starts & (0xffffffffu >> (31 - lane))) - 1;
+        const int b0 = __shfl_sync(0xffffffffu, lf.x, li);
+        const int bx = __shfl_sync(0xffffffffu, lexcl, li);
+        const unsigned bm = (unsigned)__shfl_sync(0xffffffffu, lf.z, li);
+        const int take = min(32, ltot - base);
+        if (lane < take) {
+          const int body = b0 + (base + lane - bx);
+          const float4 h = A.bhi[body], l = A.blo[body];
+          M.la[npt + lane] = h;
+          M.lb[npt + lane] = make_float4(l.x, l.y, l.z, __uint_as_float(bm));
+          if (COUNT || VJP) M.ltag[npt + lane] = body;
         }
-        float px, py, pz;
-        if constexpr (VJP)
-          flush_vjp<false, EPS0>(S, npt, lane, xh, yh, zh, xl, yl, zl, xr, yr, zr, eps2, ux, uy, uz,
-                                 gi, px, py, pz, A.g_body, A.g_node);
-        else
-          flush_point<EPS0, COUNT>(M, npt, lane, xh, yh, zh, xl, yl, zl, eps2, px, py, pz, gi,
-                                   c_m2p, c_p2p);
-        acc.add(acc64, px, py, pz);
-        npt = 0;
+        npt += take;
         __syncwarp();
       }
+
+      // ---- evaluate the other full lists
       if (nfar >= A.flush_at) {
         if (COUNT) { w_quad += nfar; split_costs(M.fc, 2, nfar, lane, w_split); }
         float px, py, pz;
