@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="default walk shape, no autotuning")
     ap.add_argument("--ensemble-steps", type=int, default=50)
     ap.add_argument("--no-grad", action="store_true", help="skip the gradient (adjoint) leg")
+    ap.add_argument("--no-components", action="store_true",
+                    help="skip the aggregate-identification leg")
     ap.add_argument("--no-sweep", action="store_true",
                     help="skip the theta / accumulator sweep (runs with the direct-sum leg)")
     return ap.parse_args()
@@ -293,6 +295,35 @@ def theta_sweep_leg(args, g, ctx, P, M, accd, p, flush, stream):
                         "of the headline; errors against the GPU direct sum", "rows": rows}
 
 
+def components_leg(args, g, ctx, P, M, p, flush, stream):
+    """Aggregate identification (contact-graph components over the gravity tree) on the
+    headline workload: contact = distance <= dmax; the tree of the headline is reused."""
+    import torch
+    n = P.shape[0]
+    g.gravity_tree_build(ctx, P, M, p)
+    label = torch.empty(n, dtype=torch.int32, device=P.device)
+    counts = torch.empty(2, dtype=torch.int64, device=P.device)
+    rows = []
+    for dmax in (5e-4, 1e-3, 2e-3):
+        g.gravity_components(ctx, label, dmax=dmax, counts=counts)      # warm-up
+        ts = []
+        for k in range(5):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.gravity_components(ctx, label, dmax=dmax, counts=counts)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        g.gravity_sync(ctx)
+        c = counts.cpu().tolist()
+        t = float(np.median(ts))
+        rows.append({"dmax": dmax, "ms": t, "bodies_per_s": n / (t * 1e-3),
+                     "components": int(c[0]), "aggregates": int(c[1])})
+    return {"workload": "the headline aggregate; contact = |x_i - x_j| <= dmax; tree reused "
+                        "(search + union-find + labels, 4 kernels)", "rows": rows}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -389,6 +420,9 @@ def run_ours(args, rank, world, local_rank):
                            "flops_per_s": FLOP_POINT * n * (n - 1) / (t_dir * 1e-3)}
         if not args.no_sweep:
             extra["theta_sweep"] = theta_sweep_leg(args, g, ctx, P, M, accd, p, flush, stream)
+
+    if not args.no_components:
+        extra["components"] = components_leg(args, g, ctx, P, M, p, flush, stream)
 
     # rooflines: the walk is FP32-ALU bound (no dense contraction, no tensor cores)
     sm_mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0

@@ -38,7 +38,8 @@ extern "C" {
 enum gravity_status {
   GRAVITY_OK = 0,
   GRAVITY_E_ARG = -1,        /* invalid argument (n < 0, theta < 0, eps < 0, null pointer, ...) */
-  GRAVITY_E_NONFINITE = -2,  /* a position coordinate is NaN or infinite (latched) */
+  GRAVITY_E_NONFINITE = -2,  /* a position coordinate is NaN or infinite, or a contact radius
+                                is negative or not finite (latched) */
   GRAVITY_E_NOMEM = -3,      /* device allocation failed */
   GRAVITY_E_CUDA = -4,       /* a CUDA runtime call failed */
   GRAVITY_E_TIMEOUT = -5,    /* a bounded device-side wait ran out (latched) */
@@ -235,6 +236,34 @@ int gravity_direct_noalloc(int64_t n, const double *pos, const double *mass, dou
  * nothing.  n = 0 writes zeros. */
 int gravity_diagnostics(gravity_ctx *ctx, int64_t n, const double *pos, const double *vel,
                         const double *mass, double eps, double G, double *out);
+
+/* Aggregate identification (Sec. 2, "Post-processing: aggregate identification"): the
+ * connected components of the contact graph whose vertices are the bodies of the current
+ * tree.  The paper takes the edges from its collision solver's contact container; here two
+ * bodies i != j of the same cloud are in contact when |x_i - x_j|^2 <= t_ij^2, in FP64 with
+ * d = x_j - x_i and |d|^2 = (dx^2 + dy^2) + dz^2, each operation rounded once (every edge is
+ * decided as a plain pairwise test decides it), t_ij = radius[i] + radius[j] (touching
+ * bounding spheres) when radius is given, else t_ij = dmax.  The positions are those of the
+ * last gravity_tree_build / gravity_batch_tree_build (the tree serves as the neighbour
+ * search).
+ *   radius  device, (n) doubles in caller order, each >= 0 and finite, or NULL
+ *   dmax    uniform threshold (>= 0, finite), used when radius is NULL
+ *   label   device, (n) int32 out, caller order: the smallest caller index of the body's
+ *           component (canonical: independent of the order of the unions)
+ *   counts  device, two int64 out: the number of components, and the number of
+ *           aggregates (components of more than one body, the paper's count); or NULL
+ * Written asynchronously on the context's stream.  Errors: GRAVITY_E_NOTREE without a
+ * tree, GRAVITY_E_ARG for a bad dmax (radius NULL) or a NULL label, GRAVITY_E_NOMEM;
+ * a negative or non-finite radius is latched (read by gravity_sync) and counts as 0. */
+int gravity_components(gravity_ctx *ctx, const double *radius, double dmax, int32_t *label,
+                       int64_t *counts);
+
+/* Largest gravity time step of Eq. (dt_g) (Sec. 4.1): *dt_g = T_g / 2 = 1 / (2 sqrt(G rho)),
+ * rho the material density of the bodies (host arithmetic, no device work).  A caller that
+ * steps contacts with dt_c evaluates gravity every ceil(dt_g / dt_c) contact steps, as the
+ * paper's two-time-step scheme does.  Errors: GRAVITY_E_ARG unless G > 0 and rho > 0 are
+ * finite and dt_g is non-NULL. */
+int gravity_dt_g(double G, double rho, double *dt_g);
 
 /* nsteps steps of a symplectic integrator (Sec. 2.3) with the tree rebuilt every
  * step (Sec. 2.1).  p->scheme 0 (kick-drift-kick leapfrog):

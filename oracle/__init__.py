@@ -82,6 +82,8 @@ def _load():
             lib.orc_leapfrog.restype = I
             lib.orc_diagnostics.argtypes = [I64, P, P, P, D, D, P]
             lib.orc_diagnostics.restype = None
+            lib.orc_components.argtypes = [I64, P, P, D, P, P]
+            lib.orc_components.restype = None
             _lib = lib
     return _lib
 
@@ -278,6 +280,19 @@ def diagnostics(pos, vel, mass, eps, G=1.0):
     _load().orc_diagnostics(len(pos), _ptr(pos), _ptr(vel), _ptr(mass), float(eps), float(G),
                             _ptr(out))
     return float(out[0]), out[1:4].copy(), out[4:7].copy()
+
+
+def components(pos, radius=None, dmax=0.0):
+    """Aggregate identification (Sec. 2): contact-graph components by depth-first search.
+    Contact: |x_i - x_j| <= r_i + r_j (radius given) or <= dmax.  Returns (label, counts):
+    label[i] = smallest index of i's component; counts = (components, components of > 1)."""
+    pos = _f64(pos, 3).reshape(-1, 3)
+    n = len(pos)
+    r = None if radius is None else _f64(radius).reshape(-1)
+    label = np.zeros(n, np.int32)
+    counts = np.zeros(2, np.int64)
+    _load().orc_components(n, _ptr(pos), _ptr(r), float(dmax), _ptr(label), _ptr(counts))
+    return label, (int(counts[0]), int(counts[1]))
 
 
 def leapfrog_grad(pos0, vel0, mass, xbar, vbar, dt, nsteps, *, theta=0.5, eps=1e-3, G=1.0,

@@ -674,4 +674,49 @@ void orc_diagnostics(int64_t n, const double *pos, const double *vel, const doub
   for (int a = 0; a < 3; ++a) { out[1 + a] = P[a]; out[4 + a] = L[a]; }
 }
 
+// Aggregate identification (Sec. 2, "Post-processing: aggregate identification"):
+// bodies are the vertices of a graph, contacts its edges, aggregates its connected
+// components of more than one body, found by depth-first search.  Our reading of
+// "contact" (the paper takes it from its collision solver): bodies i != j touch when
+// |x_i - x_j|^2 <= t_ij^2 with t_ij = r_i + r_j (radii given) or t_ij = dmax, and
+// |d|^2 = (d0*d0 + d1*d1) + d2*d2, d = x_j - x_i.  The edges are every such pair
+// (brute force); the search starts from each unvisited body in index order, so a
+// component's first body is its smallest index, which is the label.
+// counts[0] = components, counts[1] = components of more than one body.
+void orc_components(int64_t n, const double *pos, const double *radius, double dmax,
+                    int32_t *label, int64_t *counts) {
+  std::vector<std::vector<int64_t>> adj(n);
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t j = i + 1; j < n; ++j) {
+      double d0 = pos[3 * j] - pos[3 * i], d1 = pos[3 * j + 1] - pos[3 * i + 1],
+             d2 = pos[3 * j + 2] - pos[3 * i + 2];
+      double r2 = (d0 * d0 + d1 * d1) + d2 * d2;
+      double t = radius ? radius[i] + radius[j] : dmax;
+      if (r2 <= t * t) {
+        adj[i].push_back(j);
+        adj[j].push_back(i);
+      }
+    }
+  }
+  std::vector<char> seen(n, 0);
+  std::vector<int64_t> stack;
+  counts[0] = counts[1] = 0;
+  for (int64_t s = 0; s < n; ++s) {
+    if (seen[s]) continue;
+    int64_t size = 0;
+    seen[s] = 1;
+    stack.push_back(s);
+    while (!stack.empty()) {
+      int64_t v = stack.back();
+      stack.pop_back();
+      label[v] = (int32_t)s;
+      ++size;
+      for (int64_t w : adj[v])
+        if (!seen[w]) { seen[w] = 1; stack.push_back(w); }
+    }
+    ++counts[0];
+    if (size > 1) ++counts[1];
+  }
+}
+
 }  // extern "C"

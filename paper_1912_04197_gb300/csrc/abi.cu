@@ -301,6 +301,7 @@ void free_all(Ctx *c) {
   ctx_release(c, c->diag_buf); c->diag_cap = 0;
   ctx_release(c, c->h2d_pos); ctx_release(c, c->h2d_mass); ctx_release(c, c->h2d_acc);
   c->h2d_cap = 0;
+  ctx_release(c, c->comp_r); ctx_release(c, c->comp_i); c->comp_cap = 0;
   if (c->graph.exec) cudaGraphExecDestroy(c->graph.exec);
   c->graph = StepGraph{};
   ctx_release(c, c->d_status);
@@ -459,6 +460,30 @@ int gravity_forces_vjp(gravity_ctx *h, double theta, double eps, const double *l
   int rc = grav::set_device(c);
   if (rc) return rc;
   return grav::walk_vjp(&c, theta, eps, lambda, grad_pos);
+}
+
+int gravity_components(gravity_ctx *h, const double *radius, double dmax, int32_t *label,
+                       int64_t *counts) {
+  grav::Range range_("gravity_components");
+  if (!h) return GRAVITY_E_ARG;
+  if (!radius && (!(dmax >= 0.0) || !std::isfinite(dmax))) return GRAVITY_E_ARG;
+  Ctx &c = h->c;
+  if (!c.have_tree) return GRAVITY_E_NOTREE;
+  if (c.n > 0 && !label) return GRAVITY_E_ARG;
+  int rc = grav::set_device(c);
+  if (rc) return rc;
+  if (c.n == 0) {
+    if (counts) GRAV_CUDA_TRY(cudaMemsetAsync(counts, 0, 2 * sizeof(int64_t), c.stream));
+    return GRAVITY_OK;
+  }
+  return grav::components(&c, radius, dmax, label, counts);
+}
+
+int gravity_dt_g(double G, double rho, double *dt_g) {
+  if (!dt_g || !(G > 0.0) || !(rho > 0.0) || !std::isfinite(G) || !std::isfinite(rho))
+    return GRAVITY_E_ARG;
+  *dt_g = 0.5 / std::sqrt(G * rho);
+  return GRAVITY_OK;
 }
 
 int gravity_direct(gravity_ctx *h, int64_t n, const double *pos, const double *mass, double eps,
@@ -794,7 +819,7 @@ const char *gravity_strerror(int code) {
   switch (code) {
     case GRAVITY_OK: return "ok";
     case GRAVITY_E_ARG: return "invalid argument";
-    case GRAVITY_E_NONFINITE: return "non-finite position coordinate";
+    case GRAVITY_E_NONFINITE: return "non-finite position coordinate or invalid radius";
     case GRAVITY_E_NOMEM: return "device allocation failed";
     case GRAVITY_E_CUDA: return "CUDA runtime error";
     case GRAVITY_E_TIMEOUT: return "bounded device wait ran out";

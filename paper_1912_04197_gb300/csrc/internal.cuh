@@ -135,6 +135,10 @@ struct Ctx {
   // host-buffer entry point staging
   double *h2d_pos = nullptr, *h2d_mass = nullptr, *h2d_acc = nullptr;
   int64_t h2d_cap = 0;
+  // contact components: sorted radii + 3 words; parent, component minimum, root, size
+  double *comp_r = nullptr;
+  int *comp_i = nullptr;
+  int64_t comp_cap = 0;
 };
 
 // ---- launchers (tree_build.cu)
@@ -162,6 +166,8 @@ int direct_forces(Ctx *c, int64_t n, const double *pos, const double *mass, doub
                   double G, double *acc);
 int diagnostics(Ctx *c, int64_t n, const double *pos, const double *vel, const double *mass,
                 double eps, double G, double *out_dev);
+// ---- launchers (contact.cu)
+int components(Ctx *c, const double *radius, double dmax, int32_t *label, int64_t *counts);
 // ---- launchers (integrate.cu)
 int launch_kick_drift(Ctx *c, int64_t n, double *pos, double *vel, const double *acc,
                       double h_kick, double dt);

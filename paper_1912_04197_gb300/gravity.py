@@ -69,6 +69,8 @@ def _load() -> ctypes.CDLL:
         "gravity_forces_vjp": (I, [P, D, D, P, P]),
         "gravity_direct": (I, [P, I64, P, P, D, D, P]),
         "gravity_diagnostics": (I, [P, I64, P, P, P, D, D, P]),
+        "gravity_components": (I, [P, P, D, P, P]),
+        "gravity_dt_g": (I, [D, D, ctypes.POINTER(D)]),
         "leapfrog_step": (I, [P, I64, P, P, P, P, D, I, D, D, PP]),
         "leapfrog_adjoint": (I, [P, I64, P, P, P, D, I, D, D, PP, I, P, P]),
         "gravity_forces_host": (I, [P, I64, P, P, D, D, PP, P]),
@@ -114,8 +116,8 @@ def params(**kw) -> gravity_params:
 def _dev(t: torch.Tensor, name: str, shape_last=None) -> ctypes.c_void_p:
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError(f"{name} must be a CUDA tensor")
-    if t.dtype not in (torch.float64, torch.int32) or not t.is_contiguous():
-        raise TypeError(f"{name} must be contiguous float64/int32")
+    if t.dtype not in (torch.float64, torch.int32, torch.int64) or not t.is_contiguous():
+        raise TypeError(f"{name} must be contiguous float64/int32/int64")
     if shape_last is not None and t.numel() and t.shape[-1] != shape_last:
         raise ValueError(f"{name} must have trailing dimension {shape_last}")
     return ctypes.c_void_p(t.data_ptr())
@@ -273,6 +275,30 @@ def gravity_diagnostics(ctx: Context, pos, vel, mass, eps: float, G: float,
                                     _dev(vel, "vel", 3), _dev(mass, "mass"), float(eps), float(G),
                                     _dev(out, "out")), "gravity_diagnostics")
     return out
+
+
+def gravity_components(ctx: Context, label: torch.Tensor, radius: torch.Tensor = None,
+                       dmax: float = 0.0, counts: torch.Tensor = None):
+    """Contact-graph components of the current tree's bodies: label (device int32, n) gets
+    the smallest caller index of each body's component; counts (device int64, 2), if
+    given, the number of components and of aggregates (components of > 1 body).  Contact:
+    |x_i - x_j| <= radius_i + radius_j, or <= dmax without radii."""
+    if counts is not None and (counts.dtype != torch.int64 or counts.numel() < 2):
+        raise TypeError("counts must be an int64 tensor of 2 elements")
+    if label.dtype != torch.int32:
+        raise TypeError("label must be int32")
+    _check(_lib.gravity_components(ctx.handle, None if radius is None else _dev(radius, "radius"),
+                                   float(dmax), _dev(label, "label"),
+                                   None if counts is None else _dev(counts, "counts")),
+           "gravity_components")
+    return label, counts
+
+
+def gravity_dt_g(G: float, rho: float) -> float:
+    """Largest gravity time step of Eq. (dt_g): 1 / (2 sqrt(G rho)), rho the material density."""
+    out = ctypes.c_double()
+    _check(_lib.gravity_dt_g(float(G), float(rho), ctypes.byref(out)), "gravity_dt_g")
+    return out.value
 
 
 def gravity_direct_noalloc(pos, mass, eps: float, G: float, acc) -> torch.Tensor:
