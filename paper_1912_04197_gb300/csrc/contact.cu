@@ -10,8 +10,9 @@
 // rounding, so each edge is decided exactly as a plain pairwise test decides it.
 // The candidate pairs come from the octree already built for gravity: a node can
 // hold a partner of body i only if |x_i - COM| <= (r_i + r_max) + sqrt(3) l (every
-// body of a node lies in its cube of side l, and so does the COM); the test is
-// made with a relative margin, so it never prunes a true partner.  Each thread
+// body of a node lies in its cube of side l, and so does the COM); the test runs in
+// FP32 on the hi parts of the coordinates with margins that cover their truncation
+// and rounding, so it never prunes a true partner.  Each thread
 // walks the tree for one body (sorted order) and joins it to every partner j > i
 // with a lock-free union-find: roots only ever point to smaller indices (a root is
 // hooked under the smaller of two roots by compare-and-swap; path halving keeps the
@@ -82,7 +83,8 @@ __global__ void k_comp_init(const double *__restrict__ radius, const uint32_t *_
 struct CompArgs {
   const int4 *topo;
   const int32_t *ndepth;
-  const double *ncom;
+  const float4 *rec0;                // (COM hi xyz, m)
+  const float4 *bhi;                 // (x hi xyz, m), sorted
   const double *geom;
   const double *pos_s;
   const double *r_s;                 // nullptr: uniform dmax
@@ -100,10 +102,18 @@ __global__ void __launch_bounds__(kCompThreads) k_comp_search(CompArgs A) {
   if (i >= A.n) return;
   const int nn = *A.nnodes;
   const int root = A.seg_sorted ? A.seg_sorted[i] : 0;
-  const double side = A.geom[8 * root + 3];
+  const double *gr = A.geom + 8 * root;
   const double xi = A.pos_s[3 * i], yi = A.pos_s[3 * i + 1], zi = A.pos_s[3 * i + 2];
   const double ri = A.r_s ? A.r_s[i] : 0.0;
   const double reach = A.r_s ? __dadd_rn(ri, __longlong_as_double((long long)*A.rmax_bits)) : A.dmax;
+  // FP32 pruning: hi parts differ from the FP64 values by <= 2^-24 of the largest |corner
+  // coordinate| C of the root cube, FP32 differences and squares add a few 2^-24 relative;
+  // the margin 2^-18 (reach + sqrt(3) l) + 2^-18 C covers both with room
+  const float C = (float)fmax(fmax(fmax(fabs(gr[0]), fabs(gr[0] + gr[3])), fmax(fabs(gr[1]), fabs(gr[1] + gr[3]))),
+                              fmax(fabs(gr[2]), fabs(gr[2] + gr[3])));
+  const float sidef = (float)gr[3] * (1.0f + 3.814697265625e-6f);   // side, rounded up
+  const float reachf = (float)reach * (1.0f + 3.814697265625e-6f) + 3.814697265625e-6f * C;
+  const float4 bh = A.bhi[i];
   int stack[kCompStack];
   int sp = 0;
   stack[sp++] = root;
@@ -111,11 +121,11 @@ __global__ void __launch_bounds__(kCompThreads) k_comp_search(CompArgs A) {
     const int node = stack[--sp];
     if (node < 0 || node >= nn) { latch_error(A.status, kErrTree); return; }
     const int4 tp = A.topo[node];
-    const double dx = A.ncom[3 * node] - xi, dy = A.ncom[3 * node + 1] - yi,
-                 dz = A.ncom[3 * node + 2] - zi;
-    const double D2 = dx * dx + dy * dy + dz * dz;
-    const double l = side * pow2_neg(A.ndepth[node]);
-    const double S = (reach + 1.7320508075688773 * l) * (1.0 + 1e-9) + 1e-300;
+    const float4 c = A.rec0[node];
+    const float dx = c.x - bh.x, dy = c.y - bh.y, dz = c.z - bh.z;
+    const float D2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float l = sidef * __int_as_float((127 - A.ndepth[node]) << 23);   // side * 2^-depth
+    const float S = fmaf(1.7320509f, l, reachf) * (1.0f + 3.814697265625e-6f);
     if (D2 > S * S) continue;                   // no body of the node is in reach
     if (tp.x >= 0) {                            // internal: visit the children
       if (tp.x + tp.y > nn || sp + tp.y > kCompStack) { latch_error(A.status, kErrStack); return; }
@@ -194,7 +204,8 @@ int components(Ctx *c, const double *radius, double dmax, int32_t *label, int64_
   k_comp_init<<<blocks, kCompThreads, 0, c->stream>>>(radius, c->t.idx, n, c->comp_r, parent,
                                                       cmin, sc, c->d_status);
   CompArgs A{};
-  A.topo = c->t.topo; A.ndepth = c->t.ndepth; A.ncom = c->t.ncom; A.geom = c->t.geom;
+  A.topo = c->t.topo; A.ndepth = c->t.ndepth; A.rec0 = c->t.nrec0; A.bhi = c->t.body_hi;
+  A.geom = c->t.geom;
   A.pos_s = c->t.pos_s; A.r_s = radius ? c->comp_r : nullptr; A.rmax_bits = sc;
   A.seg_sorted = c->seg.nseg > 1 ? c->seg.seg_sorted : nullptr;
   A.nnodes = c->t.nnodes; A.dmax = dmax; A.n = n; A.parent = parent; A.status = c->d_status;
