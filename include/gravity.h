@@ -43,7 +43,8 @@ enum gravity_status {
   GRAVITY_E_NOMEM = -3,      /* device allocation failed */
   GRAVITY_E_CUDA = -4,       /* a CUDA runtime call failed */
   GRAVITY_E_TIMEOUT = -5,    /* a bounded device-side wait ran out (latched) */
-  GRAVITY_E_INTERNAL = -6,   /* walk stack exhausted or inconsistent tree (latched) */
+  GRAVITY_E_INTERNAL = -6,   /* walk or contact-search stack exhausted, or an inconsistent
+                                tree (latched) */
   GRAVITY_E_NOTREE = -7      /* gravity_forces called before gravity_tree_build */
 };
 
@@ -302,7 +303,7 @@ int gravity_sync(gravity_ctx *ctx);
  *   GRAVITY_DBG_MASS      nnodes double
  *   GRAVITY_DBG_COM       nnodes x 3 double
  *   GRAVITY_DBG_QUAD      nnodes x 6 double (xx, yy, zz, xy, xz, yz)
- *   GRAVITY_DBG_WALKSTATS 16 uint64 from the last gravity_forces_counted: batches, items,
+ *   GRAVITY_DBG_WALKSTATS 16 uint64 from the last gravity_forces_counted: batches, node items,
  *                         mixed nodes, FP64 decisions, point-list entries, quadrupole-list
  *                         entries, deepest stack, terms evaluated by active lanes, lockstep
  *                         iterations of lists split by 16 / 8 / 1 lanes, full-mask entries,
