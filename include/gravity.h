@@ -328,8 +328,13 @@ int gravity_debug_export(gravity_ctx *ctx, int what, void *host_dst, size_t byte
 /* Settings for failure testing.  GRAVITY_DBGSET_STACK_CAP: largest number of walk stack
  * entries a warp may hold (1 .. the built-in capacity; 0 restores the full capacity); a
  * walk that needs more latches GRAVITY_E_INTERNAL (reported by gravity_sync) instead of
- * growing, as an exhausted stack does.  GRAVITY_E_ARG for an unknown item or value. */
-enum gravity_debug_setting { GRAVITY_DBGSET_STACK_CAP = 1 };
+ * growing, as an exhausted stack does.  GRAVITY_DBGSET_SORT_STALL: value k in 1 .. 2^22
+ * makes the first tile of every radix-sort pass withhold its published digit counts and
+ * gives each tile's look-back wait a budget of k polls, so the next tile's wait runs out
+ * and GRAVITY_E_TIMEOUT is latched (the order of that build is then wrong, every index
+ * still in range, nothing faults); 0 restores normal sorting.  GRAVITY_E_ARG for an
+ * unknown item or value. */
+enum gravity_debug_setting { GRAVITY_DBGSET_STACK_CAP = 1, GRAVITY_DBGSET_SORT_STALL = 2 };
 int gravity_debug_set(gravity_ctx *ctx, int what, int64_t value);
 
 /* Number of kernels this context has enqueued since it was created (host-side

@@ -393,6 +393,10 @@ int gravity_debug_set(gravity_ctx *h, int what, int64_t value) {
       if (value < 0 || value > grav::walk_stack_capacity()) return GRAVITY_E_ARG;
       h->c.stack_cap = (int)value;
       return GRAVITY_OK;
+    case GRAVITY_DBGSET_SORT_STALL:
+      if (value < 0 || value > (1 << 22)) return GRAVITY_E_ARG;
+      h->c.sort_stall = (int)value;
+      return GRAVITY_OK;
     default:
       return GRAVITY_E_ARG;
   }

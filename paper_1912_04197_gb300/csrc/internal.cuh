@@ -56,7 +56,7 @@ struct Tree {
   double *nquad = nullptr;                      // (k,6) second moments T about the COM
   float4 *nrec0 = nullptr;                      // (com_hi xyz, m)
   float4 *nrec1 = nullptr;                      // (com_lo xyz, l^2)
-  float4 *nquadf = nullptr;                     // 2 per node: (xx,yy,zz,xy), (xz,yz,0,0)
+  float4 *nquadf = nullptr;                     // 2 per node, of -Q: (xx,yy,zz,xy), (xz,yz,0,0)
 };
 
 // Independent clouds (segments) handled in one build and one walk launch: bodies
@@ -94,6 +94,7 @@ struct Ctx {
   gravity_free_fn user_free = nullptr;
   void *alloc_user = nullptr;
   int stack_cap = 0;           // walk stack entries allowed (0 = all); failure testing
+  int sort_stall = 0;          // > 0: sort passes withhold tile 0, look-back budget (testing)
   cudaStream_t stream = nullptr;
   int num_sms = 0;
   int64_t cap = 0;             // body capacity of the buffers

@@ -281,9 +281,14 @@ int exclusive_scan(Ctx *c, uint32_t *data, int64_t n, uint32_t *total_out) {
 //     the digit + earlier warps' count in this tile + rank within the warp.
 // Digit of element i in a pass: 8 bits of the Morton key, or, for the passes that
 // order clouds, 8 bits of the cloud id of the element's caller index.
+// If a look-back wait runs out (kErrTimeout is latched), that tile's destinations are
+// wrong and some output slots keep older contents.  Both value buffers start the sort
+// holding indices below n (the identity), and every pass writes only values read from
+// its input, so the permutation still holds indices below n: the kernels that index
+// with it stay in bounds and the caller gets GRAVITY_E_TIMEOUT from gravity_sync.
 constexpr int kRsMaxPasses = 10;                 // 8 key passes + up to 2 cloud-id passes
 constexpr uint32_t kRsFlagAgg = 1u << 30, kRsFlagPre = 2u << 30, kRsValue = (1u << 30) - 1;
-constexpr int kRsSpin = 1 << 22;
+constexpr int kRsSpin = 1 << 22;                 // polls allowed per tile (look-back budget)
 constexpr int kRsLook = 8;                       // predecessor tiles read per look-back round
 
 __device__ __forceinline__ unsigned rs_digit(uint64_t key, uint32_t val, int shift,
@@ -295,7 +300,8 @@ __device__ __forceinline__ unsigned rs_digit(uint64_t key, uint32_t val, int shi
 // Digit counts of all passes: ghist[pass][256].
 __global__ void __launch_bounds__(kRsThreads)
 k_rs_count(const uint64_t *__restrict__ keys, int64_t n, int key_passes, int cloud_passes,
-           const int32_t *__restrict__ seg_of, uint32_t *__restrict__ ghist) {
+           const int32_t *__restrict__ seg_of, uint32_t *__restrict__ ghist,
+           uint32_t *__restrict__ vinit) {
   __shared__ uint32_t cnt[kRsMaxPasses][256];
   const int np = key_passes + cloud_passes;
   for (int p = 0; p < np; ++p) cnt[p][threadIdx.x] = 0;
@@ -303,6 +309,7 @@ k_rs_count(const uint64_t *__restrict__ keys, int64_t n, int key_passes, int clo
   for (int64_t i = blockIdx.x * (int64_t)kRsThreads + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * kRsThreads) {
     const uint64_t k = keys[i];
+    vinit[i] = (uint32_t)i;   // the first pass's value buffer holds indices < n throughout
     for (int p = 0; p < key_passes; ++p) atomicAdd(&cnt[p][(unsigned)(k >> (8 * p)) & 255u], 1u);
     if (cloud_passes) {
       const unsigned sg = (unsigned)seg_of[i];   // caller order: same multiset of ids
@@ -340,7 +347,7 @@ k_rs_sweep(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
            uint64_t *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n, int shift,
            const int32_t *__restrict__ seg_of, const uint32_t *__restrict__ ghist,
            uint32_t *__restrict__ status, unsigned *__restrict__ tile_counter, int ntiles,
-           unsigned *err) {
+           unsigned *err, int spin_budget, int withhold_first) {
   constexpr int W = kRsThreads / 32;
   __shared__ uint32_t s_w[W][256];      // per-warp digit counts, then exclusive bases
   __shared__ int32_t s_off[256];        // global position of the tile's local position 0, per digit
@@ -394,7 +401,9 @@ k_rs_sweep(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
   }
   const uint32_t count = run;
   volatile uint32_t *st = status + (int64_t)tile * 256 + tid;
-  *st = (tile == 0 ? kRsFlagPre : kRsFlagAgg) | count;
+  // (failure testing: with withhold_first the first tile publishes nothing, so the next
+  // tile's look-back waits on a flag that is never set until its budget runs out)
+  if (tile > 0 || !withhold_first) *st = (tile == 0 ? kRsFlagPre : kRsFlagAgg) | count;
   // look back kRsLook tiles per round (independent loads), nearest first
   uint32_t excl = 0;
   int spin = 0;                               // one bounded budget for the whole look-back
@@ -409,7 +418,7 @@ k_rs_sweep(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
     for (int k = 0; k < kRsLook; ++k) {
       if (found) break;
       const volatile uint32_t *sj = status + (int64_t)(j0 - k) * 256 + tid;
-      while ((v[k] >> 30) == 0 && ++spin < kRsSpin) v[k] = *sj;
+      while ((v[k] >> 30) == 0 && ++spin < spin_budget) v[k] = *sj;
       if ((v[k] >> 30) == 0) { atomicOr(err, kErrTimeout); found = true; break; }
       excl += v[k] & kRsValue;
       found = (v[k] >> 30) == 2u;
@@ -466,7 +475,7 @@ int radix_sort_buffers(Ctx *c, int64_t n, uint64_t *keys, uint64_t *keys_alt, ui
                                                     (size_t)np * ntiles * 256), c->stream));
   int cb = (int)((n + kRsThreads - 1) / kRsThreads);
   if (cb > 2 * c->num_sms) cb = 2 * c->num_sms;
-  k_rs_count<<<cb, kRsThreads, 0, c->stream>>>(keys, n, 8, cloud_passes, seg_of, ghist);
+  k_rs_count<<<cb, kRsThreads, 0, c->stream>>>(keys, n, 8, cloud_passes, seg_of, ghist, vb);
   ++c->launches;
   for (int pass = 0; pass < np; ++pass) {
     const bool cl = pass >= 8;
@@ -475,7 +484,9 @@ int radix_sort_buffers(Ctx *c, int64_t n, uint64_t *keys, uint64_t *keys_alt, ui
     k_rs_sweep<<<ntiles, kRsThreads, 0, c->stream>>>(ka, va, kb, vb, n, shift, so,
                                                      ghist + 256 * pass,
                                                      status + (int64_t)pass * ntiles * 256,
-                                                     counters + pass, ntiles, c->d_status);
+                                                     counters + pass, ntiles, c->d_status,
+                                                     c->sort_stall > 0 ? c->sort_stall : kRsSpin,
+                                                     c->sort_stall > 0 ? 1 : 0);
     ++c->launches;
     uint64_t *tk = ka; ka = kb; kb = tk;
     uint32_t *tv = va; va = vb; vb = tv;
@@ -635,6 +646,11 @@ __global__ void k_oct_count(int n, int leaf_max, int cbits, const int32_t *__res
   if (px < cbits) { nchild[X] = 0; return; }           // connector between clouds
   const int d = cdepth(px, cbits);
   const int P = parent[X];
+  if (P >= n - 1) {                                     // only after a failed sort pass
+    latch_error(status, kErrTree);
+    nchild[X] = 0;
+    return;
+  }
   const bool cell = P < 0 || plen[P] < cbits || cdepth(plen[P], cbits) < d;
   const int cnt = last[X] - first[X] + 1;
   if (!(cell && cnt > leaf_max && d < kLevels)) { nchild[X] = 0; return; }
@@ -825,7 +841,8 @@ __global__ void k_bucket_fill(const int4 *__restrict__ topo, const int32_t *__re
 }
 
 // Walk records: (COM hi, m) and (COM lo, l^2); l^2 = -1 marks a one-body leaf
-// (always a body-to-body term).  Quadrupole record: Q = 3T - tr(T) I as FP32.
+// (always a body-to-body term).  Quadrupole record: -Q = -(3T - tr(T) I) as FP32 (the
+// walk's term is written with the negated tensor, which needs no negation there).
 __device__ void write_records(const MomArgs &A, int id, double m, const double *com,
                               const double *T, bool single_body) {
   float h[3], lo[3];
@@ -838,12 +855,12 @@ __device__ void write_records(const MomArgs &A, int id, double m, const double *
   A.rec1[id] = make_float4(lo[0], lo[1], lo[2], l2);
   if (A.order >= 2) {
     double tr = T[0] + T[1] + T[2];
-    A.quadf[2 * id] = make_float4(__double2float_rn(fma(3.0, T[0], -tr)),
-                                  __double2float_rn(fma(3.0, T[1], -tr)),
-                                  __double2float_rn(fma(3.0, T[2], -tr)),
-                                  __double2float_rn(3.0 * T[3]));
-    A.quadf[2 * id + 1] = make_float4(__double2float_rn(3.0 * T[4]),
-                                      __double2float_rn(3.0 * T[5]), 0.f, 0.f);
+    A.quadf[2 * id] = make_float4(-__double2float_rn(fma(3.0, T[0], -tr)),
+                                  -__double2float_rn(fma(3.0, T[1], -tr)),
+                                  -__double2float_rn(fma(3.0, T[2], -tr)),
+                                  -__double2float_rn(3.0 * T[3]));
+    A.quadf[2 * id + 1] = make_float4(-__double2float_rn(3.0 * T[4]),
+                                      -__double2float_rn(3.0 * T[5]), 0.f, 0.f);
   }
 }
 

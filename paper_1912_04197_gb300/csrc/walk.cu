@@ -24,6 +24,9 @@
 //                body is then more than R_w / 2 away, which bounds the error of
 //                d = c_rel - x_rel by 5.5 * 2^-23 |d| (2^-23 (1.5 |d| + 2 R_w));
 //       near   - (quadrupole) the other node terms, on hi/lo coordinates;
+//   * the lists are stored pair-interleaved in shared memory, so that each lane
+//     evaluates two entries at once with packed two-wide FP32 instructions (f32x2 FMA,
+//     add and multiply of sm_100 and later: one issue slot for two operations);
 //   * each flushed list's partial sum enters a (hi, lo) two-sum accumulator (or an
 //     FP64 one).
 // The kernel is persistent: each warp takes 32-body tasks from an atomic counter,
@@ -75,12 +78,19 @@ enum { kStatBatches, kStatItems, kStatMixed, kStatFp64, kStatMono, kStatQuad, kS
        kStatLaneTerms, kStatSplit2, kStatSplit4, kStatSplit32, kStatFull, kStatFar,
        kStatMixedUnanimous, kStatPointLane, kStatCount = 16 };
 
+// The interaction lists are stored pair-interleaved: pair j holds entries 2j (a) and
+// 2j + 1 (b), each float4 two fields of both, (f_a, f_b, g_a, g_b), so that one
+// shared-memory load yields the operands of the packed instructions for both entries.
+constexpr int kPairCap = kListCap / 2;
 struct WarpSmem {
   uint2 st[kSmemStack];           // (first | (count-1) << 25, lane mask)
-  float4 la[kListCap];            // point list: (x_hi, y_hi, z_hi, m)
-  float4 lb[kListCap];            //             (x_lo, y_lo, z_lo, lane mask bits)
-  float4 fa[kListCap];            // far list:   (c_rel xyz, m)
-  float4 fc[kListCap];            //             (q_xz, q_yz, lane mask bits, 0)
+  float4 pA[kPairCap];            // point list: (x_hi, y_hi) of a pair of entries
+  float4 pB[kPairCap];            //             (z_hi, m)
+  float4 pC[kPairCap];            //             (x_lo, y_lo)
+  float4 pD[kPairCap];            //             (z_lo, lane mask bits)
+  float4 fA[kPairCap];            // far list:   (c_rel x, c_rel y)
+  float4 fB[kPairCap];            //             (c_rel z, m)
+  uint2 fM[kPairCap];             //             lane masks of entries a, b
   int32_t ltag[kListCap];         // counting / VJP: -(node+1) node term, else sorted body index
   float4 org_h, org_l;            // the warp origin (lane 0's body), hi and lo parts
   int32_t bitem[32];              // node id of each lane's item (mixed nodes' FP64 decisions)
@@ -96,11 +106,31 @@ struct WarpSmemV {
   float vt[3][kVjpChunk][33];     // per component, entry and lane: the term's gradient
 };
 
+// Quadrupole lists hold -Q (see the moments pass): (xx, yy), (zz, xy), (xz, yz).
 struct WarpSmemQ {
   WarpSmem base;
-  float4 fb[kListCap];            // far list:   (q_xx, q_yy, q_zz, q_xy)
-  float4 qa[kListCap], qb[kListCap], qc[kListCap], qd[kListCap];   // near node terms
+  float4 fC[kPairCap], fD[kPairCap], fE[kPairCap];                  // far list -Q
+  float4 nA[kPairCap], nB[kPairCap], nC[kPairCap], nD[kPairCap];    // near list, as point
+  float4 nE[kPairCap], nF[kPairCap], nG[kPairCap];                  // near list -Q
 };
+
+// Field k (0: the x/y slots, 1: the z/w slots) of entry p of a pair-interleaved array.
+__device__ __forceinline__ void put(float4 *a, int p, int k, float v) {
+  reinterpret_cast<float *>(a + (p >> 1))[2 * k + (p & 1)] = v;
+}
+__device__ __forceinline__ float getf(const float4 *a, int p, int k) {
+  return reinterpret_cast<const float *>(a + (p >> 1))[2 * k + (p & 1)];
+}
+// Zero the b half of pair j (an odd list's pad entry: mask 0, finite fields, adds 0).
+__device__ __forceinline__ void zero_b(float4 &v) { v.y = 0.f; v.w = 0.f; }
+
+// Packed two-wide FP32 arithmetic (IEEE round to nearest per element).
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 xy2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 zw2(float4 v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
 
 struct WalkArgs {
   const float4 *bhi, *blo;
@@ -190,105 +220,175 @@ __device__ __forceinline__ float inv_r(float r2, bool act) {
   return act ? inv : 0.f;
 }
 
-// Point terms: a += m d / (|d|^2 + eps^2)^{3/2}, d = source - body (hi/lo).
-template <bool EPS0, bool COUNT>
-__device__ __forceinline__ void flush_point(const WarpSmem &S, int cnt, int lane, float xh,
-                                            float yh, float zh, float xl, float yl, float zl,
-                                            float eps2, float &px, float &py, float &pz,
-                                            int gi, int &c_m2p, int &c_p2p) {
-  px = py = pz = 0.f;
-  const unsigned lbit = 1u << lane;
-#pragma unroll 4
-  for (int k = 0; k < cnt; ++k) {
-    const float4 a = S.la[k];
-    const float4 b = S.lb[k];
-    const bool act = (__float_as_uint(b.w) & lbit) != 0u;
-    const float dx = (a.x - xh) + (b.x - xl);
-    const float dy = (a.y - yh) + (b.y - yl);
-    const float dz = (a.z - zh) + (b.z - zl);
-    const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
-    const float inv = inv_r<EPS0>(r2, act);
-    const float s = a.w * (inv * inv * inv);
-    px = fmaf(s, dx, px);
-    py = fmaf(s, dy, py);
-    pz = fmaf(s, dz, pz);
-    if (COUNT && act) {
-      int tag = S.ltag[k];
-      if (tag < 0) ++c_m2p;
-      else if (tag != gi) ++c_p2p;
+template <bool EPS0>
+__device__ __forceinline__ float2 inv_r2(float2 r2, unsigned ma, unsigned mb, unsigned lbit) {
+  return make_float2(inv_r<EPS0>(r2.x, (ma & lbit) != 0u), inv_r<EPS0>(r2.y, (mb & lbit) != 0u));
+}
+
+// Counting variant only: decision counts of the entries of pair j.
+template <bool POINT>
+__device__ __forceinline__ void count_pair(const WarpSmem &S, int j, int cnt, unsigned ma,
+                                           unsigned mb, unsigned lbit, int gi, int &c_m2p,
+                                           int &c_p2p) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int k = 2 * j + h;
+    if (k < cnt && ((h ? mb : ma) & lbit)) {
+      if (!POINT) ++c_m2p;
+      else if (S.ltag[k] < 0) ++c_m2p;
+      else if (S.ltag[k] != gi) ++c_p2p;
     }
   }
 }
 
-// Quadrupole node term with d = source - body:
-//   a += m d r^-3 - Q d r^-5 + (5/2) (d.Q d) d r^-7,  r^2 = |d|^2 + eps^2
-// (the negative gradient of -m/r - y.Q y/(2 r^5), y = -d).
-__device__ __forceinline__ void quad_term(float dx, float dy, float dz, float m, float4 q0,
-                                          float qxz, float qyz, float inv, float &px,
-                                          float &py, float &pz) {
-  const float inv2 = inv * inv;
-  const float inv3 = inv2 * inv;
-  const float inv5 = inv3 * inv2;
-  const float inv7 = inv5 * inv2;
-  const float qx = fmaf(q0.x, dx, fmaf(q0.w, dy, qxz * dz));
-  const float qy = fmaf(q0.w, dx, fmaf(q0.y, dy, qyz * dz));
-  const float qz = fmaf(qxz, dx, fmaf(qyz, dy, q0.z * dz));
-  const float dqd = fmaf(dx, qx, fmaf(dy, qy, dz * qz));
-  const float s = fmaf(m, inv3, 2.5f * (dqd * inv7));
-  px = fmaf(s, dx, fmaf(-qx, inv5, px));
-  py = fmaf(s, dy, fmaf(-qy, inv5, py));
-  pz = fmaf(s, dz, fmaf(-qz, inv5, pz));
+// Point terms: a += m d / (|d|^2 + eps^2)^{3/2}, d = source - body (hi/lo), two
+// entries per step.
+template <bool EPS0, bool COUNT>
+__device__ __forceinline__ void flush_point(WarpSmem &S, int cnt, int lane, float xh, float yh,
+                                            float zh, float xl, float yl, float zl, float eps2,
+                                            float &px, float &py, float &pz, int gi, int &c_m2p,
+                                            int &c_p2p) {
+  if (cnt & 1) {
+    if (lane == 0) {
+      const int j = cnt >> 1;
+      zero_b(S.pA[j]); zero_b(S.pB[j]); zero_b(S.pC[j]); zero_b(S.pD[j]);
+    }
+    __syncwarp();
+  }
+  const unsigned lbit = 1u << lane;
+  const float2 nxh = dup2(-xh), nyh = dup2(-yh), nzh = dup2(-zh);
+  const float2 nxl = dup2(-xl), nyl = dup2(-yl), nzl = dup2(-zl), e2 = dup2(eps2);
+  float2 ax = dup2(0.f), ay = dup2(0.f), az = dup2(0.f);
+  const int np = (cnt + 1) >> 1;
+#pragma unroll (EPS0 ? 1 : 2)
+  for (int j = 0; j < np; ++j) {
+    const float4 A = S.pA[j], B = S.pB[j], C = S.pC[j], D = S.pD[j];
+    const float2 dx = add2(add2(xy2(A), nxh), add2(xy2(C), nxl));
+    const float2 dy = add2(add2(zw2(A), nyh), add2(zw2(C), nyl));
+    const float2 dz = add2(add2(xy2(B), nzh), add2(xy2(D), nzl));
+    const float2 r2 = fma2(dz, dz, fma2(dy, dy, fma2(dx, dx, e2)));
+    const unsigned ma = __float_as_uint(D.z), mb = __float_as_uint(D.w);
+    const float2 inv = inv_r2<EPS0>(r2, ma, mb, lbit);
+    const float2 sc = mul2(zw2(B), mul2(mul2(inv, inv), inv));
+    ax = fma2(sc, dx, ax);
+    ay = fma2(sc, dy, ay);
+    az = fma2(sc, dz, az);
+    if (COUNT) count_pair<true>(S, j, cnt, ma, mb, lbit, gi, c_m2p, c_p2p);
+  }
+  px = ax.x + ax.y;
+  py = ay.x + ay.y;
+  pz = az.x + az.y;
 }
 
-// Far node terms on warp-relative coordinates (monopole, or + quadrupole).
+// Quadrupole node terms of two entries, with d = source - body and qn = -Q:
+//   a += m d r^-3 - Q d r^-5 + (5/2) (d.Q d) d r^-7,  r^2 = |d|^2 + eps^2
+// (the negative gradient of -m/r - y.Q y/(2 r^5), y = -d); with qn = -Q the signs are
+// folded into the constant -5/2.
+__device__ __forceinline__ void quad_term2(float2 dx, float2 dy, float2 dz, float2 m, float2 qxx,
+                                           float2 qyy, float2 qzz, float2 qxy, float2 qxz,
+                                           float2 qyz, float2 inv, float2 &ax, float2 &ay,
+                                           float2 &az) {
+  const float2 inv2 = mul2(inv, inv);
+  const float2 inv3 = mul2(inv2, inv);
+  const float2 inv5 = mul2(inv3, inv2);
+  const float2 inv7 = mul2(inv5, inv2);
+  const float2 qx = fma2(qxx, dx, fma2(qxy, dy, mul2(qxz, dz)));
+  const float2 qy = fma2(qxy, dx, fma2(qyy, dy, mul2(qyz, dz)));
+  const float2 qz = fma2(qxz, dx, fma2(qyz, dy, mul2(qzz, dz)));
+  const float2 dqd = fma2(dx, qx, fma2(dy, qy, mul2(dz, qz)));
+  const float2 sc = fma2(m, inv3, mul2(dup2(-2.5f), mul2(dqd, inv7)));
+  ax = fma2(sc, dx, fma2(qx, inv5, ax));
+  ay = fma2(sc, dy, fma2(qy, inv5, ay));
+  az = fma2(sc, dz, fma2(qz, inv5, az));
+}
+
+// Far node terms on warp-relative coordinates (monopole, or + quadrupole), two entries
+// per step.
 template <int ORDER, bool EPS0, bool COUNT>
-__device__ __forceinline__ void flush_far(const void *Sv, int cnt, int lane, float xr, float yr,
+__device__ __forceinline__ void flush_far(void *Sv, int cnt, int lane, float xr, float yr,
                                           float zr, float eps2, float &px, float &py, float &pz,
                                           int &c_m2p) {
-  const WarpSmem &S = *reinterpret_cast<const WarpSmem *>(Sv);
-  px = py = pz = 0.f;
-  const unsigned lbit = 1u << lane;
-#pragma unroll 2
-  for (int k = 0; k < cnt; ++k) {
-    const float4 a = S.fa[k];
-    const float4 c = S.fc[k];
-    const bool act = (__float_as_uint(c.z) & lbit) != 0u;
-    const float dx = a.x - xr, dy = a.y - yr, dz = a.z - zr;
-    const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
-    const float inv = inv_r<EPS0>(r2, act);
-    if constexpr (ORDER == 2) {
-      const float4 q0 = reinterpret_cast<const WarpSmemQ *>(Sv)->fb[k];
-      quad_term(dx, dy, dz, a.w, q0, c.x, c.y, inv, px, py, pz);
-    } else {
-      const float s = a.w * (inv * inv * inv);
-      px = fmaf(s, dx, px);
-      py = fmaf(s, dy, py);
-      pz = fmaf(s, dz, pz);
+  WarpSmem &S = *reinterpret_cast<WarpSmem *>(Sv);
+  if (cnt & 1) {
+    if (lane == 0) {
+      const int j = cnt >> 1;
+      zero_b(S.fA[j]); zero_b(S.fB[j]); S.fM[j].y = 0u;
+      if constexpr (ORDER == 2) {
+        WarpSmemQ &Q = *reinterpret_cast<WarpSmemQ *>(Sv);
+        zero_b(Q.fC[j]); zero_b(Q.fD[j]); zero_b(Q.fE[j]);
+      }
     }
-    if (COUNT && act) ++c_m2p;
+    __syncwarp();
   }
+  const unsigned lbit = 1u << lane;
+  const float2 nx = dup2(-xr), ny = dup2(-yr), nz = dup2(-zr), e2 = dup2(eps2);
+  float2 ax = dup2(0.f), ay = dup2(0.f), az = dup2(0.f);
+  const int np = (cnt + 1) >> 1;
+#pragma unroll (ORDER == 2 ? 1 : 2)
+  for (int j = 0; j < np; ++j) {
+    const float4 A = S.fA[j], B = S.fB[j];
+    const uint2 mk = S.fM[j];
+    const float2 dx = add2(xy2(A), nx), dy = add2(zw2(A), ny), dz = add2(xy2(B), nz);
+    const float2 r2 = fma2(dz, dz, fma2(dy, dy, fma2(dx, dx, e2)));
+    const float2 inv = inv_r2<EPS0>(r2, mk.x, mk.y, lbit);
+    if constexpr (ORDER == 2) {
+      const WarpSmemQ &Q = *reinterpret_cast<const WarpSmemQ *>(Sv);
+      const float4 C = Q.fC[j], D = Q.fD[j], E = Q.fE[j];
+      quad_term2(dx, dy, dz, zw2(B), xy2(C), zw2(C), xy2(D), zw2(D), xy2(E), zw2(E), inv, ax, ay,
+                 az);
+    } else {
+      const float2 sc = mul2(zw2(B), mul2(mul2(inv, inv), inv));
+      ax = fma2(sc, dx, ax);
+      ay = fma2(sc, dy, ay);
+      az = fma2(sc, dz, az);
+    }
+    if (COUNT) {
+      int unused = 0;
+      count_pair<false>(S, j, cnt, mk.x, mk.y, lbit, 0, c_m2p, unused);
+    }
+  }
+  px = ax.x + ax.y;
+  py = ay.x + ay.y;
+  pz = az.x + az.y;
 }
 
-// Near quadrupole node terms on hi/lo coordinates.
+// Near quadrupole node terms on hi/lo coordinates, two entries per step.
 template <bool EPS0, bool COUNT>
-__device__ __forceinline__ void flush_near(const WarpSmemQ &S, int cnt, int lane, float xh,
-                                           float yh, float zh, float xl, float yl, float zl,
-                                           float eps2, float &px, float &py, float &pz,
-                                           int &c_m2p) {
-  px = py = pz = 0.f;
-  const unsigned lbit = 1u << lane;
-#pragma unroll 2
-  for (int k = 0; k < cnt; ++k) {
-    const float4 a = S.qa[k], b = S.qb[k], q0 = S.qc[k], q1 = S.qd[k];
-    const bool act = (__float_as_uint(b.w) & lbit) != 0u;
-    const float dx = (a.x - xh) + (b.x - xl);
-    const float dy = (a.y - yh) + (b.y - yl);
-    const float dz = (a.z - zh) + (b.z - zl);
-    const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
-    const float inv = inv_r<EPS0>(r2, act);
-    quad_term(dx, dy, dz, a.w, q0, q1.x, q1.y, inv, px, py, pz);
-    if (COUNT && act) ++c_m2p;
+__device__ __forceinline__ void flush_near(WarpSmemQ &Q, int cnt, int lane, float xh, float yh,
+                                           float zh, float xl, float yl, float zl, float eps2,
+                                           float &px, float &py, float &pz, int &c_m2p) {
+  if (cnt & 1) {
+    if (lane == 0) {
+      const int j = cnt >> 1;
+      zero_b(Q.nA[j]); zero_b(Q.nB[j]); zero_b(Q.nC[j]); zero_b(Q.nD[j]);
+      zero_b(Q.nE[j]); zero_b(Q.nF[j]); zero_b(Q.nG[j]);
+    }
+    __syncwarp();
   }
+  const unsigned lbit = 1u << lane;
+  const float2 nxh = dup2(-xh), nyh = dup2(-yh), nzh = dup2(-zh);
+  const float2 nxl = dup2(-xl), nyl = dup2(-yl), nzl = dup2(-zl), e2 = dup2(eps2);
+  float2 ax = dup2(0.f), ay = dup2(0.f), az = dup2(0.f);
+  const int np = (cnt + 1) >> 1;
+#pragma unroll 1
+  for (int j = 0; j < np; ++j) {
+    const float4 A = Q.nA[j], B = Q.nB[j], C = Q.nC[j], D = Q.nD[j];
+    const float2 dx = add2(add2(xy2(A), nxh), add2(xy2(C), nxl));
+    const float2 dy = add2(add2(zw2(A), nyh), add2(zw2(C), nyl));
+    const float2 dz = add2(add2(xy2(B), nzh), add2(xy2(D), nzl));
+    const float2 r2 = fma2(dz, dz, fma2(dy, dy, fma2(dx, dx, e2)));
+    const unsigned ma = __float_as_uint(D.z), mb = __float_as_uint(D.w);
+    const float2 inv = inv_r2<EPS0>(r2, ma, mb, lbit);
+    const float4 E = Q.nE[j], F = Q.nF[j], G = Q.nG[j];
+    quad_term2(dx, dy, dz, zw2(B), xy2(E), zw2(E), xy2(F), zw2(F), xy2(G), zw2(G), inv, ax, ay, az);
+    if (COUNT) {
+      int unused = 0;
+      count_pair<false>(Q.base, j, cnt, ma, mb, lbit, 0, c_m2p, unused);
+    }
+  }
+  px = ax.x + ax.y;
+  py = ay.x + ay.y;
+  pz = az.x + az.y;
 }
 
 // Vector-Jacobian product of the monopole terms of a point (FAR = false) or far
@@ -316,16 +416,15 @@ __device__ __forceinline__ void flush_vjp(WarpSmemV &V, int cnt, int lane, float
         float dx, dy, dz, m;
         bool act;
         if (FAR) {
-          const float4 a = S.fa[k], c = S.fc[k];
-          act = (__float_as_uint(c.z) >> lane) & 1u;
-          dx = a.x - xr; dy = a.y - yr; dz = a.z - zr; m = a.w;
+          act = (reinterpret_cast<const unsigned *>(S.fM)[k] >> lane) & 1u;
+          dx = getf(S.fA, k, 0) - xr; dy = getf(S.fA, k, 1) - yr; dz = getf(S.fB, k, 0) - zr;
+          m = getf(S.fB, k, 1);
         } else {
-          const float4 a = S.la[k], b = S.lb[k];
-          act = ((__float_as_uint(b.w) >> lane) & 1u) && S.ltag[k] != gi;
-          dx = (a.x - xh) + (b.x - xl);
-          dy = (a.y - yh) + (b.y - yl);
-          dz = (a.z - zh) + (b.z - zl);
-          m = a.w;
+          act = ((__float_as_uint(getf(S.pD, k, 1)) >> lane) & 1u) && S.ltag[k] != gi;
+          dx = (getf(S.pA, k, 0) - xh) + (getf(S.pC, k, 0) - xl);
+          dy = (getf(S.pA, k, 1) - yh) + (getf(S.pC, k, 1) - yl);
+          dz = (getf(S.pB, k, 0) - zh) + (getf(S.pD, k, 0) - zl);
+          m = getf(S.pB, k, 1);
         }
         const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
         const float inv = inv_r<EPS0>(r2, act);
@@ -358,14 +457,15 @@ __device__ __forceinline__ void flush_vjp(WarpSmemV &V, int cnt, int lane, float
   }
 }
 
-// Counted variant only: lockstep iteration counts of lane-group-split lists.
-__device__ __forceinline__ void split_costs(const float4 *m4, int comp, int cnt, int lane,
+// Counted variant only: lockstep iteration counts of lane-group-split lists (masks in
+// the z/w slots of a pair-interleaved array, or, with m4 = nullptr, in a mask array).
+__device__ __forceinline__ void split_costs(const float4 *m4, const uint2 *mu, int cnt, int lane,
                                             unsigned long long *st) {
   int c2 = 0, c4 = 0, c32 = 0, full = 0;
   const unsigned h = 0xFFFFu << (16 * (lane >> 4)), q = 0xFFu << (8 * (lane >> 3));
   for (int k = 0; k < cnt; ++k) {
-    const float4 v = m4[k];
-    const unsigned m = __float_as_uint(comp == 3 ? v.w : v.z);
+    const unsigned m = m4 ? __float_as_uint(getf(m4, k, 1))
+                          : reinterpret_cast<const unsigned *>(mu)[k];
     c2 += (m & h) != 0;
     c4 += (m & q) != 0;
     c32 += (m >> lane) & 1u;
@@ -542,8 +642,8 @@ k_walk(WalkArgs A) {
     auto flush_pt = [&]() {
       if (COUNT) {
         w_mono += npt;
-        split_costs(M.lb, 3, npt, lane, w_split);
-        split_costs(M.lb, 3, npt, lane, w_psplit);
+        split_costs(M.pD, nullptr, npt, lane, w_split);
+        split_costs(M.pD, nullptr, npt, lane, w_psplit);
       }
       float px, py, pz;
       if constexpr (VJP)
@@ -715,8 +815,9 @@ k_walk(WalkArgs A) {
         const unsigned bm = __ballot_sync(0xffffffffu, to_pt);
         if (to_pt) {
           const int p = npt + __popc(bm & ((1u << lane) - 1u));
-          M.la[p] = r0;
-          M.lb[p] = make_float4(r1.x, r1.y, r1.z, __uint_as_float(accm));
+          put(M.pA, p, 0, r0.x); put(M.pA, p, 1, r0.y); put(M.pB, p, 0, r0.z); put(M.pB, p, 1, r0.w);
+          put(M.pC, p, 0, r1.x); put(M.pC, p, 1, r1.y); put(M.pD, p, 0, r1.z);
+          put(M.pD, p, 1, __uint_as_float(accm));
           if (COUNT || VJP) M.ltag[p] = single ? tp.z : -(item + 1);
         }
         npt += __popc(bm);
@@ -729,13 +830,12 @@ k_walk(WalkArgs A) {
           const float cx = (r0.x - oh.x) + (r1.x - ol.x);
           const float cy = (r0.y - oh.y) + (r1.y - ol.y);
           const float cz = (r0.z - oh.z) + (r1.z - ol.z);
-          M.fa[p] = make_float4(cx, cy, cz, r0.w);
+          put(M.fA, p, 0, cx); put(M.fA, p, 1, cy); put(M.fB, p, 0, cz); put(M.fB, p, 1, r0.w);
+          reinterpret_cast<unsigned *>(M.fM)[p] = accm;
           if constexpr (VJP) S.ftag[p] = item;
           if constexpr (ORDER == 2) {
-            S.fb[p] = q0;
-            M.fc[p] = make_float4(q1.x, q1.y, __uint_as_float(accm), 0.f);
-          } else {
-            M.fc[p] = make_float4(0.f, 0.f, __uint_as_float(accm), 0.f);
+            put(S.fC, p, 0, q0.x); put(S.fC, p, 1, q0.y); put(S.fD, p, 0, q0.z);
+            put(S.fD, p, 1, q0.w); put(S.fE, p, 0, q1.x); put(S.fE, p, 1, q1.y);
           }
         }
         nfar += __popc(bf);
@@ -745,10 +845,11 @@ k_walk(WalkArgs A) {
         const unsigned bq = __ballot_sync(0xffffffffu, to_near);
         if (to_near) {
           const int p = nnear + __popc(bq & ((1u << lane) - 1u));
-          S.qa[p] = r0;
-          S.qb[p] = make_float4(r1.x, r1.y, r1.z, __uint_as_float(accm));
-          S.qc[p] = q0;
-          S.qd[p] = q1;
+          put(S.nA, p, 0, r0.x); put(S.nA, p, 1, r0.y); put(S.nB, p, 0, r0.z); put(S.nB, p, 1, r0.w);
+          put(S.nC, p, 0, r1.x); put(S.nC, p, 1, r1.y); put(S.nD, p, 0, r1.z);
+          put(S.nD, p, 1, __uint_as_float(accm));
+          put(S.nE, p, 0, q0.x); put(S.nE, p, 1, q0.y); put(S.nF, p, 0, q0.z);
+          put(S.nF, p, 1, q0.w); put(S.nG, p, 0, q1.x); put(S.nG, p, 1, q1.y);
         }
         nnear += __popc(bq);
       }
@@ -802,8 +903,10 @@ k_walk(WalkArgs A) {
         if (lane < take) {
           const int body = b0 + (base + lane - bx);
           const float4 h = A.bhi[body], l = A.blo[body];
-          M.la[npt + lane] = h;
-          M.lb[npt + lane] = make_float4(l.x, l.y, l.z, __uint_as_float(bm));
+          const int p = npt + lane;
+          put(M.pA, p, 0, h.x); put(M.pA, p, 1, h.y); put(M.pB, p, 0, h.z); put(M.pB, p, 1, h.w);
+          put(M.pC, p, 0, l.x); put(M.pC, p, 1, l.y); put(M.pD, p, 0, l.z);
+          put(M.pD, p, 1, __uint_as_float(bm));
           if (COUNT || VJP) M.ltag[npt + lane] = body;
         }
         npt += take;
@@ -812,7 +915,7 @@ k_walk(WalkArgs A) {
 
       // ---- evaluate the other full lists
       if (nfar >= A.flush_at) {
-        if (COUNT) { w_quad += nfar; split_costs(M.fc, 2, nfar, lane, w_split); }
+        if (COUNT) { w_quad += nfar; split_costs(nullptr, M.fM, nfar, lane, w_split); }
         float px, py, pz;
         if constexpr (VJP)
           flush_vjp<true, EPS0>(S, nfar, lane, xh, yh, zh, xl, yl, zl, xr, yr, zr, eps2, ux, uy, uz,
@@ -825,7 +928,7 @@ k_walk(WalkArgs A) {
       }
       if constexpr (ORDER == 2) {
         if (nnear >= A.flush_at) {
-          if (COUNT) { w_quad += nnear; split_costs(S.qb, 3, nnear, lane, w_split); }
+          if (COUNT) { w_quad += nnear; split_costs(S.nD, nullptr, nnear, lane, w_split); }
           float px, py, pz;
           flush_near<EPS0, COUNT>(S, nnear, lane, xh, yh, zh, xl, yl, zl, eps2, px, py, pz,
                                   c_m2p);
@@ -839,11 +942,11 @@ k_walk(WalkArgs A) {
       if (COUNT) {
         w_mono += npt; w_quad += nfar + nnear;
         if (npt > 0) {
-          split_costs(M.lb, 3, npt, lane, w_split);
-          split_costs(M.lb, 3, npt, lane, w_psplit);
+          split_costs(M.pD, nullptr, npt, lane, w_split);
+          split_costs(M.pD, nullptr, npt, lane, w_psplit);
         }
-        if (nfar > 0) split_costs(M.fc, 2, nfar, lane, w_split);
-        if constexpr (ORDER == 2) { if (nnear > 0) split_costs(S.qb, 3, nnear, lane, w_split); }
+        if (nfar > 0) split_costs(nullptr, M.fM, nfar, lane, w_split);
+        if constexpr (ORDER == 2) { if (nnear > 0) split_costs(S.nD, nullptr, nnear, lane, w_split); }
       }
       float px, py, pz;
       if (npt > 0) {

@@ -36,3 +36,19 @@ def gpu():
         pytest.skip("no CUDA device")
     from paper_1912_04197_gb300 import gravity
     return gravity
+
+
+def pytest_sessionfinish(session, exitstatus):
+    """Write the parity figures the GPU tests recorded (tests/util.py) to $PARITY_LOG."""
+    path = os.environ.get("PARITY_LOG")
+    if not path:
+        return
+    try:
+        from util import PARITY_RECORDS
+    except ImportError:
+        return
+    if PARITY_RECORDS:
+        import json
+        os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+        with open(path, "w") as f:
+            json.dump(PARITY_RECORDS, f, indent=1, sort_keys=True)

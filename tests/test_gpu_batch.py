@@ -10,7 +10,7 @@ import torch
 
 import oracle
 from paper_1912_04197_gb300 import inputs
-from util import force_errors, oracle_node_order, preorder_from_oracle, preorder_from_topo
+from util import check_parity, oracle_node_order, preorder_from_oracle, preorder_from_topo
 
 pytestmark = pytest.mark.gpu
 
@@ -110,8 +110,8 @@ def test_batch_forces_per_cloud(gpu, theta, leaf_max, order):
         ref, absum, oc = oracle.Tree(pos[b:e], m[b:e], leaf_max=leaf_max, order=order).forces(theta, 1e-3)
         assert np.array_equal(c[b:e, 0], oc[:, 1]) and np.array_equal(c[b:e, 1], oc[:, 2])
         assert np.array_equal(c[b:e, 2], oc[:, 0])
-        _, scale = force_errors(a[b:e], ref, np.maximum(absum, 1e-300))
-        assert scale.max() <= 1e-6, (k, scale.max())
+        check_parity(a[b:e], ref, np.maximum(absum, 1e-300),
+                     f"batch/theta{theta}/leaf{leaf_max}/order{order}/cloud{k}")
 
 
 def test_batch_leapfrog_per_cloud(gpu):

@@ -127,3 +127,25 @@ def test_torch_pool_allocator_helper(gpu):
     with pytest.raises(gpu.GravityError) as e:
         gpu.gravity_debug_set(gpu.Context(0), 99, 0)
     assert e.value.code == gpu.GRAVITY_E_ARG
+
+
+def test_sort_lookback_wait_runs_out_and_context_recovers(gpu):
+    # the first tile of every sort pass withholds its digit counts (a flag nothing sets),
+    # so the next tile's bounded look-back wait runs out: GRAVITY_E_TIMEOUT, no fault, every
+    # permutation entry still a valid index; the next build on the same context is
+    # bit-identical to a fresh context's
+    pos, _, m = inputs.clumpy_plummer(100_000, seed=8, nclusters=4)
+    ref = _forces(gpu, gpu.Context(0), pos, m, order=2, leaf_max=16)
+    ctx = gpu.Context(0)
+    gpu.gravity_debug_set(ctx, gpu.GRAVITY_DBGSET_SORT_STALL, 64)
+    with pytest.raises(gpu.GravityError) as e:
+        _forces(gpu, ctx, pos, m, order=2, leaf_max=16)
+    assert e.value.code == gpu.GRAVITY_E_TIMEOUT
+    perm = gpu.gravity_debug_export(ctx, gpu.DBG_PERM, len(pos))
+    assert perm.min() >= 0 and perm.max() < len(pos)
+    gpu.gravity_debug_set(ctx, gpu.GRAVITY_DBGSET_SORT_STALL, 0)
+    assert np.array_equal(_forces(gpu, ctx, pos, m, order=2, leaf_max=16), ref)
+    for bad in (-1, (1 << 22) + 1):
+        with pytest.raises(gpu.GravityError) as e:
+            gpu.gravity_debug_set(ctx, gpu.GRAVITY_DBGSET_SORT_STALL, bad)
+        assert e.value.code == gpu.GRAVITY_E_ARG

@@ -1,13 +1,15 @@
 """GPU walk (kernel 5, Sec. 2.1), direct sum (Eq. Newton) and stepping (Sec. 2.3)
 against the FP64 oracle on the same seeded inputs.
 
-Tolerances (derived from the FP32 pair arithmetic):
-  * decision counts (node terms, body terms) per body: exact;
-  * tree and direct accelerations: |a - a_oracle| <= 1e-6 * sum_k |term_k| for every
-    body (FP32 terms with hi/lo differences carry ~2^-22 relative error each, and
-    the two-sum accumulation adds ~2^-24 of the partial sums), and the plain
-    relative error |a - a_oracle| / max(|a_oracle|, 1e-3 rms) <= 1e-5 for 99.9 % of
-    bodies (the rest are bodies whose net force is cancelled well below the terms).
+Tolerances (derived from the FP32 pair arithmetic), checked on every body:
+  * decision counts (node terms, body terms, opening tests) per body: exact;
+  * tree accelerations: |a - a_oracle| <= 1e-6 * sum_k |term_k| (FP32 terms with hi/lo
+    differences carry ~2^-22 relative error each, and the two-sum accumulation adds
+    ~2^-24 of the partial sums), and the relative error |a - a_oracle| /
+    max(|a_oracle|, 1e-3 rms) <= 1e-5 for every body whose force is not cancelled more
+    than tenfold below its terms (sum |t| / |a| <= 10); the figures (largest relative
+    error, bodies above 1e-5 and their cancellation) are recorded per case;
+  * direct sums: the same, with a relative bound of 1e-6 (recorded per case).
 """
 import numpy as np
 import pytest
@@ -15,7 +17,7 @@ import torch
 
 import oracle
 from paper_1912_04197_gb300 import inputs
-from util import force_errors
+from util import check_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -39,11 +41,11 @@ def _gpu_forces(g, pos, m, theta, eps, counted=False, **kw):
     return acc.cpu().numpy(), None
 
 
-def _check(a, ref, absum):
-    rel, scale = force_errors(a, ref, absum)
-    assert scale.max() <= SCALE_TOL, (scale.max(), np.argmax(scale))
-    assert np.quantile(rel, 0.999) <= REL_TOL, np.quantile(rel, 0.999)
-    return rel, scale
+DIRECT_REL_TOL = 1e-6
+
+
+def _check(a, ref, absum, label, rel_tol=REL_TOL):
+    return check_parity(a, ref, absum, label, rel_tol=rel_tol, scale_tol=SCALE_TOL)
 
 
 CASES = {
@@ -68,7 +70,7 @@ def test_tree_forces_vs_oracle(gpu, case, theta, leaf_max, order):
     assert np.array_equal(cnt[:, 0], ocnt[:, 1]), "accepted-node counts differ"
     assert np.array_equal(cnt[:, 1], ocnt[:, 2]), "body-term counts differ"
     assert np.array_equal(cnt[:, 2], ocnt[:, 0]), "opening-test counts differ"
-    _check(a, ref, absum)
+    _check(a, ref, absum, f"tree/{case}/theta{theta}/leaf{leaf_max}/order{order}")
     # the uncounted kernel gives the same result
     a2, _ = _gpu_forces(gpu, pos, m, theta, eps, leaf_max=leaf_max, order=order)
     assert np.array_equal(a, a2)
@@ -94,7 +96,7 @@ def test_direct_sorted_tiles_vs_oracle(gpu, kind, n, eps, G):
     ref, absum = oracle.direct(pos, m, eps, G, targets=idx)
     a = acc.cpu().numpy()
     assert np.all(np.isfinite(a))
-    _check(a[idx], ref, absum)
+    _check(a[idx], ref, absum, f"direct_sorted/{kind}{n}", rel_tol=DIRECT_REL_TOL)
 
 
 @pytest.mark.parametrize("mac_guard,accum,eps", [(0, 0, 1e-3), (1, 1, 1e-3), (1, 0, 0.0)])
@@ -106,14 +108,14 @@ def test_tree_variants(gpu, mac_guard, accum, eps):
     ref, absum, ocnt = t.forces(0.6, eps, mac_guard=mac_guard)
     assert np.array_equal(cnt[:, 0], ocnt[:, 1]) and np.array_equal(cnt[:, 1], ocnt[:, 2])
     assert np.array_equal(cnt[:, 2], ocnt[:, 0])
-    _check(a, ref, absum)
+    _check(a, ref, absum, f"tree/variant/guard{mac_guard}/accum{accum}/eps{eps}")
 
 
 def test_theta0_equals_direct(gpu):
     pos, _, m = inputs.uniform_sphere(4099, seed=4)
     a, _ = _gpu_forces(gpu, pos, m, 0.0, 1e-3, leaf_max=8)
     ref, absum = oracle.direct(pos, m, 1e-3)
-    _check(a, ref, absum)
+    _check(a, ref, absum, "tree/theta0_vs_direct/sphere4099")
 
 
 @pytest.mark.parametrize("n,eps,G", [(2048, 1e-3, 1.0), (10_007, 5e-3, 2.5), (3, 0.0, 1.0)])
@@ -133,7 +135,7 @@ def test_direct_vs_oracle(gpu, n, eps, G):
         ref[1] = G * m[0] * (pos[0] - pos[1]) / np.linalg.norm(pos[0] - pos[1]) ** 3
         ref[2] = ref[1]
         absum = np.linalg.norm(ref, axis=1) + 1e-300
-    _check(acc.cpu().numpy(), ref, absum)
+    _check(acc.cpu().numpy(), ref, absum, f"direct/sphere{n}/eps{eps}", rel_tol=DIRECT_REL_TOL)
 
 
 def test_two_body_closed_form(gpu):
@@ -232,4 +234,4 @@ def test_opening_band_on_a_lattice(gpu, mac_guard):
     c = cnt.cpu().numpy()
     assert np.array_equal(c[:, 0], ocnt[:, 1]) and np.array_equal(c[:, 1], ocnt[:, 2])
     assert np.array_equal(c[:, 2], ocnt[:, 0])
-    _check(acc.cpu().numpy(), ref, absum)
+    _check(acc.cpu().numpy(), ref, absum, f"tree/lattice_band/guard{mac_guard}")

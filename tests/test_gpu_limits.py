@@ -7,7 +7,7 @@ import torch
 
 import oracle
 from paper_1912_04197_gb300 import inputs
-from util import force_errors
+from util import check_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -28,8 +28,7 @@ def _sampled(g, pos, m, theta, ntarg, seed, **kw):
     ref, absum, ocnt = t.forces(theta, 1e-3, targets=idx)
     assert np.array_equal(c[:, 0], ocnt[:, 1]) and np.array_equal(c[:, 1], ocnt[:, 2])
     assert np.array_equal(c[:, 2], ocnt[:, 0])
-    _, scale = force_errors(a, ref, absum)
-    assert scale.max() <= 1e-6, scale.max()
+    check_parity(a, ref, absum, f"limits/n{len(pos)}/" + "/".join(f"{k}{v}" for k, v in sorted(kw.items())))
 
 
 def test_largest_body_count(gpu):

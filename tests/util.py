@@ -48,3 +48,43 @@ def force_errors(a, ref, absum):
     rel = d / np.maximum(np.maximum(r, floor), 1e-300)
     scale = d / np.maximum(absum, 1e-300)
     return rel, scale
+
+
+# Parity records of this session (label -> figures); conftest writes them to the file named
+# by the environment variable PARITY_LOG at the end of the session, if it is set.
+PARITY_RECORDS = {}
+
+
+def check_parity(a, ref, absum, label, rel_tol=1e-5, scale_tol=1e-6):
+    """Per-body parity of accelerations `a` against the oracle's `ref`, for EVERY body given.
+
+    rel   = |a - ref| / max(|ref|, 1e-3 rms|ref|)      (the stated relative bound, rel_tol)
+    scale = |a - ref| / sum_k |t_k|                     (the rounding scale of a sum of terms)
+    kappa = sum_k |t_k| / max(|ref|, 1e-3 rms|ref|)     (cancellation of the body's terms)
+
+    Rule, body by body: scale <= scale_tol, and rel <= rel_tol unless kappa > rel_tol /
+    scale_tol (a force cancelled that far below its terms cannot carry rel_tol with FP32
+    terms, each of which rounds at a few 2^-24 of itself: there the scale bound is the
+    bound).  The figures (max rel, how many bodies exceed rel_tol, their largest and
+    smallest kappa, max scale) are recorded under `label` and returned."""
+    a = np.asarray(a)
+    ref = np.asarray(ref)
+    absum = np.asarray(absum)
+    rel, scale = force_errors(a, ref, absum)
+    r = np.linalg.norm(ref, axis=1)
+    floor = 1e-3 * np.sqrt(np.mean(r * r)) if len(r) else 0.0
+    kappa = absum / np.maximum(np.maximum(r, floor), 1e-300)
+    over = rel > rel_tol
+    k_cut = rel_tol / scale_tol
+    rec = {"bodies": int(len(rel)), "rel_tol": rel_tol, "scale_tol": scale_tol,
+           "max_rel": float(rel.max()) if len(rel) else 0.0,
+           "over_rel_tol": int(over.sum()),
+           "kappa_of_over_min": float(kappa[over].min()) if over.any() else None,
+           "kappa_of_over_max": float(kappa[over].max()) if over.any() else None,
+           "max_scale": float(scale.max()) if len(scale) else 0.0,
+           "median_rel": float(np.median(rel)) if len(rel) else 0.0}
+    PARITY_RECORDS[label] = rec
+    assert rec["max_scale"] <= scale_tol, (label, rec, int(np.argmax(scale)))
+    bad = over & (kappa <= k_cut)
+    assert not bad.any(), (label, rec, np.flatnonzero(bad)[:10])
+    return rec
