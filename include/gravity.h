@@ -128,6 +128,45 @@ int gravity_forces(gravity_ctx *ctx, double theta, double eps, double *acc);
 int gravity_forces_counted(gravity_ctx *ctx, double theta, double eps, double *acc,
                            int32_t *counts);
 
+/* ---- Sharded evaluation of one cloud (several GPUs, one context each).  Kernel 5 of the
+ * paper's list (Sec. 2.1) computes every body's force from the tree independently of the
+ * other bodies, so the bodies can be split between devices: every device builds the same
+ * tree from the same positions (the build is deterministic), walks a contiguous range of
+ * the walk's tasks, and the ranges' results are exchanged by the caller (one all-gather
+ * per step; this library makes no collective call).  A task is up to 32 bodies that are
+ * consecutive in the tree's (Morton) order and belong to one cloud. */
+
+/* Number of walk tasks of the current tree.  GRAVITY_E_NOTREE before a build. */
+int gravity_walk_tasks(gravity_ctx *ctx, int64_t *ntasks);
+
+/* Bodies of tasks [first_task, first_task + ntasks): *first_body is the first sorted
+ * position, *nbodies their count (the tasks' bodies are consecutive in sorted order).
+ * Host arithmetic only.  GRAVITY_E_ARG for a range outside [0, gravity_walk_tasks). */
+int gravity_task_bodies(gravity_ctx *ctx, int64_t first_task, int64_t ntasks,
+                        int64_t *first_body, int64_t *nbodies);
+
+/* gravity_forces restricted to tasks [first_task, first_task + ntasks): acc_sorted
+ * (device, (nbodies, 3) FP64, caller-owned) receives the G-scaled accelerations of the
+ * tasks' bodies in sorted order (row i = sorted body first_body + i, see
+ * gravity_task_bodies).  Each row equals the one gravity_forces computes for that body,
+ * bit for bit (same tasks, same launch decisions).  Asynchronous. */
+int gravity_forces_range(gravity_ctx *ctx, double theta, double eps, int64_t first_task,
+                         int64_t ntasks, double *acc_sorted);
+
+/* dst[perm[first_body + i]] = src_sorted[i] for i < nbodies: rows in the tree's sorted
+ * order back to the caller's order (perm = the current tree's order, gravity_tree_build).
+ * Device (n,3)-row arrays, FP64; rows of dst not addressed are left unchanged. */
+int gravity_scatter_sorted(gravity_ctx *ctx, int64_t first_body, int64_t nbodies,
+                           const double *src_sorted, double *dst);
+
+/* The integrator's pieces (Sec. 2.3) as separate calls, for a caller that assembles a step
+ * around gravity_forces_range: kick-drift v += h_kick a; x += dt v, and the kick
+ * v += h_kick a, over n bodies (device (n,3) FP64, no FMA contraction: the same roundings
+ * as leapfrog_step). */
+int gravity_kick_drift(gravity_ctx *ctx, int64_t n, double *pos, double *vel, const double *acc,
+                       double h_kick, double dt);
+int gravity_kick(gravity_ctx *ctx, int64_t n, double *vel, const double *acc, double h_kick);
+
 /* Vector-Jacobian product of the tree accelerations with respect to the body
  * positions, the interaction decisions of the current tree held fixed (the tree
  * of the last gravity_tree_build; monopole terms of Eq. (Force_thetaTrue) and

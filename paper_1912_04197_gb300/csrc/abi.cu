@@ -1,5 +1,6 @@
 // C ABI of libgravity: context, scratch management, argument checks, status
 // latching.  Declarations and their documentation are in include/gravity.h.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -171,6 +172,8 @@ int set_segments(Ctx *c, int nseg, const int64_t *off) {
       ts.push_back(k);
     }
   sg.ntasks = (int)tb.size();
+  sg.h_task_begin = tb;
+  sg.h_task_end = te;
   int rc = GRAVITY_OK;
   if (rc == GRAVITY_OK) rc = ctx_alloc(c, sg.off, nseg + 1);
   if (rc == GRAVITY_OK) rc = ctx_alloc(c, sg.seg_of, n);
@@ -449,6 +452,91 @@ int gravity_forces_counted(gravity_ctx *h, double theta, double eps, double *acc
                            int32_t *counts) {
   if (h && h->c.n > 0 && !counts) return GRAVITY_E_ARG;
   return forces_common(h, theta, eps, acc, counts);
+}
+
+int gravity_walk_tasks(gravity_ctx *h, int64_t *ntasks) {
+  if (!h || !ntasks) return GRAVITY_E_ARG;
+  if (!h->c.have_tree) return GRAVITY_E_NOTREE;
+  *ntasks = grav::walk_task_count(&h->c);
+  return GRAVITY_OK;
+}
+
+namespace grav {
+namespace {
+// Sorted-order bodies [*b0, *b0 + *nb) of walk tasks [first, first + count) of the tree.
+int task_bodies(const Ctx &c, int64_t first, int64_t count, int64_t *b0, int64_t *nb) {
+  const int64_t total = walk_task_count(&c);
+  if (first < 0 || count < 0 || first + count > total) return GRAVITY_E_ARG;
+  if (count == 0) { *b0 = 0; *nb = 0; return GRAVITY_OK; }
+  if (c.seg.nseg > 1) {
+    const int64_t last = first + count - 1;
+    const int64_t beg = c.seg.h_task_begin[(size_t)first];
+    const int64_t end = std::min<int64_t>(c.seg.h_task_begin[(size_t)last] + 32,
+                                          c.seg.h_task_end[(size_t)last]);
+    *b0 = beg;
+    *nb = end - beg;
+  } else {
+    *b0 = 32 * first;
+    *nb = std::min<int64_t>(32 * (first + count), c.n) - 32 * first;
+  }
+  return GRAVITY_OK;
+}
+}  // namespace
+}  // namespace grav
+
+int gravity_task_bodies(gravity_ctx *h, int64_t first_task, int64_t ntasks, int64_t *first_body,
+                        int64_t *nbodies) {
+  if (!h || !first_body || !nbodies) return GRAVITY_E_ARG;
+  if (!h->c.have_tree) return GRAVITY_E_NOTREE;
+  return grav::task_bodies(h->c, first_task, ntasks, first_body, nbodies);
+}
+
+int gravity_forces_range(gravity_ctx *h, double theta, double eps, int64_t first_task,
+                         int64_t ntasks, double *acc_sorted) {
+  grav::Range range_("gravity_forces_range");
+  if (!h || !(theta >= 0.0) || !(eps >= 0.0) || !std::isfinite(theta) || !std::isfinite(eps))
+    return GRAVITY_E_ARG;
+  Ctx &c = h->c;
+  if (!c.have_tree) return GRAVITY_E_NOTREE;
+  int64_t b0 = 0, nb = 0;
+  int rc = grav::task_bodies(c, first_task, ntasks, &b0, &nb);
+  if (rc) return rc;
+  if (nb == 0) return GRAVITY_OK;
+  if (!acc_sorted) return GRAVITY_E_ARG;
+  if ((rc = grav::set_device(c))) return rc;
+  return grav::walk_forces_range(&c, theta, eps, first_task, ntasks, b0, nb, acc_sorted);
+}
+
+int gravity_scatter_sorted(gravity_ctx *h, int64_t first_body, int64_t nbodies,
+                           const double *src_sorted, double *dst) {
+  if (!h) return GRAVITY_E_ARG;
+  Ctx &c = h->c;
+  if (!c.have_tree) return GRAVITY_E_NOTREE;
+  if (first_body < 0 || nbodies < 0 || first_body + nbodies > c.n) return GRAVITY_E_ARG;
+  if (nbodies == 0) return GRAVITY_OK;
+  if (!src_sorted || !dst) return GRAVITY_E_ARG;
+  int rc = grav::set_device(c);
+  if (rc) return rc;
+  return grav::launch_scatter_sorted(&c, first_body, nbodies, src_sorted, dst);
+}
+
+int gravity_kick_drift(gravity_ctx *h, int64_t n, double *pos, double *vel, const double *acc,
+                       double h_kick, double dt) {
+  if (!h || n < 0 || !std::isfinite(h_kick) || !std::isfinite(dt)) return GRAVITY_E_ARG;
+  if (n == 0) return GRAVITY_OK;
+  if (!pos || !vel || !acc) return GRAVITY_E_ARG;
+  int rc = grav::set_device(h->c);
+  if (rc) return rc;
+  return grav::launch_kick_drift(&h->c, n, pos, vel, acc, h_kick, dt);
+}
+
+int gravity_kick(gravity_ctx *h, int64_t n, double *vel, const double *acc, double h_kick) {
+  if (!h || n < 0 || !std::isfinite(h_kick)) return GRAVITY_E_ARG;
+  if (n == 0) return GRAVITY_OK;
+  if (!vel || !acc) return GRAVITY_E_ARG;
+  int rc = grav::set_device(h->c);
+  if (rc) return rc;
+  return grav::launch_kick(&h->c, n, vel, acc, h_kick);
 }
 
 int gravity_forces_vjp(gravity_ctx *h, double theta, double eps, const double *lambda,

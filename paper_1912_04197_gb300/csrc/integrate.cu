@@ -46,6 +46,19 @@ int launch_adjoint_kick_drift(Ctx *c, int64_t n, double *xbar, double *vbar, con
   return cuda_status(cudaGetLastError());
 }
 
+// dst rows perm[first + i] = src rows i (sorted order back to the caller's order).
+__global__ void k_scatter_sorted(int64_t first, int64_t nb, int64_t n,
+                                 const uint32_t *__restrict__ perm, const double *__restrict__ src,
+                                 double *__restrict__ dst) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nb) return;
+  const int64_t j = perm[first + i];
+  if (j >= n) return;                         // only after a failed sort (status latched)
+  dst[3 * j] = src[3 * i];
+  dst[3 * j + 1] = src[3 * i + 1];
+  dst[3 * j + 2] = src[3 * i + 2];
+}
+
 int launch_kick_drift(Ctx *c, int64_t n, double *pos, double *vel, const double *acc,
                       double h_kick, double dt) {
   int64_t n3 = 3 * n;
@@ -57,6 +70,15 @@ int launch_kick_drift(Ctx *c, int64_t n, double *pos, double *vel, const double 
 int launch_kick(Ctx *c, int64_t n, double *vel, const double *acc, double h_kick) {
   int64_t n3 = 3 * n;
   k_kick<<<(unsigned)((n3 + 255) / 256), 256, 0, c->stream>>>(n3, vel, acc, h_kick);
+  ++c->launches;
+  return cuda_status(cudaGetLastError());
+}
+
+int launch_scatter_sorted(Ctx *c, int64_t first_body, int64_t nbodies, const double *src,
+                          double *dst) {
+  if (nbodies <= 0) return GRAVITY_OK;
+  k_scatter_sorted<<<(unsigned)((nbodies + 255) / 256), 256, 0, c->stream>>>(
+      first_body, nbodies, c->n, c->t.idx, src, dst);
   ++c->launches;
   return cuda_status(cudaGetLastError());
 }

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "gravity.h"
 
 namespace grav {
@@ -73,6 +75,7 @@ struct Segs {
   int ntasks = 0;
   int64_t n = 0;                 // total bodies the segmentation describes
   int64_t body_cap = 0;
+  std::vector<int32_t> h_task_begin, h_task_end;   // host copies (task ranges of a shard)
 };
 
 // Captured leapfrog step (a CUDA graph) and the arguments it was captured with.
@@ -157,6 +160,12 @@ int64_t radix_hist_words(int64_t n);
 // ---- launchers (walk.cu)
 int walk_forces(Ctx *c, double theta, double eps, double *acc, int32_t *counts,
                 double *vel, double kick);
+// The walk of tasks [first_task, first_task + ntasks) only, their bodies' accelerations
+// written in sorted order to acc_sorted (nbodies rows, from sorted body body0).
+int walk_forces_range(Ctx *c, double theta, double eps, int64_t first_task, int64_t ntasks,
+                      int64_t body0, int64_t nbodies, double *acc_sorted);
+// Number of walk tasks of the current tree (32 Morton-consecutive bodies of one cloud each).
+int64_t walk_task_count(const Ctx *c);
 int walk_vjp(Ctx *c, double theta, double eps, const double *lambda, double *grad);
 // The same on a tree held elsewhere (a saved copy of the arrays the product reads).
 int walk_vjp_tree(Ctx *c, const Tree &t, double theta, double eps, const double *lambda,
@@ -173,6 +182,8 @@ int components(Ctx *c, const double *radius, double dmax, int32_t *label, int64_
 int launch_kick_drift(Ctx *c, int64_t n, double *pos, double *vel, const double *acc,
                       double h_kick, double dt);
 int launch_kick(Ctx *c, int64_t n, double *vel, const double *acc, double h_kick);
+int launch_scatter_sorted(Ctx *c, int64_t first_body, int64_t nbodies, const double *src,
+                          double *dst);
 int launch_adjoint_kick_drift(Ctx *c, int64_t n, double *xbar, double *vbar, const double *g,
                               double coef, double dt, bool drift);
 

@@ -166,6 +166,11 @@ struct WalkArgs {
   const int32_t *task_end;
   const int32_t *task_seg;
   unsigned long long *stats;      // counted variant only
+  int task0;                      // first task of the walked range (0: all tasks)
+  int split_basis;                // task count the split decision is taken on (the whole tree's)
+  double *acc_sorted;             // range walk: rows in sorted order from body body0 (else null)
+  int body0;
+  int nrange;                     // bodies of the range (rows of acc_sorted)
   const double *lambda;           // VJP: cotangent of the accelerations, caller order (n,3)
   double *g_own;                  // VJP: gradient of each body from its own terms, sorted order
   double *g_body;                 // VJP: gradient scattered to body sources, sorted order
@@ -548,7 +553,7 @@ k_walk(WalkArgs A) {
 
     // task: up to 32 consecutive bodies of one cloud; the walk starts at the cloud root
     const int part = A.split > 1 ? task % A.split : 0;
-    task = A.split > 1 ? task / A.split : task;
+    task = (A.split > 1 ? task / A.split : task) + A.task0;
     const int wbeg = A.task_begin ? A.task_begin[task] : task * 32;
     const int wend = min(A.task_begin ? A.task_end[task] : n, wbeg + 32);
     const int root = A.task_seg ? A.task_seg[task] : 0;
@@ -1010,16 +1015,25 @@ k_walk(WalkArgs A) {
       double ax, ay, az;
       acc.get(acc64, ax, ay, az);
       const int64_t ci = A.perm[gi];
-      atomicAdd(&A.acc[3 * ci], ax * A.G);
-      atomicAdd(&A.acc[3 * ci + 1], ay * A.G);
-      atomicAdd(&A.acc[3 * ci + 2], az * A.G);
+      double *dst = A.acc_sorted ? A.acc_sorted + 3 * (int64_t)(gi - A.body0) : A.acc + 3 * ci;
+      atomicAdd(dst, ax * A.G);
+      atomicAdd(dst + 1, ay * A.G);
+      atomicAdd(dst + 2, az * A.G);
       if (COUNT) {
         atomicAdd(&A.counts[3 * ci], c_m2p);
         atomicAdd(&A.counts[3 * ci + 1], c_p2p);
         atomicAdd(&A.counts[3 * ci + 2], c_tests);
       }
     }
-    if (!VJP && valid && A.split == 1) {
+    if (!VJP && valid && A.split == 1 && A.acc_sorted) {   // range walk: sorted rows
+      double ax, ay, az;
+      acc.get(acc64, ax, ay, az);
+      double *dst = A.acc_sorted + 3 * (int64_t)(gi - A.body0);
+      dst[0] = ax * A.G;
+      dst[1] = ay * A.G;
+      dst[2] = az * A.G;
+    }
+    if (!VJP && valid && A.split == 1 && !A.acc_sorted) {
       double ax, ay, az;
       acc.get(acc64, ax, ay, az);
       ax *= A.G; ay *= A.G; az *= A.G;
@@ -1072,14 +1086,19 @@ int launch_walk(Ctx *c, WalkArgs A) {
   int bps = blocks_per_sm[dev] - shape.blocks_less;
   if (bps < 1) bps = 1;
   int blocks = bps * c->num_sms;
-  // split tasks when there are no more of them than resident warps
+  // split tasks when the tree has no more of them than resident warps (decided on the
+  // whole tree's task count, so that a range walk computes what the full walk does)
   const int base_tasks = A.ntasks;
-  A.split = (A.mac_guard && base_tasks <= blocks * kWalkWarps) ? 2 : 1;
+  const int basis = A.split_basis > 0 ? A.split_basis : base_tasks;
+  A.split = (A.mac_guard && basis <= blocks * kWalkWarps) ? 2 : 1;
   A.ntasks = base_tasks * A.split;
   if (A.split > 1) {
     const size_t n3 = 3 * (size_t)A.n;
     if (MODE == kModeVjp) {
       GRAV_CUDA_TRY(cudaMemsetAsync(A.g_own, 0, sizeof(double) * n3, c->stream));
+    } else if (A.acc_sorted) {
+      GRAV_CUDA_TRY(cudaMemsetAsync(A.acc_sorted, 0, sizeof(double) * 3 * (size_t)A.nrange,
+                                    c->stream));
     } else {
       GRAV_CUDA_TRY(cudaMemsetAsync(A.acc, 0, sizeof(double) * n3, c->stream));
       if (MODE == kModeCount)
@@ -1115,6 +1134,46 @@ int launch_walk(Ctx *c, WalkArgs A) {
 }  // namespace
 
 int walk_stack_capacity() { return kStackCap; }
+
+int64_t walk_task_count(const Ctx *c) {
+  return c->seg.nseg > 1 ? (int64_t)c->seg.ntasks : (c->n + 31) / 32;
+}
+
+int walk_forces_range(Ctx *c, double theta, double eps, int64_t first_task, int64_t ntasks,
+                      int64_t body0, int64_t nbodies, double *acc_sorted) {
+  Tree &t = c->t;
+  WalkArgs A{};
+  A.bhi = t.body_hi; A.blo = t.body_lo; A.pos_s = t.pos_s;
+  A.rec0 = t.nrec0; A.rec1 = t.nrec1; A.quadf = t.nquadf;
+  A.topo = t.topo; A.ndepth = t.ndepth; A.ncom = t.ncom; A.geom = t.geom;
+  A.perm = t.idx; A.nnodes = t.nnodes;
+  A.n = (int)c->n;
+  if (c->seg.nseg > 1) {
+    A.task_begin = c->seg.task_begin;
+    A.task_end = c->seg.task_end;
+    A.task_seg = c->seg.task_seg;
+  }
+  A.ntasks = (int)ntasks;
+  A.task0 = (int)first_task;
+  A.split_basis = (int)walk_task_count(c);
+  A.acc_sorted = acc_sorted;
+  A.body0 = (int)body0;
+  A.nrange = (int)nbodies;
+  A.theta2d = theta * theta;
+  A.theta2f = (float)(theta * theta);
+  A.eps2 = (float)(eps * eps);
+  A.G = c->params.G;
+  A.mac_guard = c->params.mac_guard;
+  A.acc64 = c->params.accum == 1;
+  A.status = c->d_status;
+  A.max_iter = (int)(8 * c->n + 64);
+  A.task_counter = c->walk_queues;
+  A.stats = c->walk_stats;
+  const bool q = c->params.order == 2;
+  const bool e0 = !(A.eps2 > 0.f);
+  if (q) return e0 ? launch_walk<2, true, kModeForce>(c, A) : launch_walk<2, false, kModeForce>(c, A);
+  return e0 ? launch_walk<0, true, kModeForce>(c, A) : launch_walk<0, false, kModeForce>(c, A);
+}
 
 int walk_forces(Ctx *c, double theta, double eps, double *acc, int32_t *counts, double *vel,
                 double kick) {

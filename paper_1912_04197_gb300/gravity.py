@@ -82,6 +82,12 @@ def _load() -> ctypes.CDLL:
         "gravity_probe_fp32": (I, [P, I64, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "gravity_direct_noalloc": (I, [I64, P, P, D, D, P, P]),
         "gravity_set_clouds": (I, [P, ctypes.c_int32, P]),
+        "gravity_walk_tasks": (I, [P, ctypes.POINTER(I64)]),
+        "gravity_task_bodies": (I, [P, I64, I64, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
+        "gravity_forces_range": (I, [P, D, D, I64, I64, P]),
+        "gravity_scatter_sorted": (I, [P, I64, I64, P, P]),
+        "gravity_kick_drift": (I, [P, I64, P, P, P, D, D]),
+        "gravity_kick": (I, [P, I64, P, P, D]),
         "gravity_batch_tree_build": (I, [P, ctypes.c_int32, P, P, P, PP]),
     }
     for name, (res, args) in sig.items():
@@ -246,6 +252,52 @@ def gravity_forces(ctx: Context, theta: float, eps: float, acc: torch.Tensor) ->
     _check(_lib.gravity_forces(ctx.handle, float(theta), float(eps), _dev(acc, "acc", 3)),
            "gravity_forces")
     return acc
+
+
+def gravity_walk_tasks(ctx: Context) -> int:
+    n = ctypes.c_int64()
+    _check(_lib.gravity_walk_tasks(ctx.handle, ctypes.byref(n)), "gravity_walk_tasks")
+    return n.value
+
+
+def gravity_task_bodies(ctx: Context, first_task: int, ntasks: int) -> tuple[int, int]:
+    """(first sorted body, body count) of walk tasks [first_task, first_task + ntasks)."""
+    b0, nb = ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.gravity_task_bodies(ctx.handle, int(first_task), int(ntasks), ctypes.byref(b0),
+                                    ctypes.byref(nb)), "gravity_task_bodies")
+    return b0.value, nb.value
+
+
+def gravity_forces_range(ctx: Context, theta: float, eps: float, first_task: int, ntasks: int,
+                         acc_sorted: torch.Tensor) -> torch.Tensor:
+    _, nb = gravity_task_bodies(ctx, first_task, ntasks)
+    if acc_sorted.shape[0] < nb:
+        raise ValueError(f"acc_sorted needs {nb} rows")
+    _check(_lib.gravity_forces_range(ctx.handle, float(theta), float(eps), int(first_task),
+                                     int(ntasks), _dev(acc_sorted, "acc_sorted", 3)),
+           "gravity_forces_range")
+    return acc_sorted
+
+
+def gravity_scatter_sorted(ctx: Context, first_body: int, src_sorted: torch.Tensor,
+                           dst: torch.Tensor, nbodies: int | None = None) -> torch.Tensor:
+    nb = src_sorted.shape[0] if nbodies is None else int(nbodies)
+    _check(_lib.gravity_scatter_sorted(ctx.handle, int(first_body), nb,
+                                       _dev(src_sorted, "src_sorted", 3), _dev(dst, "dst", 3)),
+           "gravity_scatter_sorted")
+    return dst
+
+
+def gravity_kick_drift(ctx: Context, pos: torch.Tensor, vel: torch.Tensor, acc: torch.Tensor,
+                       h_kick: float, dt: float):
+    _check(_lib.gravity_kick_drift(ctx.handle, pos.shape[0], _dev(pos, "pos", 3),
+                                   _dev(vel, "vel", 3), _dev(acc, "acc", 3), float(h_kick),
+                                   float(dt)), "gravity_kick_drift")
+
+
+def gravity_kick(ctx: Context, vel: torch.Tensor, acc: torch.Tensor, h_kick: float):
+    _check(_lib.gravity_kick(ctx.handle, vel.shape[0], _dev(vel, "vel", 3), _dev(acc, "acc", 3),
+                             float(h_kick)), "gravity_kick")
 
 
 def gravity_forces_counted(ctx: Context, theta: float, eps: float, acc: torch.Tensor,
