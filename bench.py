@@ -74,22 +74,31 @@ def parse():
     ap.add_argument("--no-components", action="store_true",
                     help="skip the aggregate-identification leg")
     ap.add_argument("--no-sweep", action="store_true",
-                    help="skip the theta / accumulator sweep (runs with the direct-sum leg)")
+                    help="skip the theta / order / accumulator sweep (runs with the direct-sum leg)")
+    ap.add_argument("--fp64-sample", type=int, default=65536,
+                    help="bodies of the FP64 direct-sum reference computed by the oracle in the "
+                         "cpu_baseline leg (0 = none)")
+    ap.add_argument("--shard", action="store_true",
+                    help="N > 1: one cloud split between the ranks (replicated build, a range "
+                         "of the walk per rank, one all-gather; strong scaling) instead of one "
+                         "independent cloud per rank")
     return ap.parse_args()
 
 
 def workload(args):
+    """The benchmark's configuration, the same for both arms (the arithmetic each arm
+    computes in is reported in its own dtype / precision keys)."""
     return {"workload": f"clumpy aggregate: {args.n} bodies in 64 Plummer spheres (a=0.05, r<=10a) "
                         f"uniform in the unit sphere, equal masses, at rest",
             "n": args.n, "theta": args.theta, "eps": args.eps, "order": args.order,
-            "leaf_max": args.leaf_max, "accum": "fp32-two-sum" if args.accum == 0 else "fp64",
-            "mac_guard": 1, "step": "tree build + walk (one full force evaluation)",
+            "leaf_max": args.leaf_max, "mac_guard": 1,
+            "step": "tree build + walk (one full force evaluation)",
             "l2": "flushed before each timed step (256 MB write)", "seed": args.seed}
 
 
 def gen(args, rank):
     from paper_1912_04197_gb300 import inputs
-    return inputs.clumpy_plummer(args.n, seed=args.seed + rank)
+    return inputs.clumpy_plummer(args.n, seed=args.seed + (0 if args.shard else rank))
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -158,20 +167,22 @@ def whole_job_value(n_per_rank: int, world: int, t_max_ms: float) -> float:
     return world * n_per_rank / (t_max_ms * 1e-3)
 
 
-def oracle_eval(pos, m, args, ntarg):
-    """Oracle tree build (all bodies) + walk of ntarg seeded targets; returns the
-    extrapolated body-forces/s of a full evaluation and the times."""
+def oracle_eval(pos, m, args, ntarg, with_forces=False):
+    """Oracle tree build (all bodies) + walk of ntarg seeded targets (every body when
+    ntarg = N); returns body-forces/s of the evaluation (scaled to N targets when
+    sampled), the build and walk times and, on request, the walk's (targets, acc, absum)."""
     import oracle
     from paper_1912_04197_gb300 import inputs
-    idx = inputs.subset(len(pos), ntarg, seed=7)
+    idx = None if ntarg >= len(pos) else inputs.subset(len(pos), ntarg, seed=7)
     t0 = time.perf_counter()
     tree = oracle.Tree(pos, m, leaf_max=args.leaf_max, order=args.order)
     t1 = time.perf_counter()
-    tree.forces(args.theta, args.eps, targets=idx)
+    acc, absum, _ = tree.forces(args.theta, args.eps, targets=idx)
     t2 = time.perf_counter()
     t_build, t_walk = t1 - t0, t2 - t1
-    full = t_build + t_walk * len(pos) / len(idx)
-    return len(pos) / full, t_build, t_walk
+    full = t_build + t_walk * len(pos) / (len(pos) if idx is None else len(idx))
+    out = (len(pos) / full, t_build, t_walk)
+    return out + ((idx, acc, absum),) if with_forces else out
 
 
 def omp_threads():
@@ -179,41 +190,95 @@ def omp_threads():
     return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
 
 
-def cpu_baseline(pos, m, args):
+def parity_figures(a_gpu, ref, absum):
+    """Per-body parity of the GPU walk against the oracle's walk (the tests' rule):
+    rel = |d| / max(|a|, 1e-3 rms|a|), scale = |d| / sum|t|, kappa = sum|t| / max(...)."""
+    d = np.linalg.norm(a_gpu - ref, axis=1)
+    r = np.linalg.norm(ref, axis=1)
+    den = np.maximum(r, 1e-3 * np.sqrt(np.mean(r * r)))
+    rel, scale, kappa = d / den, d / np.maximum(absum, 1e-300), absum / den
+    over = rel > 1e-5
+    return {"bodies": int(len(rel)), "rel_max": float(rel.max()), "rel_median": float(np.median(rel)),
+            "over_1e-5": int(over.sum()), "scale_max": float(scale.max()),
+            "kappa_of_over_min": float(kappa[over].min()) if over.any() else None}
+
+
+def cpu_baseline_leg(pos, m, args, gpu):
+    """The FP64 oracle on the host cores: (1) the whole evaluation of the benchmark's
+    configuration (tree build + walk of every body), timed: the CPU baseline; its forces
+    also give the GPU walk's parity figures against the oracle; (2) the oracle's FP64
+    direct sum of `--fp64-sample` seeded bodies (all N sources), timed: the CPU direct-sum
+    baseline, and the reference for the error of every GPU configuration sampled in
+    `gpu["sampled"]` (median / 99th percentile of |a - a_FP64| / |a_FP64|)."""
+    import oracle
+    from paper_1912_04197_gb300 import inputs
     ntarg = args.cpu_sample if 0 < args.cpu_sample < len(pos) else len(pos)
-    runs = [oracle_eval(pos, m, args, ntarg) for _ in range(max(1, args.cpu_reps))]
-    val, tb, tw = sorted(runs)[len(runs) // 2]
+    runs = [oracle_eval(pos, m, args, ntarg, with_forces=(k == 0))
+            for k in range(max(1, args.cpu_reps))]
+    idx, oacc, oabs = runs[0][3]
+    val, tb, tw = sorted(r[:3] for r in runs)[len(runs) // 2]
     what = ("every body (the whole evaluation, no extrapolation)" if ntarg == len(pos)
             else f"{ntarg} seeded targets, scaled to N targets")
-    return {"value": val, "unit": UNIT, "cores": omp_threads(), "kind": "oracle",
-            "sample": f"FP64 oracle on the same workload: tree build of all {len(pos)} bodies "
-                      f"({tb:.2f} s, 1 thread) + walk of {what} ({tw:.2f} s, OpenMP); "
-                      f"median of {len(runs)} runs"}
+    cpu = {"value": val, "unit": UNIT, "cores": omp_threads(), "kind": "oracle",
+           "sample": f"FP64 oracle on the same workload: tree build of all {len(pos)} bodies "
+                     f"({tb:.2f} s, 1 thread) + walk of {what} ({tw:.2f} s, OpenMP); "
+                     f"median of {len(runs)} runs"}
+    acc_gpu = gpu["acc"] if idx is None else gpu["acc"][idx]
+    parity = parity_figures(acc_gpu, oacc, oabs)
+    parity["against"] = "the oracle's walk of the same tree configuration (FP64)"
+    accuracy = None
+    if args.fp64_sample > 0:
+        sidx = gpu["sample_idx"]
+        t0 = time.perf_counter()
+        ref, _ = oracle.direct(pos, m, args.eps, targets=sidx)
+        t_dir = time.perf_counter() - t0
+        rn = np.linalg.norm(ref, axis=1)
+        rows = []
+        for row in gpu["sampled"]:
+            rel = np.linalg.norm(row.pop("acc") - ref, axis=1) / rn
+            row.update({"median_vs_fp64": float(np.median(rel)),
+                        "p99_vs_fp64": float(np.quantile(rel, 0.99)),
+                        "meets_1e-3": bool(np.median(rel) <= 1e-3)})
+            rows.append(row)
+        qual = [r for r in rows if r.get("theta") == args.theta and r["meets_1e-3"]
+                and r["kind"] == "tree"]
+        best = min(qual, key=lambda r: r["build_ms"] + r["walk_ms"]) if qual else None
+        accuracy = {"reference": f"oracle FP64 direct sum of {len(sidx)} seeded bodies (all "
+                                 f"{len(pos)} sources)",
+                    "rows": rows,
+                    "fastest_meeting_1e-3_at_theta": None if best is None else
+                    {k: best[k] for k in ("order", "leaf_max", "accum", "build_ms", "walk_ms",
+                                          "median_vs_fp64")}}
+        cpu["direct_sample"] = {"bodies": len(sidx), "s": t_dir, "cores": omp_threads(),
+                                "value_scaled_to_N": len(pos) / (t_dir * len(pos) / len(sidx)),
+                                "unit": UNIT}
+    return cpu, parity, accuracy
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle, as it stands, on the host cores, timed on the
+    benchmark's configuration.  Each step is the whole evaluation (tree build of all
+    bodies + walk of every body), so ms_per_step is measured, not extrapolated."""
     if rank != 0:
         return 0
     pos, _, m = gen(args, 0)
-    # each step: full build + walk of a target sample sized so K+W steps take ~2-3 minutes
-    ntarg = 65536 if args.steps + args.warmup > 20 else args.n
     for _ in range(args.warmup):
-        oracle_eval(pos, m, args, ntarg)
-    vals = []
+        oracle_eval(pos, m, args, args.n)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(oracle_eval(pos, m, args, ntarg)[0])
+        oracle_eval(pos, m, args, args.n)
     wall = time.perf_counter() - t0
-    value = float(statistics.median(vals))
+    ms = 1e3 * wall / max(1, args.steps)
+    value = args.n / (ms * 1e-3)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * args.n / value,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload(args),
+            "precision": "FP64 throughout (the oracle)", "data": "synthetic",
+            "config": workload(args),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": omp_threads(), "kind": "oracle",
-                             "sample": f"per step: full FP64 tree build of {args.n} bodies + walk "
-                                       + ("of every body" if ntarg >= args.n else
-                                          f"of {ntarg} seeded targets, extrapolated to N targets")
-                                       + f"; median of {args.steps} steps ({wall:.1f} s wall)"},
+                             "sample": f"per step: FP64 tree build of all {args.n} bodies + walk "
+                                       f"of every body (the whole evaluation); {args.steps} steps "
+                                       f"in {wall:.1f} s"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -248,51 +313,69 @@ def walk_traffic(order):
     return float(vals[key]) if key in vals else None
 
 
-def theta_sweep_leg(args, g, ctx, P, M, accd, p, flush, stream):
-    """The same workload at theta 0.3 / 0.5 / 0.7 / 0.9, with the FP32 two-sum and the FP64
-    accumulator: walk time (CUDA events, L2 flushed), FLOP rate from the exact decision
-    counts, error against the direct sum, and the largest difference between the two
-    accumulators relative to the force."""
+def config_sweep_leg(args, g, ctx, P, M, accd, p, flush, stream, sample_idx):
+    """The headline workload at other opening angles (0.3 / 0.5 / 0.7 / 0.9, with the FP32
+    two-sum and the FP64 accumulator), and at theta 0.5 with the monopole (leaf 1, 16) and
+    other leaf sizes: build and walk time (CUDA events, L2 flushed), FLOP rate from the
+    exact decision counts, error against the GPU direct sum over every body, and the
+    accelerations of the sampled bodies for the FP64 direct-sum comparison."""
     import torch
     n = P.shape[0]
     dev = P.device
-    f_node = FLOP_QUAD if args.order == 2 else FLOP_POINT
     acc = torch.empty_like(P)
     cnt = torch.empty((n, 3), dtype=torch.int32, device=dev)
-    res = {}
-    rows = []
-    for accum in (0, 1):
-        q = g.params(order=args.order, leaf_max=args.leaf_max, accum=accum, walk_cfg=p.walk_cfg)
-        g.gravity_tree_build(ctx, P, M, q)
-        for theta in (0.3, 0.5, 0.7, 0.9):
-            g.gravity_forces_counted(ctx, theta, args.eps, acc, cnt)
-            c = cnt.to(torch.int64).sum(0).cpu().numpy()
-            flops = int(c[0]) * f_node + int(c[1]) * FLOP_POINT + int(c[2]) * FLOP_MAC
-            ts = []
-            for k in range(5):
-                flush.fill_(float(k))
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                g.gravity_forces(ctx, theta, args.eps, acc)
-                e1.record(stream)
-                e1.synchronize()
-                ts.append(e0.elapsed_time(e1))
-            g.gravity_sync(ctx)
-            t = float(np.median(ts))
-            rel = (torch.linalg.norm(acc - accd, dim=1) / torch.linalg.norm(accd, dim=1)).cpu().numpy()
-            res[(accum, theta)] = acc.clone()
-            rows.append({"theta": theta, "accum": "fp32-two-sum" if accum == 0 else "fp64",
-                         "walk_ms": t, "tflops": flops / (t * 1e-3) / 1e12,
-                         "node_terms": int(c[0]), "body_terms": int(c[1]), "opening_tests": int(c[2]),
-                         "median_error": float(np.median(rel)),
-                         "p99_error": float(np.quantile(rel, 0.99))})
+    sidx = None if sample_idx is None else torch.as_tensor(sample_idx, device=dev)
+    rows, res = [], {}
+    cfgs = [(args.order, args.leaf_max, accum, theta) for accum in (0, 1)
+            for theta in (0.3, 0.5, 0.7, 0.9)]
+    cfgs += [(0, 16, 0, args.theta), (0, 1, 0, args.theta), (2, 8, 0, args.theta),
+             (2, 32, 0, args.theta)]
+    for order, leaf, accum, theta in cfgs:
+        q = g.params(order=order, leaf_max=leaf, accum=accum, walk_cfg=p.walk_cfg)
+        tb = []
+        for k in range(5):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.gravity_tree_build(ctx, P, M, q)
+            e1.record(stream)
+            e1.synchronize()
+            tb.append(e0.elapsed_time(e1))
+        g.gravity_forces_counted(ctx, theta, args.eps, acc, cnt)
+        c = cnt.to(torch.int64).sum(0).cpu().numpy()
+        f_node = FLOP_QUAD if order == 2 else FLOP_POINT
+        flops = int(c[0]) * f_node + int(c[1]) * FLOP_POINT + int(c[2]) * FLOP_MAC
+        ts = []
+        for k in range(5):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.gravity_forces(ctx, theta, args.eps, acc)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        g.gravity_sync(ctx)
+        t = float(np.median(ts))
+        rel = (torch.linalg.norm(acc - accd, dim=1) / torch.linalg.norm(accd, dim=1)).cpu().numpy()
+        res[(order, leaf, accum, theta)] = acc.clone()
+        rows.append({"kind": "tree", "theta": theta, "order": order, "leaf_max": leaf,
+                     "accum": "fp32-two-sum" if accum == 0 else "fp64",
+                     "build_ms": float(np.median(tb)), "walk_ms": t,
+                     "tflops": flops / (t * 1e-3) / 1e12,
+                     "node_terms": int(c[0]), "body_terms": int(c[1]), "opening_tests": int(c[2]),
+                     "median_error_vs_gpu_direct": float(np.median(rel)),
+                     "p99_error_vs_gpu_direct": float(np.quantile(rel, 0.99)),
+                     "acc": None if sidx is None else acc[sidx].cpu().numpy()})
     for r in rows:
-        if r["accum"] == "fp32-two-sum":
-            a32, a64 = res[(0, r["theta"])], res[(1, r["theta"])]
+        if r["accum"] == "fp32-two-sum" and r["order"] == args.order and r["leaf_max"] == args.leaf_max:
+            a32 = res[(r["order"], r["leaf_max"], 0, r["theta"])]
+            a64 = res[(r["order"], r["leaf_max"], 1, r["theta"])]
             d = (torch.linalg.norm(a32 - a64, dim=1) / torch.linalg.norm(a64, dim=1)).max()
             r["max_rel_diff_vs_fp64_accum"] = float(d)
-    return {"workload": "the headline aggregate, one tree build per accumulator, walk shape "
-                        "of the headline; errors against the GPU direct sum", "rows": rows}
+    rows.append({"kind": "direct", "theta": None, "order": None, "leaf_max": None, "accum": None,
+                 "build_ms": 0.0, "walk_ms": None,
+                 "acc": None if sidx is None else accd[sidx].cpu().numpy()})
+    return rows
 
 
 def components_leg(args, g, ctx, P, M, p, flush, stream):
@@ -343,10 +426,22 @@ def run_ours(args, rank, world, local_rank):
         p.walk_cfg = autotune.tune_walk(ctx, P, M, p, args.theta, args.eps)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
     stream = torch.cuda.current_stream(dev)
+    shard_mode = args.shard and world > 1
+    if shard_mode:
+        # one cloud split between the ranks: the same tree on every rank, a range of the
+        # walk per rank, one all-gather of the ranges' accelerations (NCCL)
+        from paper_1912_04197_gb300 import shard
+        eng, comm = shard.GpuEngine(ctx, p), shard.TorchComm()
+
+    def walk():
+        if shard_mode:
+            shard.sharded_forces(eng, comm, args.theta, args.eps, acc)
+        else:
+            g.gravity_forces(ctx, args.theta, args.eps, acc)
 
     def step():
         g.gravity_tree_build(ctx, P, M, p)
-        g.gravity_forces(ctx, args.theta, args.eps, acc)
+        walk()
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -357,7 +452,13 @@ def run_ours(args, rank, world, local_rank):
     g.gravity_tree_build(ctx, P, M, p)
     g.gravity_forces_counted(ctx, args.theta, args.eps, acc, cnt)
     g.gravity_sync(ctx)
-    c = cnt.to(torch.int64).sum(0).cpu().numpy()
+    if shard_mode:         # this rank's range of the walk only
+        first, count = shard.plan(g.gravity_walk_tasks(ctx), world)[rank]
+        b0, nb = g.gravity_task_bodies(ctx, first, count)
+        perm = g.gravity_debug_export(ctx, g.DBG_PERM, n).astype(np.int64)
+        c = cnt.to(torch.int64)[torch.as_tensor(perm[b0:b0 + nb], device=dev)].sum(0).cpu().numpy()
+    else:
+        c = cnt.to(torch.int64).sum(0).cpu().numpy()
     node_terms, body_terms, tests = int(c[0]), int(c[1]), int(c[2])
     f_node = FLOP_QUAD if args.order == 2 else FLOP_POINT
     walk_flops = node_terms * f_node + body_terms * FLOP_POINT + tests * FLOP_MAC
@@ -380,10 +481,11 @@ def run_ours(args, rank, world, local_rank):
         e0.record(stream)
         g.gravity_tree_build(ctx, P, M, p)
         e1.record(stream)
-        g.gravity_forces(ctx, args.theta, args.eps, acc)
+        walk()
         e2.record(stream)
     torch.cuda.synchronize(dev)
     wall = time.perf_counter() - wall0
+    acc_head = acc.cpu().numpy()
     clk = clocks.stop()
     if world > 1:
         dist.barrier()
@@ -393,11 +495,15 @@ def run_ours(args, rank, world, local_rank):
     t_walk = sum(e1.elapsed_time(e2) for _, e1, e2 in ev) / args.steps
     t_step = t_build + t_walk
     t_max = max_over_ranks(t_step, world, dev)
-    value = whole_job_value(n, world, t_max)
+    # sharded: one cloud of n bodies over all ranks; else one cloud per rank
+    value = whole_job_value(n, 1, t_max) if shard_mode else whole_job_value(n, world, t_max)
+    from paper_1912_04197_gb300 import inputs
+    sample_idx = inputs.subset(n, args.fp64_sample, seed=17) if args.fp64_sample > 0 else None
+    sweep_rows = []
 
     # error against the direct sum, and the direct-sum throughput on the same GPU
     extra = {}
-    if not args.no_direct:
+    if not args.no_direct and not shard_mode:
         accd = torch.empty_like(P)
         g.gravity_direct(ctx, P, M, args.eps, 1.0, accd)       # warm-up
         d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -419,9 +525,9 @@ def run_ours(args, rank, world, local_rank):
                            "interactions_per_s": n * (n - 1) / (t_dir * 1e-3),
                            "flops_per_s": FLOP_POINT * n * (n - 1) / (t_dir * 1e-3)}
         if not args.no_sweep:
-            extra["theta_sweep"] = theta_sweep_leg(args, g, ctx, P, M, accd, p, flush, stream)
+            sweep_rows = config_sweep_leg(args, g, ctx, P, M, accd, p, flush, stream, sample_idx)
 
-    if not args.no_components:
+    if not args.no_components and not shard_mode:
         extra["components"] = components_leg(args, g, ctx, P, M, p, flush, stream)
 
     # rooflines: the walk is FP32-ALU bound (no dense contraction, no tensor cores)
@@ -442,7 +548,26 @@ def run_ours(args, rank, world, local_rank):
                                                   "opening_test": FLOP_MAC}}}
 
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and shard_mode:
+        # host positions and masses in, build + sharded walk + all-gather, host forces out
+        ph = torch.tensor(pos).pin_memory()
+        mh = torch.tensor(m).pin_memory()
+        ah = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+        ke = min(args.steps, 10)
+        dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            P.copy_(ph, non_blocking=True)
+            M.copy_(mh, non_blocking=True)
+            step()
+            ah.copy_(acc, non_blocking=True)
+            torch.cuda.synchronize(dev)
+        te = max_over_ranks((time.perf_counter() - t0) / ke, world, dev)
+        e2e = {"value": whole_job_value(n, 1, 1e3 * te), "unit": UNIT,
+               "h2d_bytes_per_step": int(ph.nbytes + mh.nbytes), "d2h_bytes_per_step": int(ah.nbytes),
+               "ms_per_step": 1e3 * te,
+               "api": "pinned host copies + gravity_tree_build + shard.sharded_forces per rank"}
+    elif not args.no_e2e:
         ph = torch.tensor(pos).pin_memory()
         mh = torch.tensor(m).pin_memory()
         ah = torch.empty((n, 3), dtype=torch.float64).pin_memory()
@@ -457,24 +582,43 @@ def run_ours(args, rank, world, local_rank):
                "ms_per_step": 1e3 * te,
                "api": "gravity_forces_host (pinned host buffers, copies + build + walk + sync)"}
 
-    ens = None if args.no_ensemble else ensemble_leg(args, g, dev, rank)
-    grad = None if args.no_grad else gradient_leg(args, g, dev, rank)
+    ens = None if args.no_ensemble or shard_mode else ensemble_leg(args, g, dev, rank)
+    grad = None if args.no_grad or shard_mode else gradient_leg(args, g, dev, rank)
 
     if rank != 0:
         return 0
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline(pos, m, args)
+        if sample_idx is not None and not sweep_rows:      # no sweep: the headline alone
+            sweep_rows = [{"kind": "tree", "theta": args.theta, "order": args.order,
+                           "leaf_max": args.leaf_max, "accum": "fp32-two-sum" if args.accum == 0
+                           else "fp64", "build_ms": t_build, "walk_ms": t_walk,
+                           "acc": acc_head[sample_idx]}]
+        cpu, parity, accuracy = cpu_baseline_leg(pos, m, args, {"acc": acc_head,
+                                                                "sample_idx": sample_idx,
+                                                                "sampled": sweep_rows})
+        extra["parity_vs_oracle"] = parity
+        if accuracy is not None:
+            extra["config_sweep"] = accuracy
+    elif sweep_rows:
+        for r in sweep_rows:
+            r.pop("acc", None)
+        extra["config_sweep"] = {"reference": "GPU direct sum only (no oracle leg)",
+                                 "rows": sweep_rows}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "scaling": "strong" if shard_mode else "weak", "vs_baseline": None, "dtype": "f32",
             "dtype_note": "FP32 pair terms and opening tests on hi/lo coordinates; FP64 moments, "
                           "FP64 decisions in the guard band, FP64 outputs",
+            "precision": {"accum": "fp32-two-sum" if args.accum == 0 else "fp64"},
             "data": "synthetic", "config": workload(args), "phases_ms": {"build": t_build, "walk": t_walk},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "gpu_launches_per_step": launches / args.steps, "clocks": clk,
-            "timed_wall_s": wall}
-    line["config"]["walk_cfg"] = int(p.walk_cfg)
+            "timed_wall_s": wall, "launch": {"walk_cfg": int(p.walk_cfg)}}
+    if shard_mode:
+        line["sharding"] = {"mode": "one cloud over all ranks: replicated build, walk task range "
+                                    "per rank, one all-gather of accelerations per evaluation",
+                            "ranks": world}
     if ens is not None:
         line["ensemble"] = ens
     if grad is not None:

@@ -23,3 +23,15 @@ def test_reference_arm_json_line():
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
     assert d["config"]["n"] == 3000
+    # the same configuration dictionary as the GPU arm's (precision is reported apart)
+    sys.path.insert(0, ROOT)
+    import bench
+    argv = sys.argv
+    try:
+        sys.argv = ["bench.py", "--n", "3000"]
+        assert d["config"] == bench.workload(bench.parse())
+    finally:
+        sys.argv = argv
+    assert "accum" not in d["config"] and "walk_cfg" not in d["config"]
+    # measured, not extrapolated: every step is the whole evaluation
+    assert "every body" in d["cpu_baseline"]["sample"]
