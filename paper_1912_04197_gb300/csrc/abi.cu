@@ -74,7 +74,7 @@ namespace {
 void free_tree(Ctx *c) {
   Tree &t = c->t;
   ctx_release(c, t.keys); ctx_release(c, t.keys_alt); ctx_release(c, t.idx);
-  ctx_release(c, t.idx_alt); ctx_release(c, t.hist); ctx_release(c, t.scan_aux);
+  ctx_release(c, t.idx_alt); ctx_release(c, t.hist);
   ctx_release(c, t.bbox_part); ctx_release(c, t.pos_s); ctx_release(c, t.mass_s);
   ctx_release(c, t.body_hi); ctx_release(c, t.body_lo); ctx_release(c, t.bchild);
   ctx_release(c, t.bparent); ctx_release(c, t.bfirst); ctx_release(c, t.blast);
@@ -110,15 +110,12 @@ int ensure_capacity(Ctx *c, int64_t n) {
   int64_t cap = n + n / 8;
   if (cap < 1024) cap = 1024;
   if (cap > kMaxBodies) cap = kMaxBodies;
-  const int64_t ntiles = (cap + 2047) / 2048;
-  const int64_t scan_n = (256 * ntiles > cap ? 256 * ntiles : cap);
   const int64_t nodes = 2 * cap;
   int rc = GRAVITY_OK;
 #define GRAV_ALLOC(p, cnt) if (rc == GRAVITY_OK) rc = ctx_alloc(c, p, cnt)
   GRAV_ALLOC(t.keys, cap); GRAV_ALLOC(t.keys_alt, cap);
   GRAV_ALLOC(t.idx, cap); GRAV_ALLOC(t.idx_alt, cap);
   GRAV_ALLOC(t.hist, radix_hist_words(cap));         // radix sort: counts + tile states
-  GRAV_ALLOC(t.scan_aux, scan_n / 4096 + 64);
   GRAV_ALLOC(t.bbox_part, 6 * (4 * (int64_t)c->num_sms + 3));
   GRAV_ALLOC(t.pos_s, 3 * cap); GRAV_ALLOC(t.mass_s, cap);
   GRAV_ALLOC(t.body_hi, cap); GRAV_ALLOC(t.body_lo, cap);

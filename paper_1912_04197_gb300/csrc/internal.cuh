@@ -29,7 +29,6 @@ struct Tree {
   uint64_t *keys = nullptr, *keys_alt = nullptr;
   uint32_t *idx = nullptr, *idx_alt = nullptr;   // after the sort: idx = perm (sorted -> caller)
   uint32_t *hist = nullptr;                     // radix sort: digit counts and tile states
-  uint32_t *scan_aux = nullptr;                 // block sums of the scan
   double *bbox_part = nullptr;                  // [blocks][6]
   unsigned *bbox_ticket = nullptr;
   // sorted bodies

@@ -16,9 +16,9 @@ constexpr int kBBoxThreads = 256;
 constexpr int kRsThreads = 256;
 constexpr int kRsItems = 8;
 constexpr int kRsTile = kRsThreads * kRsItems;   // keys per radix tile
-constexpr int kScanThreads = 1024;
-constexpr int kScanItems = 4;
-constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr int kOctThreads = 256;                 // octree count + scan: threads per tile,
+constexpr int kOctItems = 4;                     //   nodes per thread,
+constexpr int kOctTile = kOctThreads * kOctItems;  //   binary nodes per tile
 
 __device__ __forceinline__ int cap_depth(int plen) {
   int d = plen / 3;
@@ -185,87 +185,6 @@ __global__ void k_keys(const double *__restrict__ pos, int64_t n, const double *
   idx[i] = (uint32_t)i;
 }
 
-// ------------------------------------------------------------------ exclusive scan (u32)
-__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
-  int l = threadIdx.x & 31;
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
-    if (l >= o) v += t;
-  }
-  return v;
-}
-
-// Block-wide exclusive scan of one value per thread (blockDim = kScanThreads).
-__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *s_warp, uint32_t &total) {
-  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  uint32_t inc = warp_incl_scan(v);
-  if (l == 31) s_warp[w] = inc;
-  __syncthreads();
-  if (w == 0) {
-    uint32_t x = (l < (kScanThreads >> 5)) ? s_warp[l] : 0u;
-    uint32_t xi = warp_incl_scan(x);
-    s_warp[l] = xi - x;
-    if (l == 31) s_warp[32] = xi;
-  }
-  __syncthreads();
-  uint32_t r = s_warp[w] + inc - v;
-  total = s_warp[32];
-  __syncthreads();
-  return r;
-}
-
-__global__ void __launch_bounds__(kScanThreads)
-k_scan_tiles(uint32_t *__restrict__ data, int64_t n, uint32_t *__restrict__ sums) {
-  __shared__ uint32_t s_warp[33];
-  int64_t base = blockIdx.x * (int64_t)kScanTile + threadIdx.x * kScanItems;
-  uint32_t v[kScanItems], t = 0;
-  for (int k = 0; k < kScanItems; ++k) {
-    v[k] = (base + k < n) ? data[base + k] : 0u;
-    t += v[k];
-  }
-  uint32_t total;
-  uint32_t ex = block_excl_scan(t, s_warp, total);
-  for (int k = 0; k < kScanItems; ++k) {
-    if (base + k < n) data[base + k] = ex;
-    ex += v[k];
-  }
-  if (threadIdx.x == 0) sums[blockIdx.x] = total;
-}
-
-// One block scans all tile sums (any count, in chunks) and writes the grand total.
-__global__ void __launch_bounds__(kScanThreads)
-k_scan_sums(uint32_t *__restrict__ sums, int nb, uint32_t *__restrict__ total_out) {
-  __shared__ uint32_t s_warp[33];
-  uint32_t carry = 0;
-  for (int c0 = 0; c0 < nb; c0 += kScanThreads) {
-    int i = c0 + threadIdx.x;
-    uint32_t v = (i < nb) ? sums[i] : 0u, tot;
-    uint32_t ex = block_excl_scan(v, s_warp, tot);
-    if (i < nb) sums[i] = carry + ex;
-    carry += tot;
-  }
-  if (threadIdx.x == 0 && total_out) *total_out = carry;
-}
-
-__global__ void __launch_bounds__(kScanThreads)
-k_scan_add(uint32_t *__restrict__ data, int64_t n, const uint32_t *__restrict__ sums) {
-  int64_t base = blockIdx.x * (int64_t)kScanTile + threadIdx.x * kScanItems;
-  uint32_t add = sums[blockIdx.x];
-  for (int k = 0; k < kScanItems; ++k)
-    if (base + k < n) data[base + k] += add;
-}
-
-int exclusive_scan(Ctx *c, uint32_t *data, int64_t n, uint32_t *total_out) {
-  if (n <= 0) return GRAVITY_OK;
-  int nb = (int)((n + kScanTile - 1) / kScanTile);
-  k_scan_tiles<<<nb, kScanThreads, 0, c->stream>>>(data, n, c->t.scan_aux);
-  ++c->launches;
-  k_scan_sums<<<1, kScanThreads, 0, c->stream>>>(c->t.scan_aux, nb, total_out);
-  ++c->launches;
-  if (nb > 1) { k_scan_add<<<nb, kScanThreads, 0, c->stream>>>(data, n, c->t.scan_aux); ++c->launches; }
-  return cuda_status(cudaGetLastError());
-}
-
 // ------------------------------------------------------------------ a3: radix sort
 // Stable LSD radix sort of (key, index) pairs, 8 passes of 8-bit digits (then, with
 // several clouds, passes over the cloud id), one kernel per pass ("one sweep"):
@@ -347,7 +266,7 @@ k_rs_sweep(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
            uint64_t *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n, int shift,
            const int32_t *__restrict__ seg_of, const uint32_t *__restrict__ ghist,
            uint32_t *__restrict__ status, unsigned *__restrict__ tile_counter, int ntiles,
-           unsigned *err, int spin_budget, int withhold_first) {
+           unsigned *err, int spin_budget) {
   constexpr int W = kRsThreads / 32;
   __shared__ uint32_t s_w[W][256];      // per-warp digit counts, then exclusive bases
   __shared__ int32_t s_off[256];        // global position of the tile's local position 0, per digit
@@ -401,9 +320,9 @@ k_rs_sweep(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
   }
   const uint32_t count = run;
   volatile uint32_t *st = status + (int64_t)tile * 256 + tid;
-  // (failure testing: with withhold_first the first tile publishes nothing, so the next
-  // tile's look-back waits on a flag that is never set until its budget runs out)
-  if (tile > 0 || !withhold_first) *st = (tile == 0 ? kRsFlagPre : kRsFlagAgg) | count;
+  // (failure testing: a negative budget -k makes the first tile publish nothing, so the
+  // next tile's look-back waits on a flag that is never set until its k polls run out)
+  if (tile > 0 || spin_budget > 0) *st = (tile == 0 ? kRsFlagPre : kRsFlagAgg) | count;
   // look back kRsLook tiles per round (independent loads), nearest first
   uint32_t excl = 0;
   int spin = 0;                               // one bounded budget for the whole look-back
@@ -418,7 +337,7 @@ k_rs_sweep(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
     for (int k = 0; k < kRsLook; ++k) {
       if (found) break;
       const volatile uint32_t *sj = status + (int64_t)(j0 - k) * 256 + tid;
-      while ((v[k] >> 30) == 0 && ++spin < spin_budget) v[k] = *sj;
+      while ((v[k] >> 30) == 0 && ++spin < abs(spin_budget)) v[k] = *sj;
       if ((v[k] >> 30) == 0) { atomicOr(err, kErrTimeout); found = true; break; }
       excl += v[k] & kRsValue;
       found = (v[k] >> 30) == 2u;
@@ -461,7 +380,7 @@ k_rs_sweep(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
 // and tile states (257 * kRsMaxPasses + passes * tiles * 256 words).
 int radix_sort_buffers(Ctx *c, int64_t n, uint64_t *keys, uint64_t *keys_alt, uint32_t *idx,
                        uint32_t *idx_alt, uint32_t *hist, int cloud_passes,
-                       const int32_t *seg_of) {
+                       const int32_t *seg_of, int64_t extra_zero_words) {
   const int ntiles = (int)((n + kRsTile - 1) / kRsTile);
   uint64_t *ka = keys, *kb = keys_alt;
   uint32_t *va = idx, *vb = idx_alt;
@@ -472,7 +391,8 @@ int radix_sort_buffers(Ctx *c, int64_t n, uint64_t *keys, uint64_t *keys_alt, ui
   uint32_t *status = counters + kRsMaxPasses;
   GRAV_CUDA_TRY(cudaMemsetAsync(hist, 0,
                                 sizeof(uint32_t) * ((size_t)(256 + 1) * kRsMaxPasses +
-                                                    (size_t)np * ntiles * 256), c->stream));
+                                                    (size_t)np * ntiles * 256 +
+                                                    (size_t)extra_zero_words), c->stream));
   int cb = (int)((n + kRsThreads - 1) / kRsThreads);
   if (cb > 2 * c->num_sms) cb = 2 * c->num_sms;
   k_rs_count<<<cb, kRsThreads, 0, c->stream>>>(keys, n, 8, cloud_passes, seg_of, ghist, vb);
@@ -485,8 +405,7 @@ int radix_sort_buffers(Ctx *c, int64_t n, uint64_t *keys, uint64_t *keys_alt, ui
                                                      ghist + 256 * pass,
                                                      status + (int64_t)pass * ntiles * 256,
                                                      counters + pass, ntiles, c->d_status,
-                                                     c->sort_stall > 0 ? c->sort_stall : kRsSpin,
-                                                     c->sort_stall > 0 ? 1 : 0);
+                                                     c->sort_stall > 0 ? -c->sort_stall : kRsSpin);
     ++c->launches;
     uint64_t *tk = ka; ka = kb; kb = tk;
     uint32_t *tv = va; va = vb; vb = tv;
@@ -498,11 +417,20 @@ int radix_sort_buffers(Ctx *c, int64_t n, uint64_t *keys, uint64_t *keys_alt, ui
   return cuda_status(cudaGetLastError());
 }
 
+// The octree scan's tile counter and tile states sit in the sort's count buffer right after
+// the sort's own words, so the sort's clearing memset clears them too.
+int64_t oct_scan_words(int64_t n) { return (n + kOctTile - 1) / kOctTile + 1; }
+uint32_t *oct_scan_state(Ctx *c, int64_t n) {
+  const int np = 8 + (c->seg.nseg > 1 ? (c->seg.cbits + 7) / 8 : 0);
+  const int64_t ntiles = (n + kRsTile - 1) / kRsTile;
+  return c->t.hist + (int64_t)(256 + 1) * kRsMaxPasses + (int64_t)np * ntiles * 256;
+}
+
 int radix_sort(Ctx *c, int64_t n) {
   Tree &t = c->t;
   const int cloud_passes = c->seg.nseg > 1 ? (c->seg.cbits + 7) / 8 : 0;
   return radix_sort_buffers(c, n, t.keys, t.keys_alt, t.idx, t.idx_alt, t.hist, cloud_passes,
-                            c->seg.seg_of);
+                            c->seg.seg_of, oct_scan_words(n));
 }
 
 // Launch of k_bbox over one cloud of n bodies (grid a multiple of 3, see k_bbox).
@@ -636,31 +564,123 @@ __device__ __forceinline__ int cdepth(int plen, int cbits) {
   return plen < cbits ? -1 : cap_depth(plen - cbits);
 }
 
-__global__ void k_oct_count(int n, int leaf_max, int cbits, const int32_t *__restrict__ child,
-                            const int32_t *__restrict__ parent, const int32_t *__restrict__ first,
-                            const int32_t *__restrict__ last, const int32_t *__restrict__ plen,
-                            uint32_t *__restrict__ nchild, unsigned *status) {
-  int X = blockIdx.x * blockDim.x + threadIdx.x;
-  if (X >= n - 1) return;
+// Children count of every binary node (0 unless it is an internal octree cell), fused with
+// the exclusive scan that gives each cell the first octree id of its children: each block
+// claims the next tile of kOctTile binary nodes in order (kOctItems per thread), scans it,
+// publishes its total, and its first warp finds the sum of the earlier tiles by a decoupled
+// look-back, 32 predecessors per round (a bounded wait on tiles not yet published: those
+// were claimed earlier by running blocks, which publish before they wait themselves).  The
+// last tile writes the grand total (octree nodes below the cloud roots).
+constexpr uint32_t kOsAgg = 1u << 30, kOsPre = 2u << 30, kOsValue = (1u << 30) - 1;
+constexpr int kOsSpin = 1 << 22;
+
+__device__ __forceinline__ uint32_t oct_children(int X, int n, int leaf_max, int cbits,
+                                                 const int32_t *__restrict__ child,
+                                                 const int32_t *__restrict__ parent,
+                                                 const int32_t *__restrict__ first,
+                                                 const int32_t *__restrict__ last,
+                                                 const int32_t *__restrict__ plen,
+                                                 unsigned *status) {
   const int px = plen[X];
-  if (px < cbits) { nchild[X] = 0; return; }           // connector between clouds
-  const int d = cdepth(px, cbits);
   const int P = parent[X];
   if (P >= n - 1) {                                     // only after a failed sort pass
     latch_error(status, kErrTree);
-    nchild[X] = 0;
-    return;
+    return 0;
   }
+  if (px < cbits) return 0;                             // connector between clouds
+  const int d = cdepth(px, cbits);
   const bool cell = P < 0 || plen[P] < cbits || cdepth(plen[P], cbits) < d;
-  const int cnt = last[X] - first[X] + 1;
-  if (!(cell && cnt > leaf_max && d < kLevels)) { nchild[X] = 0; return; }
+  const int count = last[X] - first[X] + 1;
+  if (!(cell && count > leaf_max && d < kLevels)) return 0;
   Frontier f;
   if (!frontier(child, plen, X, cbits + 3 * (d + 1), f) || f.count < 2) {
     latch_error(status, kErrTree);
-    nchild[X] = 0;
-    return;
+    return 0;
   }
-  nchild[X] = (uint32_t)f.count;
+  return (uint32_t)f.count;
+}
+
+__global__ void __launch_bounds__(kOctThreads)
+k_oct_count(int n, int leaf_max, int cbits, const int32_t *__restrict__ child,
+            const int32_t *__restrict__ parent, const int32_t *__restrict__ first,
+            const int32_t *__restrict__ last, const int32_t *__restrict__ plen,
+            uint32_t *__restrict__ nchild, uint32_t *__restrict__ base, uint32_t *__restrict__ total,
+            uint32_t *__restrict__ tstate, unsigned *__restrict__ tile_counter, int ntiles,
+            unsigned *status) {
+  __shared__ int s_tile;
+  __shared__ uint32_t s_warp[kOctThreads / 32];
+  __shared__ uint32_t s_excl;
+  if (threadIdx.x == 0) s_tile = (int)atomicAdd(tile_counter, 1u);
+  __syncthreads();
+  const int tile = s_tile;
+  if (tile >= ntiles) return;
+  const int X0 = tile * kOctTile + threadIdx.x * kOctItems;   // kOctItems consecutive nodes
+  uint32_t cnt[kOctItems], sum = 0;
+#pragma unroll
+  for (int k = 0; k < kOctItems; ++k) {
+    const int X = X0 + k;
+    cnt[k] = X < n - 1 ? oct_children(X, n, leaf_max, cbits, child, parent, first, last, plen,
+                                      status) : 0u;
+    if (X < n - 1) nchild[X] = cnt[k];
+    sum += cnt[k];
+  }
+  // block-wide exclusive scan of the threads' sums
+  const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t inc = sum;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (l >= o) inc += t;
+  }
+  if (l == 31) s_warp[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t r = 0;
+    if (l == 0) {
+      for (int ww = 0; ww < kOctThreads / 32; ++ww) { const uint32_t t = s_warp[ww]; s_warp[ww] = r; r += t; }
+      *(volatile uint32_t *)(tstate + tile) = (tile == 0 ? kOsPre : kOsAgg) | r;
+    }
+    r = __shfl_sync(0xffffffffu, r, 0);
+    // look back 32 tiles per round: lane j reads tile j0 - j
+    uint32_t excl = 0;
+    int spin = 0;
+    bool done = tile == 0;
+    for (int j0 = tile - 1; !done; j0 -= 32) {
+      const int j = j0 - l;
+      uint32_t v = j >= 0 ? *(const volatile uint32_t *)(tstate + j) : kOsPre;
+      // the nearest predecessor with a prefix; wait until every nearer one has published
+      for (;;) {
+        const unsigned pre = __ballot_sync(0xffffffffu, (v >> 30) == 2u);
+        const int lim = pre ? __ffs(pre) - 1 : 31;      // lanes 0 .. lim are needed
+        const bool miss = l <= lim && (v >> 30) == 0u;
+        if (!__any_sync(0xffffffffu, miss)) {
+          uint32_t add = l <= lim ? (v & kOsValue) : 0u;
+          for (int o = 16; o > 0; o >>= 1) add += __shfl_xor_sync(0xffffffffu, add, o);
+          excl += add;
+          done = pre != 0u;
+          break;
+        }
+        if (++spin >= kOsSpin) {
+          if (l == 0) latch_error(status, kErrTimeout);
+          done = true;
+          break;
+        }
+        if (miss) v = *(const volatile uint32_t *)(tstate + j);
+      }
+    }
+    if (l == 0) {
+      if (tile > 0) *(volatile uint32_t *)(tstate + tile) = kOsPre | (excl + r);
+      if (tile == ntiles - 1) *total = excl + r;
+      s_excl = excl;
+    }
+  }
+  __syncthreads();
+  uint32_t pre = s_excl + s_warp[w] + inc - sum;
+#pragma unroll
+  for (int k = 0; k < kOctItems; ++k) {
+    const int X = X0 + k;
+    if (X < n - 1) base[X] = pre;
+    pre += cnt[k];
+  }
 }
 
 struct OctWriteArgs {
@@ -1035,16 +1055,16 @@ int tree_build(Ctx *c, int64_t n, const double *pos, const double *mass) {
                                                      t.bplen);
     ++c->launches;
     // a6: octree
-    k_oct_count<<<blocks_for(ni, 256), 256, 0, s>>>((int)n, leaf_max, kv.cbits, t.bchild, t.bparent,
-                                                    t.bfirst, t.blast, t.bplen, t.bnchild,
-                                                    c->d_status);
-    ++c->launches;
+    // a6: octree children counts and their exclusive scan (one launch; tile states zeroed
+    // with the sort's counters)
     uint32_t *base = t.bbase;
-    GRAV_CUDA_TRY(cudaMemcpyAsync(base, t.bnchild, sizeof(uint32_t) * ni,
-                                  cudaMemcpyDeviceToDevice, s));
     uint32_t *total = t.scalars;             // number of octree nodes below the cloud roots
-    rc = exclusive_scan(c, base, ni, total);
-    if (rc) return rc;
+    uint32_t *oct_state = oct_scan_state(c, n);
+    const int otiles = (int)((ni + kOctTile - 1) / kOctTile);
+    k_oct_count<<<otiles, kOctThreads, 0, s>>>((int)n, leaf_max, kv.cbits, t.bchild, t.bparent,
+                                            t.bfirst, t.blast, t.bplen, t.bnchild, base, total,
+                                            oct_state + 1, oct_state, otiles, c->d_status);
+    ++c->launches;
     OctWriteArgs W{(int)n, leaf_max, kv.cbits, sg.nseg, cap_nodes, t.bchild, t.bfirst, t.blast,
                    t.bplen, kv.seg, t.bnchild, base, total, t.topo, t.ndepth, t.nnodes,
                    c->d_status};
@@ -1080,14 +1100,15 @@ int tree_build(Ctx *c, int64_t n, const double *pos, const double *mass) {
 // (sorted position -> caller index).
 int64_t radix_hist_words(int64_t n) {
   const int64_t ntiles = (n + kRsTile - 1) / kRsTile;
-  return (int64_t)257 * kRsMaxPasses + (int64_t)kRsMaxPasses * 256 * ntiles;
+  return (int64_t)257 * kRsMaxPasses + (int64_t)kRsMaxPasses * 256 * ntiles +
+         (n + kOctTile - 1) / kOctTile + 2;    // + the octree scan's tile counter and states
 }
 
 int morton_order(Ctx *c, int64_t n, const double *pos, const MortonBuffers &b) {
   launch_bbox(c, pos, n, b.part, b.ticket, b.geom);
   k_keys<<<blocks_for(n, 256), 256, 0, c->stream>>>(pos, n, b.geom, nullptr, b.keys, b.idx);
   ++c->launches;
-  return radix_sort_buffers(c, n, b.keys, b.keys_alt, b.idx, b.idx_alt, b.hist, 0, nullptr);
+  return radix_sort_buffers(c, n, b.keys, b.keys_alt, b.idx, b.idx_alt, b.hist, 0, nullptr, 0);
 }
 
 }  // namespace grav
