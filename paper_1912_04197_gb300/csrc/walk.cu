@@ -410,39 +410,56 @@ __device__ __forceinline__ void flush_vjp(WarpSmemV &V, int cnt, int lane, float
                                           float yr, float zr, float eps2, float ux, float uy,
                                           float uz, int gi, float &px, float &py, float &pz,
                                           double *g_body, double *g_node) {
-  const WarpSmem &S = V.base;
-  px = py = pz = 0.f;
+  WarpSmem &S = V.base;
+  if (cnt & 1) {                                  // pad entry: mask 0, finite fields
+    if (lane == 0) {
+      const int j = cnt >> 1;
+      if (FAR) { zero_b(S.fA[j]); zero_b(S.fB[j]); S.fM[j].y = 0u; }
+      else { zero_b(S.pA[j]); zero_b(S.pB[j]); zero_b(S.pC[j]); zero_b(S.pD[j]); }
+    }
+    __syncwarp();
+  }
+  const unsigned lbit = 1u << lane;
+  const float2 e2 = dup2(eps2), u_x = dup2(ux), u_y = dup2(uy), u_z = dup2(uz), m3 = dup2(-3.f);
+  const float2 nxh = dup2(FAR ? -xr : -xh), nyh = dup2(FAR ? -yr : -yh), nzh = dup2(FAR ? -zr : -zh);
+  const float2 nxl = dup2(-xl), nyl = dup2(-yl), nzl = dup2(-zl);
+  float2 ox = dup2(0.f), oy = dup2(0.f), oz = dup2(0.f);
   for (int c0 = 0; c0 < cnt; c0 += kVjpChunk) {
     const int ce = min(kVjpChunk, cnt - c0);
 #pragma unroll
-    for (int e = 0; e < kVjpChunk; ++e) {
-      if (e < ce) {
-        const int k = c0 + e;
-        float dx, dy, dz, m;
-        bool act;
+    for (int q = 0; q < kVjpChunk / 2; ++q) {
+      if (2 * q < ce) {
+        const int j = (c0 >> 1) + q;
+        float2 dx, dy, dz, m;
+        unsigned ma, mb;
         if (FAR) {
-          act = (reinterpret_cast<const unsigned *>(S.fM)[k] >> lane) & 1u;
-          dx = getf(S.fA, k, 0) - xr; dy = getf(S.fA, k, 1) - yr; dz = getf(S.fB, k, 0) - zr;
-          m = getf(S.fB, k, 1);
+          const float4 A = S.fA[j], B = S.fB[j];
+          const uint2 mk = S.fM[j];
+          dx = add2(xy2(A), nxh); dy = add2(zw2(A), nyh); dz = add2(xy2(B), nzh);
+          m = zw2(B);
+          ma = mk.x; mb = mk.y;
         } else {
-          act = ((__float_as_uint(getf(S.pD, k, 1)) >> lane) & 1u) && S.ltag[k] != gi;
-          dx = (getf(S.pA, k, 0) - xh) + (getf(S.pC, k, 0) - xl);
-          dy = (getf(S.pA, k, 1) - yh) + (getf(S.pC, k, 1) - yl);
-          dz = (getf(S.pB, k, 0) - zh) + (getf(S.pD, k, 0) - zl);
-          m = getf(S.pB, k, 1);
+          const float4 A = S.pA[j], B = S.pB[j], C = S.pC[j], D = S.pD[j];
+          dx = add2(add2(xy2(A), nxh), add2(xy2(C), nxl));
+          dy = add2(add2(zw2(A), nyh), add2(zw2(C), nyl));
+          dz = add2(add2(xy2(B), nzh), add2(xy2(D), nzl));
+          m = zw2(B);
+          ma = __float_as_uint(D.z); mb = __float_as_uint(D.w);
+          if (S.ltag[2 * j] == gi) ma = 0u;       // the body's own entry: no dependence
+          if (2 * j + 1 < cnt && S.ltag[2 * j + 1] == gi) mb = 0u;
         }
-        const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
-        const float inv = inv_r<EPS0>(r2, act);
-        const float inv2 = inv * inv;
-        const float s = m * (inv2 * inv);
-        const float c3 = 3.f * fmaf(dx, ux, fmaf(dy, uy, dz * uz)) * inv2;
-        const float wx = s * fmaf(-c3, dx, ux);
-        const float wy = s * fmaf(-c3, dy, uy);
-        const float wz = s * fmaf(-c3, dz, uz);
-        px += wx; py += wy; pz += wz;
-        V.vt[0][e][lane] = wx;
-        V.vt[1][e][lane] = wy;
-        V.vt[2][e][lane] = wz;
+        const float2 r2 = fma2(dz, dz, fma2(dy, dy, fma2(dx, dx, e2)));
+        const float2 inv = inv_r2<EPS0>(r2, ma, mb, lbit);
+        const float2 inv2 = mul2(inv, inv);
+        const float2 sc = mul2(m, mul2(inv2, inv));
+        const float2 c3n = mul2(mul2(m3, fma2(dx, u_x, fma2(dy, u_y, mul2(dz, u_z)))), inv2);
+        const float2 wx = mul2(sc, fma2(c3n, dx, u_x));
+        const float2 wy = mul2(sc, fma2(c3n, dy, u_y));
+        const float2 wz = mul2(sc, fma2(c3n, dz, u_z));
+        ox = add2(ox, wx); oy = add2(oy, wy); oz = add2(oz, wz);
+        V.vt[0][2 * q][lane] = wx.x; V.vt[0][2 * q + 1][lane] = wx.y;
+        V.vt[1][2 * q][lane] = wy.x; V.vt[1][2 * q + 1][lane] = wy.y;
+        V.vt[2][2 * q][lane] = wz.x; V.vt[2][2 * q + 1][lane] = wz.y;
       }
     }
     __syncwarp();
@@ -450,7 +467,7 @@ __device__ __forceinline__ void flush_vjp(WarpSmemV &V, int cnt, int lane, float
     if (comp < 3 && e < ce) {
       float sum = 0.f;
 #pragma unroll 8
-      for (int j = 0; j < 32; ++j) sum += V.vt[comp][e][j];
+      for (int jj = 0; jj < 32; ++jj) sum += V.vt[comp][e][jj];
       if (sum != 0.f) {
         const int tag = FAR ? V.ftag[c0 + e] : S.ltag[c0 + e];
         double *dst = (!FAR && tag >= 0) ? g_body + 3 * (int64_t)tag
@@ -460,6 +477,9 @@ __device__ __forceinline__ void flush_vjp(WarpSmemV &V, int cnt, int lane, float
     }
     __syncwarp();
   }
+  px = ox.x + ox.y;
+  py = oy.x + oy.y;
+  pz = oz.x + oz.y;
 }
 
 // Counted variant only: lockstep iteration counts of lane-group-split lists (masks in
@@ -504,11 +524,11 @@ struct Stack {
   }
 };
 
-// Force and VJP modes are held to 6 (quadrupole: 80 registers; the shared memory of its
-// lists allows no more) or 7 (monopole: 72 registers) resident blocks of 4 warps per SM;
-// the counted mode is not held to either.
+// The force mode is held to 6 (quadrupole: 80 registers; the shared memory of its lists
+// allows no more) or 7 (monopole: 72 registers) resident blocks of 4 warps per SM, the VJP
+// mode to 6 (80 registers); the counted mode is not held to any.
 template <int ORDER, bool EPS0, int MODE>
-__global__ void __launch_bounds__(32 * kWalkWarps, MODE == kModeCount ? 1 : (ORDER == 2 ? 6 : 7))
+__global__ void __launch_bounds__(32 * kWalkWarps, MODE == kModeCount ? 1 : (ORDER == 2 || MODE == kModeVjp ? 6 : 7))
 k_walk(WalkArgs A) {
   constexpr bool COUNT = MODE == kModeCount;
   constexpr bool VJP = MODE == kModeVjp;
