@@ -73,11 +73,17 @@ typedef struct gravity_params {
   int32_t use_graph;   /* leapfrog_step with nsteps > 2 on a non-default stream: 1 (default)
                           = capture one step as a CUDA graph and replay it, 0 = launch
                           every kernel of every step */
-  int32_t reserved;
+  int32_t grav_every;  /* leapfrog_step only: evaluate gravity every grav_every-th step and hold
+                          the last acceleration in between (the two time steps of Sec. 4.1:
+                          a stepper at the contact step dt with gravity every Delta t_g, Eq.
+                          (dt_g), i.e. grav_every = ceil(Delta t_g / dt)); 0 or 1 = every step
+                          (default 1).  The context counts steps since gravity was last
+                          evaluated across calls; gravity_tree_build and gravity_forces reset
+                          the count (the acceleration passed in acc_cache counts as fresh). */
 } gravity_params;
 
 /* Fill *p with the defaults: G = 1, order 0, leaf_max 1, accum 0, mac_guard 1,
- * scheme 0, walk_cfg -1, use_graph 1. */
+ * scheme 0, walk_cfg -1, use_graph 1, grav_every 1. */
 void gravity_params_default(gravity_params *p);
 
 /* Create a context on CUDA device `device` whose work goes to `cuda_stream`

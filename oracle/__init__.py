@@ -78,7 +78,7 @@ def _load():
             lib.orc_tree_forces_frozen.restype = I
             lib.orc_direct.argtypes = [I64, P, P, D, D, I64, P, P, P]
             lib.orc_direct.restype = None
-            lib.orc_leapfrog.argtypes = [I64, P, P, P, P, D, I, I, I, D, D, D, I, I, I]
+            lib.orc_leapfrog.argtypes = [I64, P, P, P, P, D, I, I, I, D, D, D, I, I, I, I]
             lib.orc_leapfrog.restype = I
             lib.orc_diagnostics.argtypes = [I64, P, P, P, D, D, P]
             lib.orc_diagnostics.restype = None
@@ -255,8 +255,10 @@ def tree_forces(pos, mass, theta, eps, G=1.0, leaf_max=1, order=0, mac_guard=1):
 
 
 def step(pos, vel, mass, acc, dt, nsteps, *, scheme=0, use_tree=True, theta=0.5, eps=0.0,
-         G=1.0, leaf_max=1, order=0, mac_guard=1):
-    """Symplectic stepping (Sec. 2.3): scheme 0 = KDK leapfrog, 1 = semi-implicit Euler.
+         G=1.0, leaf_max=1, order=0, mac_guard=1, grav_every=1):
+    """Symplectic stepping (Sec. 2.3): scheme 0 = KDK leapfrog, 1 = semi-implicit Euler;
+    with grav_every = k > 1, gravity is evaluated only every k-th step and held in between
+    (the two time steps of Sec. 4.1).
 
     Returns new (pos, vel, acc); inputs are not modified."""
     pos = _f64(pos, 3).reshape(-1, 3).copy()
@@ -265,7 +267,8 @@ def step(pos, vel, mass, acc, dt, nsteps, *, scheme=0, use_tree=True, theta=0.5,
     acc = _f64(acc, 3).reshape(-1, 3).copy()
     rc = _load().orc_leapfrog(len(pos), _ptr(pos), _ptr(vel), _ptr(mass), _ptr(acc), float(dt),
                               int(nsteps), int(scheme), int(bool(use_tree)), float(theta),
-                              float(eps), float(G), int(leaf_max), int(order), int(mac_guard))
+                              float(eps), float(G), int(leaf_max), int(order), int(mac_guard),
+                              int(grav_every))
     if rc:
         raise OracleError(rc)
     return pos, vel, acc

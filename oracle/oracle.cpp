@@ -626,15 +626,25 @@ static int forces_all(int64_t n, const double *pos, const double *mass, int use_
 //   v += dt/2 a(x); x += dt v; a = a(x) (tree rebuilt every step); v += dt/2 a.
 // scheme 1 = semi-implicit Euler: v += dt a(x); x += dt v; a = a(x).
 // acc holds a(x) on entry and on exit.
+// Two time steps (Sec. 4.1): the stepper advances by the contact step dt, gravity is
+// evaluated only every grav_every-th step (about Delta t_g / Delta t_c, Eq. dt_g bounds
+// Delta t_g) and the last evaluated acceleration is used in between; grav_every <= 1
+// evaluates it every step.  The count starts at the call.
 int orc_leapfrog(int64_t n, double *pos, double *vel, const double *mass, double *acc,
                  double dt, int nsteps, int scheme, int use_tree, double theta, double eps,
-                 double G, int leaf_max, int order, int mac_guard) {
+                 double G, int leaf_max, int order, int mac_guard, int grav_every) {
+  const int every = grav_every > 1 ? grav_every : 1;
+  int since = 0;                        // steps since gravity was last evaluated
   for (int s = 0; s < nsteps; ++s) {
     const double h = scheme == 0 ? 0.5 * dt : dt;
     for (int64_t i = 0; i < 3 * n; ++i) vel[i] = vel[i] + h * acc[i];
     for (int64_t i = 0; i < 3 * n; ++i) pos[i] = pos[i] + dt * vel[i];
-    int rc = forces_all(n, pos, mass, use_tree, theta, eps, G, leaf_max, order, mac_guard, acc);
-    if (rc != ORC_OK) return rc;
+    since = since + 1;
+    if (since == every) {
+      int rc = forces_all(n, pos, mass, use_tree, theta, eps, G, leaf_max, order, mac_guard, acc);
+      if (rc != ORC_OK) return rc;
+      since = 0;
+    }
     if (scheme == 0)
       for (int64_t i = 0; i < 3 * n; ++i) vel[i] = vel[i] + h * acc[i];
   }

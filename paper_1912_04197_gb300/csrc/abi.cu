@@ -94,6 +94,7 @@ int check_params(const gravity_params *p) {
   if (p->mac_guard != 0 && p->mac_guard != 1) return GRAVITY_E_ARG;
   if (p->scheme != 0 && p->scheme != 1) return GRAVITY_E_ARG;
   if (p->use_graph != 0 && p->use_graph != 1) return GRAVITY_E_ARG;
+  if (p->grav_every < 0) return GRAVITY_E_ARG;
   return GRAVITY_OK;
 }
 
@@ -324,6 +325,7 @@ void gravity_params_default(gravity_params *p) {
   p->scheme = 0;
   p->walk_cfg = -1;
   p->use_graph = 1;
+  p->grav_every = 1;
 }
 
 int gravity_create(gravity_ctx **out, int device, void *cuda_stream) {
@@ -419,6 +421,7 @@ int gravity_tree_build(gravity_ctx *h, int64_t n, const double *pos, const doubl
   if (c.seg.nseg > 1 && n != c.seg.n) return GRAVITY_E_ARG;
   if (p) c.params = *p; else gravity_params_default(&c.params);
   c.have_tree = false;
+  c.grav_since = 0;
   c.n = n;
   if (n == 0) { c.have_tree = true; return GRAVITY_OK; }
   if ((rc = grav::set_device(c))) return rc;
@@ -438,6 +441,7 @@ static int forces_common(gravity_ctx *h, double theta, double eps, double *acc, 
   if (!acc) return GRAVITY_E_ARG;
   int rc = grav::set_device(c);
   if (rc) return rc;
+  c.grav_since = 0;
   return grav::walk_forces(&c, theta, eps, acc, counts, nullptr, 0.0);
 }
 
@@ -622,6 +626,27 @@ int leapfrog_step(gravity_ctx *h, int64_t n, double *pos, double *vel, const dou
   auto one_step = [&]() -> int {
     return grav::integrate_one(c, n, pos, vel, mass, acc_cache, dt, theta, eps);
   };
+  if (c.params.grav_every > 1) {
+    // two time steps (Sec. 4.1): kick-drift every step, gravity (build + walk, with the
+    // closing kick fused for KDK) every grav_every-th step, the held acceleration in between
+    const bool kdk = c.params.scheme == 0;
+    const double hk = kdk ? 0.5 * dt : dt;
+    for (int s = 0; s < nsteps; ++s) {
+      if ((rc = grav::launch_kick_drift(&c, n, pos, vel, acc_cache, hk, dt))) return rc;
+      if (++c.grav_since >= c.params.grav_every) {
+        c.grav_since = 0;
+        c.n = n;
+        if ((rc = grav::tree_build(&c, n, pos, mass))) return rc;
+        c.have_tree = true;
+        if ((rc = grav::walk_forces(&c, theta, eps, acc_cache, nullptr, kdk ? vel : nullptr,
+                                    kdk ? hk : 0.0)))
+          return rc;
+      } else if (kdk && (rc = grav::launch_kick(&c, n, vel, acc_cache, hk))) {
+        return rc;
+      }
+    }
+    return GRAVITY_OK;
+  }
   // The first step runs eagerly (it sizes every buffer); later steps replay a
   // CUDA graph of one step captured on the caller's stream when graphs are enabled.
   grav::StepGraph &g = c.graph;
@@ -677,7 +702,7 @@ int leapfrog_adjoint(gravity_ctx *h, int64_t n, const double *pos0, const double
   if (rc) return rc;
   gravity_params q;
   if (p) q = *p; else gravity_params_default(&q);
-  if (q.order != 0 || q.scheme != 0) return GRAVITY_E_ARG;
+  if (q.order != 0 || q.scheme != 0 || q.grav_every > 1) return GRAVITY_E_ARG;
   if (n == 0) return GRAVITY_OK;
   if (!pos0 || !vel0 || !mass || !xbar || !vbar) return GRAVITY_E_ARG;
   Ctx &c = h->c;

@@ -97,6 +97,7 @@ struct Ctx {
   void *alloc_user = nullptr;
   int stack_cap = 0;           // walk stack entries allowed (0 = all); failure testing
   int sort_stall = 0;          // > 0: sort passes withhold tile 0, look-back budget (testing)
+  int grav_since = 0;          // leapfrog_step with grav_every > 1: steps since the last force
   cudaStream_t stream = nullptr;
   int num_sms = 0;
   int64_t cap = 0;             // body capacity of the buffers

@@ -47,7 +47,7 @@ class gravity_params(ctypes.Structure):
     _fields_ = [("G", ctypes.c_double), ("order", ctypes.c_int32), ("leaf_max", ctypes.c_int32),
                 ("accum", ctypes.c_int32), ("mac_guard", ctypes.c_int32),
                 ("scheme", ctypes.c_int32), ("walk_cfg", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("grav_every", ctypes.c_int32)]
 
 
 def _load() -> ctypes.CDLL:

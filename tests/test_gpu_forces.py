@@ -235,3 +235,40 @@ def test_opening_band_on_a_lattice(gpu, mac_guard):
     assert np.array_equal(c[:, 0], ocnt[:, 1]) and np.array_equal(c[:, 1], ocnt[:, 2])
     assert np.array_equal(c[:, 2], ocnt[:, 0])
     _check(acc.cpu().numpy(), ref, absum, f"tree/lattice_band/guard{mac_guard}")
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_two_time_steps_vs_oracle(gpu, scheme):
+    # Sec. 4.1: the stepper advances by the contact step dt and gravity is evaluated every
+    # grav_every-th step (Delta t_g = grav_every dt, bounded by Eq. dt_g), held in between;
+    # against the oracle's run with the same schedule, and the count carries across calls
+    pos, vel, m = inputs.rubble_pile(3000, seed=16)
+    eps, dt, theta, k, steps = 5e-3, 1e-3, 0.5, 4, 12
+    ref0 = oracle.tree_forces(pos, m, theta, eps, leaf_max=1, order=2)
+    out = []
+    for split in ((steps,), (5, 7)):
+        ctx = gpu.Context(0)
+        P = torch.tensor(pos, device="cuda")
+        V = torch.tensor(vel, device="cuda")
+        M = torch.tensor(m, device="cuda")
+        A = torch.tensor(ref0, device="cuda")
+        p = gpu.params(order=2, scheme=scheme, grav_every=k)
+        for ns in split:
+            gpu.leapfrog_step(ctx, P, V, M, A, dt, ns, theta, eps, p)
+        gpu.gravity_sync(ctx)
+        out.append((P.cpu().numpy(), V.cpu().numpy(), A.cpu().numpy()))
+    for x, y in zip(*out):
+        assert np.array_equal(x, y)
+    op, ov, oa = oracle.step(pos, vel, m, ref0, dt, steps, scheme=scheme, theta=theta, eps=eps,
+                             order=2, grav_every=k)
+    P, V, A = out[0]
+    assert np.abs(P - op).max() < 1e-9 and np.abs(V - ov).max() < 1e-6
+    # the last step evaluated gravity: the forces at the run's own final positions
+    ref, absum, _ = oracle.Tree(P, m, leaf_max=1, order=2).forces(theta, eps)
+    check_parity(A, ref, absum, f"two_time_steps/scheme{scheme}")
+    assert np.abs(A - oa).max() <= 1e-6 * np.abs(oa).max()
+    with pytest.raises(gpu.GravityError):
+        gpu.leapfrog_step(gpu.Context(0), torch.tensor(pos, device="cuda"),
+                          torch.tensor(vel, device="cuda"), torch.tensor(m, device="cuda"),
+                          torch.tensor(ref0, device="cuda"), dt, 1, theta, eps,
+                          gpu.params(grav_every=-1))

@@ -460,3 +460,37 @@ def test_diagnostics_two_body_closed_form():
     assert E == pytest.approx(0.5 * 2 * 1 + 0.5 * 0.5 * 4 - 2 * 0.5 / 5, rel=1e-15)
     assert P.tolist() == [2.0, -1.0, 0.0]
     assert L.tolist() == [0.0, 0.0, 0.5 * (3.0 * -2.0)]
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_two_time_steps_hold_gravity_between_evaluations(scheme):
+    # Sec. 4.1: the stepper advances by the contact step, gravity is evaluated every k-th
+    # step and held in between.  With the acceleration held at a0 for s < k steps, the
+    # steppers reduce to constant-acceleration motion with closed forms:
+    #   semi-implicit Euler: v_s = v0 + s dt a0, x_s = x0 + s dt v0 + dt^2 a0 s (s + 1) / 2
+    #   KDK leapfrog:        v_s = v0 + s dt a0, x_s = x0 + s dt v0 + dt^2 a0 s^2 / 2
+    # and at step k the acceleration is the force field at x_k (here the direct sum).
+    pos, vel, m = inputs.rubble_pile(300, seed=21)
+    eps, dt, k = 5e-3, 1e-3, 5
+    a0, _ = oracle.direct(pos, m, eps)
+    for s in range(1, k):
+        p, v, a = oracle.step(pos, vel, m, a0, dt, s, scheme=scheme, use_tree=False, eps=eps,
+                              grav_every=k)
+        quad = s * (s + 1) / 2 if scheme == 1 else s * s / 2
+        scale = np.abs(pos).max() + s * dt * np.abs(vel).max()
+        assert np.abs(v - (vel + s * dt * a0)).max() <= 1e-13 * (np.abs(vel).max() + 1)
+        assert np.abs(p - (pos + s * dt * vel + dt * dt * quad * a0)).max() <= 1e-14 * scale
+        assert np.array_equal(a, a0)                      # held, not re-evaluated
+    p, v, a = oracle.step(pos, vel, m, a0, dt, k, scheme=scheme, use_tree=False, eps=eps,
+                          grav_every=k)
+    assert np.array_equal(a, oracle.direct(p, m, eps)[0])   # evaluated at x_k
+    # k = 1 (and 0) is the single-rate stepper; a run of 2k steps is two runs of k steps
+    p1, v1, a1 = oracle.step(pos, vel, m, a0, dt, 7, scheme=scheme, use_tree=False, eps=eps)
+    for ge in (0, 1):
+        q = oracle.step(pos, vel, m, a0, dt, 7, scheme=scheme, use_tree=False, eps=eps,
+                        grav_every=ge)
+        assert all(np.array_equal(x, y) for x, y in zip(q, (p1, v1, a1)))
+    r1 = oracle.step(pos, vel, m, a0, dt, 2 * k, scheme=scheme, use_tree=False, eps=eps,
+                     grav_every=k)
+    r2 = oracle.step(p, v, m, a, dt, k, scheme=scheme, use_tree=False, eps=eps, grav_every=k)
+    assert all(np.array_equal(x, y) for x, y in zip(r1, r2))
