@@ -264,7 +264,8 @@ int gravity_direct(gravity_ctx *ctx, int64_t n, const double *pos, const double 
  *   cuda_stream     stream the two kernels are enqueued on (NULL = legacy default)
  * The first call on a device (with that device current) resolves the array's
  * device address with cudaGetSymbolAddress; make that first call before any stream
- * capture.  All calls on a device share the one array, which keeps the last call's
+ * capture.  The address is cached for the life of the process: a process that resets
+ * the device (cudaDeviceReset) must not call this entry point afterwards.  All calls on a device share the one array, which keeps the last call's
  * contents (every entry a call reads is written by that call first): calls that
  * overlap on the GPU (different streams, or different host threads) race and give
  * wrong results - serialise them. */

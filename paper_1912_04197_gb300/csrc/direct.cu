@@ -457,6 +457,8 @@ int diagnostics(Ctx *c, int64_t n, const double *pos, const double *vel, const d
 // instead of context-owned scratch, and it needs no context at all.
 #include <mutex>
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace grav {
 namespace {
 
@@ -470,8 +472,18 @@ constexpr int kNoAllocMaxDevices = 64;
 // cudaGetSymbolAddress, once per device.
 static __device__ __align__(256) float4 g_direct_scratch[2 * kNoAllocMaxBodies];
 
+// The device address of the array, resolved once per device.  It belongs to the device's
+// primary context: after a cudaDeviceReset the cached value is stale (the array's module
+// is loaded again in the new context), so this entry point is not for processes that
+// reset a device while using it.
 std::mutex g_noalloc_mu;
 float4 *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// A named range for a profiler's timeline, as around the context entry points.
+struct NoAllocRange {
+  NoAllocRange() { nvtxRangePushA("gravity_direct_noalloc"); }
+  ~NoAllocRange() { nvtxRangePop(); }
+};
 
 }  // namespace
 }  // namespace grav
@@ -479,6 +491,7 @@ float4 *g_noalloc_ptr[kNoAllocMaxDevices] = {};
 extern "C" int gravity_direct_noalloc(int64_t n, const double *pos, const double *mass,
                                       double eps, double G, double *acc, void *cuda_stream) {
   using namespace grav;
+  NoAllocRange range_;
   if (n < 0 || n > kNoAllocMaxBodies || !(eps >= 0.0) || !isfinite(eps) || !isfinite(G))
     return GRAVITY_E_ARG;
   if (n == 0) return GRAVITY_OK;
