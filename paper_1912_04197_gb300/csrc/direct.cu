@@ -40,65 +40,7 @@ __device__ __forceinline__ void two_sum_add(float &hi, float &lo, float p) {
 template <bool EPS0>
 __global__ void __launch_bounds__(kDirThreads)
 k_direct(const float4 *__restrict__ hi, const float4 *__restrict__ lo, int64_t n, float eps2,
-         double G, double *__restrict__ acc) {
-  __shared__ float4 sh[kDirThreads], sl[kDirThreads];
-  constexpr int P = kDirPerThread;
-  float xh[P], yh[P], zh[P], xl[P], yl[P], zl[P];
-  float ahx[P], ahy[P], ahz[P], alx[P], aly[P], alz[P];
-  int64_t i0 = (blockIdx.x * (int64_t)kDirThreads) * P + threadIdx.x;
-#pragma unroll
-  for (int p = 0; p < P; ++p) {
-    int64_t i = i0 + p * kDirThreads;
-    float4 h = i < n ? hi[i] : make_float4(0, 0, 0, 0);
-    float4 l = i < n ? lo[i] : make_float4(0, 0, 0, 0);
-    xh[p] = h.x; yh[p] = h.y; zh[p] = h.z; xl[p] = l.x; yl[p] = l.y; zl[p] = l.z;
-    ahx[p] = ahy[p] = ahz[p] = alx[p] = aly[p] = alz[p] = 0.f;
-  }
-  for (int64_t t0 = 0; t0 < n; t0 += kDirThreads) {
-    int64_t j = t0 + threadIdx.x;
-    sh[threadIdx.x] = j < n ? hi[j] : make_float4(0, 0, 0, 0);
-    sl[threadIdx.x] = j < n ? lo[j] : make_float4(0, 0, 0, 0);
-    __syncthreads();
-    float px[P], py[P], pz[P];
-#pragma unroll
-    for (int p = 0; p < P; ++p) px[p] = py[p] = pz[p] = 0.f;
-#pragma unroll 4
-    for (int k = 0; k < kDirThreads; ++k) {
-      const float4 a = sh[k], b = sl[k];
-#pragma unroll
-      for (int p = 0; p < P; ++p) {
-        float dx = (a.x - xh[p]) + (b.x - xl[p]);
-        float dy = (a.y - yh[p]) + (b.y - yl[p]);
-        float dz = (a.z - zh[p]) + (b.z - zl[p]);
-        float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
-        float inv = rsqrtf(r2);
-        // with eps > 0, r^2 >= eps^2 > 0 and the self pair (d = 0) adds m * 0;
-        // with eps = 0 a pair at r^2 = 0 must add nothing
-        if (EPS0) inv = r2 > 0.f ? inv : 0.f;
-        float s = a.w * (inv * inv * inv);
-        px[p] = fmaf(s, dx, px[p]);
-        py[p] = fmaf(s, dy, py[p]);
-        pz[p] = fmaf(s, dz, pz[p]);
-      }
-    }
-#pragma unroll
-    for (int p = 0; p < P; ++p) {
-      two_sum_add(ahx[p], alx[p], px[p]);
-      two_sum_add(ahy[p], aly[p], py[p]);
-      two_sum_add(ahz[p], alz[p], pz[p]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int p = 0; p < P; ++p) {
-    int64_t i = i0 + p * kDirThreads;
-    if (i < n) {
-      acc[3 * i] = G * ((double)ahx[p] + (double)alx[p]);
-      acc[3 * i + 1] = G * ((double)ahy[p] + (double)aly[p]);
-      acc[3 * i + 2] = G * ((double)ahz[p] + (double)alz[p]);
-    }
-  }
-}
+         double G, double *__restrict__ acc);
 
 // Sorted hi/lo bodies (Morton order) and the box of each 256-body tile (hi parts).
 __global__ void k_split_sorted(const double *__restrict__ pos, const double *__restrict__ mass,
@@ -144,21 +86,103 @@ k_tile_box(const float4 *__restrict__ hi, int64_t n, float4 *__restrict__ box) {
   }
 }
 
-// One block: 512 Morton-consecutive bodies (2 per thread) against every 256-body tile.
+// Packed two-wide FP32 arithmetic (sm_100+): one issue slot for the same operation on the
+// two bodies a thread holds; each half is the scalar IEEE operation, so the result equals
+// the one-body-at-a-time arithmetic bit for bit.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 xy2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 zw2(float4 v) { return make_float2(v.z, v.w); }
+
+// Caller order, hi/lo coordinates for every pair: each thread's two bodies (i0 and
+// i0 + 256) evaluated as one packed pair against every 256-body tile, sources staged
+// duplicated as in k_direct_sorted.
+template <bool EPS0>
+__global__ void __launch_bounds__(kDirThreads)
+k_direct(const float4 *__restrict__ hi, const float4 *__restrict__ lo, int64_t n, float eps2,
+         double G, double *__restrict__ acc) {
+  __shared__ float4 sA[kDirThreads], sB[kDirThreads], sC[kDirThreads], sD[kDirThreads];
+  static_assert(kDirPerThread == 2, "the two bodies of a thread form one packed pair");
+  const int64_t i0 = (blockIdx.x * (int64_t)kDirThreads) * 2 + threadIdx.x;
+  float nh[2][3], nl[2][3];
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    const int64_t i = i0 + p * kDirThreads;
+    const float4 h = i < n ? hi[i] : make_float4(0, 0, 0, 0);
+    const float4 l = i < n ? lo[i] : make_float4(0, 0, 0, 0);
+    nh[p][0] = -h.x; nh[p][1] = -h.y; nh[p][2] = -h.z;
+    nl[p][0] = -l.x; nl[p][1] = -l.y; nl[p][2] = -l.z;
+  }
+  const float2 nhx = make_float2(nh[0][0], nh[1][0]), nhy = make_float2(nh[0][1], nh[1][1]),
+               nhz = make_float2(nh[0][2], nh[1][2]);
+  const float2 nlx = make_float2(nl[0][0], nl[1][0]), nly = make_float2(nl[0][1], nl[1][1]),
+               nlz = make_float2(nl[0][2], nl[1][2]);
+  const float2 e2 = make_float2(eps2, eps2);
+  float ahx[2] = {0.f, 0.f}, ahy[2] = {0.f, 0.f}, ahz[2] = {0.f, 0.f};
+  float alx[2] = {0.f, 0.f}, aly[2] = {0.f, 0.f}, alz[2] = {0.f, 0.f};
+  for (int64_t t0 = 0; t0 < n; t0 += kDirThreads) {
+    const int64_t j = t0 + threadIdx.x;
+    const float4 h = j < n ? hi[j] : make_float4(0, 0, 0, 0);
+    const float4 l = j < n ? lo[j] : make_float4(0, 0, 0, 0);
+    sA[threadIdx.x] = make_float4(h.x, h.x, h.y, h.y);
+    sB[threadIdx.x] = make_float4(h.z, h.z, h.w, h.w);
+    sC[threadIdx.x] = make_float4(l.x, l.x, l.y, l.y);
+    sD[threadIdx.x] = make_float4(l.z, l.z, 0.f, 0.f);
+    __syncthreads();
+    float2 px = make_float2(0.f, 0.f), py = px, pz = px;
+#pragma unroll 4
+    for (int k = 0; k < kDirThreads; ++k) {
+      const float4 A = sA[k], B = sB[k], Cc = sC[k], D = sD[k];
+      const float2 dx = add2(add2(xy2(A), nhx), add2(xy2(Cc), nlx));
+      const float2 dy = add2(add2(zw2(A), nhy), add2(zw2(Cc), nly));
+      const float2 dz = add2(add2(xy2(B), nhz), add2(xy2(D), nlz));
+      const float2 r2 = fma2(dz, dz, fma2(dy, dy, fma2(dx, dx, e2)));
+      float2 inv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+      // with eps > 0, r^2 >= eps^2 > 0 and the self pair (d = 0) adds m * 0;
+      // with eps = 0 a pair at r^2 = 0 must add nothing
+      if (EPS0) {
+        inv.x = r2.x > 0.f ? inv.x : 0.f;
+        inv.y = r2.y > 0.f ? inv.y : 0.f;
+      }
+      const float2 sc = mul2(zw2(B), mul2(mul2(inv, inv), inv));
+      px = fma2(sc, dx, px);
+      py = fma2(sc, dy, py);
+      pz = fma2(sc, dz, pz);
+    }
+    two_sum_add(ahx[0], alx[0], px.x); two_sum_add(ahx[1], alx[1], px.y);
+    two_sum_add(ahy[0], aly[0], py.x); two_sum_add(ahy[1], aly[1], py.y);
+    two_sum_add(ahz[0], alz[0], pz.x); two_sum_add(ahz[1], alz[1], pz.y);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    const int64_t i = i0 + p * kDirThreads;
+    if (i < n) {
+      acc[3 * i] = G * ((double)ahx[p] + (double)alx[p]);
+      acc[3 * i + 1] = G * ((double)ahy[p] + (double)aly[p]);
+      acc[3 * i + 2] = G * ((double)ahz[p] + (double)alz[p]);
+    }
+  }
+}
+
+// One block: 512 Morton-consecutive bodies (2 per thread, evaluated as one packed pair)
+// against every 256-body tile; the tile's sources are staged duplicated, (x, x, y, y) and
+// (z, z, m, m), so that each shared-memory load gives a packed operand.
 template <bool EPS0>
 __global__ void __launch_bounds__(kDirThreads)
 k_direct_sorted(const float4 *__restrict__ hi, const float4 *__restrict__ lo,
                 const float4 *__restrict__ box, const uint32_t *__restrict__ perm, int64_t n,
                 float eps2, double G, double *__restrict__ acc) {
-  __shared__ float4 sh[kDirThreads], sl[kDirThreads];
-  constexpr int P = kDirPerThread;
-  const int64_t b0 = blockIdx.x * (int64_t)kDirThreads * P;
+  __shared__ float4 sA[kDirThreads], sB[kDirThreads], sC[kDirThreads], sD[kDirThreads];
+  static_assert(kDirPerThread == 2, "the two bodies of a thread form one packed pair");
+  const int64_t b0 = blockIdx.x * (int64_t)kDirThreads * 2;
   const int64_t ntiles = (n + kDirThreads - 1) / kDirThreads;
   // origin (the block's first body) and the block's box from its tiles' boxes
   const float4 oh = hi[b0], ol = lo[b0];
   float bl[3] = {INFINITY, INFINITY, INFINITY}, bu[3] = {-INFINITY, -INFINITY, -INFINITY};
 #pragma unroll
-  for (int p = 0; p < P; ++p) {
+  for (int p = 0; p < 2; ++p) {
     const int64_t t = b0 / kDirThreads + p;
     if (t < ntiles) {
       const float4 a = box[2 * t], c = box[2 * t + 1];
@@ -172,19 +196,28 @@ k_direct_sorted(const float4 *__restrict__ hi, const float4 *__restrict__ lo,
   // far: gap >= diag / 2 (the hi parts' rounding is taken off the gap below)
   const float far2 = 0.25f * fmaf(ex, ex, fmaf(ey, ey, ez * ez)) * 1.01f + 1e-30f;
   const float slack = C * 2.4e-7f;            // 2^-22 |x|: hi parts are within 2^-24 |x|
-  float xh[P], yh[P], zh[P], xl[P], yl[P], zl[P], xr[P], yr[P], zr[P];
-  float ahx[P], ahy[P], ahz[P], alx[P], aly[P], alz[P];
+  // the thread's two bodies, negated (d = source - body is source + (-body))
+  float nh[2][3], nl[2][3], nr[2][3];
 #pragma unroll
-  for (int p = 0; p < P; ++p) {
+  for (int p = 0; p < 2; ++p) {
     const int64_t i = b0 + threadIdx.x + p * kDirThreads;
     const float4 h = i < n ? hi[i] : oh;
     const float4 l = i < n ? lo[i] : ol;
-    xh[p] = h.x; yh[p] = h.y; zh[p] = h.z; xl[p] = l.x; yl[p] = l.y; zl[p] = l.z;
-    xr[p] = (h.x - oh.x) + (l.x - ol.x);
-    yr[p] = (h.y - oh.y) + (l.y - ol.y);
-    zr[p] = (h.z - oh.z) + (l.z - ol.z);
-    ahx[p] = ahy[p] = ahz[p] = alx[p] = aly[p] = alz[p] = 0.f;
+    nh[p][0] = -h.x; nh[p][1] = -h.y; nh[p][2] = -h.z;
+    nl[p][0] = -l.x; nl[p][1] = -l.y; nl[p][2] = -l.z;
+    nr[p][0] = -((h.x - oh.x) + (l.x - ol.x));
+    nr[p][1] = -((h.y - oh.y) + (l.y - ol.y));
+    nr[p][2] = -((h.z - oh.z) + (l.z - ol.z));
   }
+  const float2 nhx = make_float2(nh[0][0], nh[1][0]), nhy = make_float2(nh[0][1], nh[1][1]),
+               nhz = make_float2(nh[0][2], nh[1][2]);
+  const float2 nlx = make_float2(nl[0][0], nl[1][0]), nly = make_float2(nl[0][1], nl[1][1]),
+               nlz = make_float2(nl[0][2], nl[1][2]);
+  const float2 nrx = make_float2(nr[0][0], nr[1][0]), nry = make_float2(nr[0][1], nr[1][1]),
+               nrz = make_float2(nr[0][2], nr[1][2]);
+  const float2 e2 = make_float2(eps2, eps2);
+  float ahx[2] = {0.f, 0.f}, ahy[2] = {0.f, 0.f}, ahz[2] = {0.f, 0.f};
+  float alx[2] = {0.f, 0.f}, aly[2] = {0.f, 0.f}, alz[2] = {0.f, 0.f};
   for (int64_t t = 0; t < ntiles; ++t) {
     const float4 a0 = box[2 * t], a1 = box[2 * t + 1];
     float gx = fmaxf(fmaxf(a0.x - bu[0], bl[0] - a1.x) - slack, 0.f);
@@ -195,61 +228,60 @@ k_direct_sorted(const float4 *__restrict__ hi, const float4 *__restrict__ lo,
     const float4 h = j < n ? hi[j] : make_float4(0, 0, 0, 0);
     const float4 l = j < n ? lo[j] : make_float4(0, 0, 0, 0);
     if (far) {   // sources relative to the origin; past the end: massless and very far
-      sh[threadIdx.x] = j < n ? make_float4((h.x - oh.x) + (l.x - ol.x), (h.y - oh.y) + (l.y - ol.y),
-                                            (h.z - oh.z) + (l.z - ol.z), h.w)
-                              : make_float4(1e30f, 1e30f, 1e30f, 0.f);
+      const float4 r = j < n ? make_float4((h.x - oh.x) + (l.x - ol.x), (h.y - oh.y) + (l.y - ol.y),
+                                           (h.z - oh.z) + (l.z - ol.z), h.w)
+                             : make_float4(1e30f, 1e30f, 1e30f, 0.f);
+      sA[threadIdx.x] = make_float4(r.x, r.x, r.y, r.y);
+      sB[threadIdx.x] = make_float4(r.z, r.z, r.w, r.w);
     } else {
-      sh[threadIdx.x] = h;
-      sl[threadIdx.x] = l;
+      sA[threadIdx.x] = make_float4(h.x, h.x, h.y, h.y);
+      sB[threadIdx.x] = make_float4(h.z, h.z, h.w, h.w);
+      sC[threadIdx.x] = make_float4(l.x, l.x, l.y, l.y);
+      sD[threadIdx.x] = make_float4(l.z, l.z, 0.f, 0.f);
     }
     __syncthreads();
-    float px[P], py[P], pz[P];
-#pragma unroll
-    for (int p = 0; p < P; ++p) px[p] = py[p] = pz[p] = 0.f;
+    float2 px = make_float2(0.f, 0.f), py = px, pz = px;
     if (far) {
 #pragma unroll 4
       for (int k = 0; k < kDirThreads; ++k) {
-        const float4 a = sh[k];
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-          const float dx = a.x - xr[p], dy = a.y - yr[p], dz = a.z - zr[p];
-          const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
-          const float inv = rsqrtf(r2);           // r2 > 0: the tile is away from the block
-          const float sc = a.w * (inv * inv * inv);
-          px[p] = fmaf(sc, dx, px[p]);
-          py[p] = fmaf(sc, dy, py[p]);
-          pz[p] = fmaf(sc, dz, pz[p]);
-        }
+        const float4 A = sA[k], B = sB[k];
+        const float2 dx = add2(xy2(A), nrx), dy = add2(zw2(A), nry), dz = add2(xy2(B), nrz);
+        const float2 r2 = fma2(dz, dz, fma2(dy, dy, fma2(dx, dx, e2)));
+        // r2 > 0: the tile is away from the block
+        const float2 inv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+        const float2 sc = mul2(zw2(B), mul2(mul2(inv, inv), inv));
+        px = fma2(sc, dx, px);
+        py = fma2(sc, dy, py);
+        pz = fma2(sc, dz, pz);
       }
     } else {
 #pragma unroll 4
       for (int k = 0; k < kDirThreads; ++k) {
-        const float4 a = sh[k], b = sl[k];
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-          const float dx = (a.x - xh[p]) + (b.x - xl[p]);
-          const float dy = (a.y - yh[p]) + (b.y - yl[p]);
-          const float dz = (a.z - zh[p]) + (b.z - zl[p]);
-          const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
-          float inv = rsqrtf(r2);
-          if (EPS0) inv = r2 > 0.f ? inv : 0.f;
-          const float sc = a.w * (inv * inv * inv);
-          px[p] = fmaf(sc, dx, px[p]);
-          py[p] = fmaf(sc, dy, py[p]);
-          pz[p] = fmaf(sc, dz, pz[p]);
+        const float4 A = sA[k], B = sB[k], Cc = sC[k], D = sD[k];
+        const float2 dx = add2(add2(xy2(A), nhx), add2(xy2(Cc), nlx));
+        const float2 dy = add2(add2(zw2(A), nhy), add2(zw2(Cc), nly));
+        const float2 dz = add2(add2(xy2(B), nhz), add2(xy2(D), nlz));
+        const float2 r2 = fma2(dz, dz, fma2(dy, dy, fma2(dx, dx, e2)));
+        float2 inv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+        // with eps > 0, r^2 >= eps^2 > 0 and the self pair (d = 0) adds m * 0;
+        // with eps = 0 a pair at r^2 = 0 must add nothing
+        if (EPS0) {
+          inv.x = r2.x > 0.f ? inv.x : 0.f;
+          inv.y = r2.y > 0.f ? inv.y : 0.f;
         }
+        const float2 sc = mul2(zw2(B), mul2(mul2(inv, inv), inv));
+        px = fma2(sc, dx, px);
+        py = fma2(sc, dy, py);
+        pz = fma2(sc, dz, pz);
       }
     }
-#pragma unroll
-    for (int p = 0; p < P; ++p) {
-      two_sum_add(ahx[p], alx[p], px[p]);
-      two_sum_add(ahy[p], aly[p], py[p]);
-      two_sum_add(ahz[p], alz[p], pz[p]);
-    }
+    two_sum_add(ahx[0], alx[0], px.x); two_sum_add(ahx[1], alx[1], px.y);
+    two_sum_add(ahy[0], aly[0], py.x); two_sum_add(ahy[1], aly[1], py.y);
+    two_sum_add(ahz[0], alz[0], pz.x); two_sum_add(ahz[1], alz[1], pz.y);
     __syncthreads();
   }
 #pragma unroll
-  for (int p = 0; p < P; ++p) {
+  for (int p = 0; p < 2; ++p) {
     const int64_t i = b0 + threadIdx.x + p * kDirThreads;
     if (i < n) {
       const int64_t ci = perm[i];
