@@ -289,6 +289,7 @@ void free_all(Ctx *c) {
   ctx_release(c, c->t.bbox_ticket); ctx_release(c, c->t.nnodes); ctx_release(c, c->t.scalars);
   ctx_release(c, c->walk_stats); ctx_release(c, c->walk_queues);
   ctx_release(c, c->walk_gstack); c->walk_gstack_cap = 0;
+  ctx_release(c, c->walk_part); c->walk_part_cap = 0;
   ctx_release(c, c->vjp_own); ctx_release(c, c->vjp_body); ctx_release(c, c->vjp_node);
   c->vjp_cap = 0;
   ctx_release(c, c->adj_levels); ctx_release(c, c->adj_work);

@@ -112,6 +112,8 @@ struct Ctx {
   void *walk_gstack = nullptr;                // walk stack overflow, per persistent warp
   unsigned *walk_queues = nullptr;            // walk task-queue counters, one per SM
   size_t walk_gstack_cap = 0;                 // in 8-byte entries
+  double *walk_part = nullptr;                // four-way split walk: partial sums
+  size_t walk_part_cap = 0;                   // in doubles
   // vector-Jacobian product scratch (sorted order; nodes 2 cap)
   double *vjp_own = nullptr, *vjp_body = nullptr, *vjp_node = nullptr;
   int64_t vjp_cap = 0;

@@ -31,11 +31,11 @@
 //     FP64 one).
 // The kernel is persistent: each warp takes 32-body tasks from an atomic counter,
 // and owns an overflow area in global memory for the deep part of its stack.  When
-// there are too few tasks to fill the GPU (small N), each task is split in two: two
-// warps walk the same 32 bodies, each from one half of the root's children (the root
-// contains every body, so the guard opens it for all of them), and add their partial
-// sums to the zeroed output with FP64 atomics (two addends: the result does not
-// depend on their order).
+// there are too few tasks to fill the GPU (small N), each task is split in two or four:
+// warps walk the same 32 bodies, each from its share of the root's children (the root
+// contains every body, so the guard opens it for all of them); two partial sums are added
+// to the zeroed output with FP64 atomics (two addends: the result does not depend on their
+// order), four are written to scratch and added in a fixed order by a closing pass.
 // A second mode computes the vector-Jacobian product of the accelerations on the
 // same decisions (see flush_vjp and k_vjp_finish); a third counts decisions and
 // collects walk statistics.
@@ -63,6 +63,7 @@ inline WalkShape walk_shape(int cfg) {
   const int fl[3] = {16, 12, 8};
   return WalkShape{fl[cfg % 3], (cfg / 3) % 3, cfg / 9};
 }
+constexpr int kSplitWarpsPerSM = 28;           // resident warps per SM of the monopole walk
 constexpr uint32_t kFirstMask = 0x01FFFFFFu;   // 25-bit first index
 constexpr int kCntShift = 25;                  // 6-bit (count - 1)
 
@@ -93,6 +94,7 @@ struct WarpSmem {
   uint2 fM[kPairCap];             //             lane masks of entries a, b
   int32_t ltag[kListCap];         // counting / VJP: -(node+1) node term, else sorted body index
   float4 org_h, org_l;            // the warp origin (lane 0's body), hi and lo parts
+  int32_t part;                   // split task: which share of the root's children
   int32_t bitem[32];              // node id of each lane's item (mixed nodes' FP64 decisions)
   int4 lfx[32];                   // opened leaves of a batch: first body, bodies, lane mask
 };
@@ -144,7 +146,9 @@ struct WalkArgs {
   const int32_t *nnodes;
   int n;
   int ntasks;                     // tasks after splitting (base tasks x split)
-  int split;                      // 1, or 2: two warps per base task (see above)
+  int split;                      // 1, 2 or 4 warps per base task (see above)
+  double *part;                   // split 4: partial sums [4][rows][3] (rows = n or nrange)
+  int rows;
   float theta2f;
   double theta2d;
   float eps2;
@@ -577,14 +581,14 @@ k_walk(WalkArgs A) {
     const int wbeg = A.task_begin ? A.task_begin[task] : task * 32;
     const int wend = min(A.task_begin ? A.task_end[task] : n, wbeg + 32);
     const int root = A.task_seg ? A.task_seg[task] : 0;
-    // first stack entry: the root, or (split) this part's half of the root's children
+    // first stack entry: the root, or (split) this part's share of the root's children
     uint32_t first_entry = (uint32_t)root;
     if (A.split > 1) {
       const int4 rt = A.topo[root];
       if (rt.x < 0) {                           // a one-leaf tree: part 0 takes it whole
         if (part != 0) continue;
       } else {
-        const int h = (rt.y + 1) / 2;
+        const int h = (rt.y + A.split - 1) / A.split;
         const int cnt = min(h, rt.y - part * h);
         if (cnt <= 0) continue;
         first_entry = (uint32_t)(rt.x + part * h) | ((uint32_t)(cnt - 1) << kCntShift);
@@ -612,6 +616,7 @@ k_walk(WalkArgs A) {
     if (lane == 0) {                            // kept in shared memory for the far appends
       M.org_h = make_float4(ohx, ohy, ohz, 0.f);
       M.org_l = make_float4(olx, oly, olz, 0.f);
+      M.part = part;                            // (read back when the sums are written)
     }
     const float xr = valid ? (xh - ohx) + (xl - olx) : 0.f;
     const float yr = valid ? (yh - ohy) + (yl - oly) : 0.f;
@@ -1034,12 +1039,24 @@ k_walk(WalkArgs A) {
     if (!VJP && valid && A.split > 1) {         // partial sums of a split task
       double ax, ay, az;
       acc.get(acc64, ax, ay, az);
-      const int64_t ci = A.perm[gi];
-      double *dst = A.acc_sorted ? A.acc_sorted + 3 * (int64_t)(gi - A.body0) : A.acc + 3 * ci;
-      atomicAdd(dst, ax * A.G);
-      atomicAdd(dst + 1, ay * A.G);
-      atomicAdd(dst + 2, az * A.G);
+      double *dst;
+      if (A.part) {                             // four parts: added in a fixed order later
+        dst = A.part + 3 * ((int64_t)M.part * A.rows + (gi - A.body0));
+      } else {                                  // two parts: two addends, order-free
+        dst = A.acc_sorted ? A.acc_sorted + 3 * (int64_t)(gi - A.body0)
+                           : A.acc + 3 * (int64_t)A.perm[gi];
+      }
+      if (A.part) {
+        dst[0] = ax * A.G;
+        dst[1] = ay * A.G;
+        dst[2] = az * A.G;
+      } else {
+        atomicAdd(dst, ax * A.G);
+        atomicAdd(dst + 1, ay * A.G);
+        atomicAdd(dst + 2, az * A.G);
+      }
       if (COUNT) {
+        const int64_t ci = A.perm[gi];
         atomicAdd(&A.counts[3 * ci], c_m2p);
         atomicAdd(&A.counts[3 * ci + 1], c_p2p);
         atomicAdd(&A.counts[3 * ci + 2], c_tests);
@@ -1075,6 +1092,39 @@ k_walk(WalkArgs A) {
   }
 }
 
+// Four-way split: the parts' partial sums added in a fixed order (so results do not depend
+// on which warp finished first), written in caller order (or as range rows), with the
+// leapfrog's closing kick when asked for.
+__global__ void k_walk_finish(const double *__restrict__ part, int rows,
+                              const uint32_t *__restrict__ perm, double *__restrict__ acc,
+                              double *__restrict__ acc_sorted, double *__restrict__ vel,
+                              double kick) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  double a[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double *p = part + 3 * (int64_t)i + k;
+    a[k] = __dadd_rn(__dadd_rn(__dadd_rn(p[0], p[3 * (int64_t)rows]), p[6 * (int64_t)rows]),
+                     p[9 * (int64_t)rows]);
+  }
+  if (acc_sorted) {
+    acc_sorted[3 * (int64_t)i] = a[0];
+    acc_sorted[3 * (int64_t)i + 1] = a[1];
+    acc_sorted[3 * (int64_t)i + 2] = a[2];
+    return;
+  }
+  const int64_t ci = perm[i];
+  acc[3 * ci] = a[0];
+  acc[3 * ci + 1] = a[1];
+  acc[3 * ci + 2] = a[2];
+  if (vel) {
+    vel[3 * ci] = __dadd_rn(vel[3 * ci], __dmul_rn(kick, a[0]));
+    vel[3 * ci + 1] = __dadd_rn(vel[3 * ci + 1], __dmul_rn(kick, a[1]));
+    vel[3 * ci + 2] = __dadd_rn(vel[3 * ci + 2], __dmul_rn(kick, a[2]));
+  }
+}
+
 template <int ORDER, bool EPS0, int MODE>
 int launch_walk(Ctx *c, WalkArgs A) {
   using Smem = typename std::conditional<
@@ -1106,13 +1156,33 @@ int launch_walk(Ctx *c, WalkArgs A) {
   int bps = blocks_per_sm[dev] - shape.blocks_less;
   if (bps < 1) bps = 1;
   int blocks = bps * c->num_sms;
-  // split tasks when the tree has no more of them than resident warps (decided on the
-  // whole tree's task count, so that a range walk computes what the full walk does)
+  // split tasks when the tree has no more of them than a full GPU of warps, in four when it
+  // has no more than half as many; the decision depends only on the whole tree's task count
+  // and the SM count (not on the kernel variant, the launch shape or a range), so every
+  // variant and a range walk compute what the full walk does; the VJP splits in two at most
   const int base_tasks = A.ntasks;
   const int basis = A.split_basis > 0 ? A.split_basis : base_tasks;
-  A.split = (A.mac_guard && basis <= blocks * kWalkWarps) ? 2 : 1;
+  const int slots = kSplitWarpsPerSM * c->num_sms;
+  A.split = !A.mac_guard ? 1 : (2 * basis <= slots && MODE != kModeVjp) ? 4 : basis <= slots ? 2 : 1;
   A.ntasks = base_tasks * A.split;
-  if (A.split > 1) {
+  const int rows = A.acc_sorted ? A.nrange : A.n;
+  A.rows = rows;
+  A.part = nullptr;
+  if (A.split == 4) {
+    const size_t need_part = (size_t)12 * rows;
+    if (need_part > c->walk_part_cap) {
+      GRAV_CUDA_TRY(cudaStreamSynchronize(c->stream));
+      ctx_release(c, c->walk_part);
+      c->walk_part_cap = 0;
+      const int rc = ctx_alloc(c, c->walk_part, (int64_t)need_part);
+      if (rc) return rc;
+      c->walk_part_cap = need_part;
+    }
+    A.part = c->walk_part;
+    GRAV_CUDA_TRY(cudaMemsetAsync(A.part, 0, sizeof(double) * need_part, c->stream));
+    if (MODE == kModeCount)
+      GRAV_CUDA_TRY(cudaMemsetAsync(A.counts, 0, sizeof(int32_t) * 3 * (size_t)A.n, c->stream));
+  } else if (A.split > 1) {
     const size_t n3 = 3 * (size_t)A.n;
     if (MODE == kModeVjp) {
       GRAV_CUDA_TRY(cudaMemsetAsync(A.g_own, 0, sizeof(double) * n3, c->stream));
@@ -1147,6 +1217,12 @@ int launch_walk(Ctx *c, WalkArgs A) {
   kern<<<blocks, 32 * kWalkWarps, smem, c->stream>>>(A);
   ++c->launches;
   GRAV_CUDA_TRY(cudaGetLastError());
+  if (A.split == 4) {
+    k_walk_finish<<<(unsigned)((rows + 255) / 256), 256, 0, c->stream>>>(
+        A.part, rows, A.perm, A.acc_sorted ? nullptr : A.acc, A.acc_sorted, kick_vel, A.kick);
+    ++c->launches;
+    return cuda_status(cudaGetLastError());
+  }
   if (A.split > 1 && kick_vel) return launch_kick(c, A.n, kick_vel, A.acc, A.kick);
   return GRAVITY_OK;
 }
