@@ -223,6 +223,17 @@ def cpu_baseline_leg(pos, m, args, gpu):
            "sample": f"FP64 oracle on the same workload: tree build of all {len(pos)} bodies "
                      f"({tb:.2f} s, 1 thread) + walk of {what} ({tw:.2f} s, OpenMP); "
                      f"median of {len(runs)} runs"}
+    # one core: the build is single-threaded already; a walk of a seeded sample on one thread
+    oracle.set_threads(1)
+    try:
+        n1 = min(16384, len(pos))
+        v1, tb1, tw1 = oracle_eval(pos, m, args, n1)
+    finally:
+        oracle.set_threads(0)
+    cpu["single_thread"] = {"value": v1, "unit": UNIT, "cores": 1,
+                            "sample": f"tree build of all {len(pos)} bodies ({tb1:.2f} s) + walk of "
+                                      f"{n1} seeded targets on one thread ({tw1:.2f} s), scaled to "
+                                      f"N targets"}
     acc_gpu = gpu["acc"] if idx is None else gpu["acc"][idx]
     parity = parity_figures(acc_gpu, oacc, oabs)
     parity["against"] = "the oracle's walk of the same tree configuration (FP64)"
@@ -582,7 +593,7 @@ def run_ours(args, rank, world, local_rank):
                "ms_per_step": 1e3 * te,
                "api": "gravity_forces_host (pinned host buffers, copies + build + walk + sync)"}
 
-    ens = None if args.no_ensemble or shard_mode else ensemble_leg(args, g, dev, rank)
+    ens = None if args.no_ensemble or shard_mode else ensemble_leg(args, g, dev, rank, world)
     grad = None if args.no_grad or shard_mode else gradient_leg(args, g, dev, rank)
 
     if rank != 0:
@@ -628,13 +639,20 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
-def ensemble_leg(args, g, dev, rank):
+def ensemble_leg(args, g, dev, rank, world=1):
     """Batched ensemble: 256 independent spinning clouds (N_k log-uniform in
     [1024, 65536]), one build + one walk launch per step, KDK leapfrog steps
-    replayed as a CUDA graph on a side stream, autotuned walk shape."""
+    replayed as a CUDA graph on a side stream, autotuned walk shape.  With several ranks
+    the same 256 clouds are partitioned between them by cost (N_k log N_k, no exchange)
+    and the whole job's rate is reported over the slowest rank."""
     import torch
-    from paper_1912_04197_gb300 import autotune, inputs
-    off, pos, vel, m = inputs.ensemble(nclouds=256, seed=args.seed + 100 + rank)
+    from paper_1912_04197_gb300 import autotune, inputs, shard
+    off, pos, vel, m = inputs.ensemble(nclouds=256, seed=args.seed + 100)
+    n_total = len(pos)
+    if world > 1:
+        k0, k1 = shard.partition_clouds(np.diff(off), world)[rank]
+        b0, b1 = int(off[k0]), int(off[k1])
+        off, pos, vel, m = off[k0:k1 + 1] - off[k0], pos[b0:b1], vel[b0:b1], m[b0:b1]
     n = len(pos)
     stream = torch.cuda.Stream(dev)
     with torch.cuda.stream(stream):
@@ -660,10 +678,13 @@ def ensemble_leg(args, g, dev, rank):
         ms = e0.elapsed_time(e1)
         kernels = g.gravity_stats(ctx) - k0
     steps = args.ensemble_steps
-    return {"workload": f"256 independent clouds, {n} bodies (N_k log-uniform in [1024, 65536]), "
-                        f"uniform spheres with random spin, eps={args.eps}, theta={args.theta}, "
-                        f"order {args.order}, leaf {args.leaf_max}, dt=1e-3",
-            "steps": steps, "ms_per_step": ms / steps, "value": n * steps / (ms * 1e-3),
+    ms = max_over_ranks(ms, world, dev)
+    return {"workload": f"256 independent clouds, {n_total} bodies (N_k log-uniform in [1024, "
+                        f"65536]), uniform spheres with random spin, eps={args.eps}, "
+                        f"theta={args.theta}, order {args.order}, leaf {args.leaf_max}, dt=1e-3"
+                        + (f"; clouds partitioned over {world} ranks by N_k log N_k" if world > 1
+                           else ""),
+            "steps": steps, "ms_per_step": ms / steps, "value": n_total * steps / (ms * 1e-3),
             "unit": "body-forces/s (leapfrog steps, one force evaluation each)",
             "graph": True, "kernels_per_step": kernels / steps, "walk_cfg": int(p.walk_cfg)}
 

@@ -80,6 +80,8 @@ def _load():
             lib.orc_direct.restype = None
             lib.orc_leapfrog.argtypes = [I64, P, P, P, P, D, I, I, I, D, D, D, I, I, I, I]
             lib.orc_leapfrog.restype = I
+            lib.orc_set_threads.argtypes = [I]
+            lib.orc_set_threads.restype = None
             lib.orc_diagnostics.argtypes = [I64, P, P, P, D, D, P]
             lib.orc_diagnostics.restype = None
             lib.orc_components.argtypes = [I64, P, P, D, P, P]
@@ -272,6 +274,11 @@ def step(pos, vel, mass, acc, dt, nsteps, *, scheme=0, use_tree=True, theta=0.5,
     if rc:
         raise OracleError(rc)
     return pos, vel, acc
+
+
+def set_threads(n: int = 0):
+    """Host threads of the oracle's parallel loops (0 = all cores); for timing only."""
+    _load().orc_set_threads(int(n))
 
 
 def diagnostics(pos, vel, mass, eps, G=1.0):

@@ -31,6 +31,8 @@
 //   * a leaf holding a single body is always a body-to-body term (Eq. Force_leaf);
 //     a leaf holding several bodies is tested like an internal node.
 
+#include <omp.h>
+
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -728,5 +730,9 @@ void orc_components(int64_t n, const double *pos, const double *radius, double d
     if (size > 1) ++counts[1];
   }
 }
+
+// Number of host threads the OpenMP loops use (timing at one core and at all cores);
+// n <= 0 restores the default.  No arithmetic depends on it.
+void orc_set_threads(int n) { omp_set_num_threads(n > 0 ? n : omp_get_num_procs()); }
 
 }  // extern "C"

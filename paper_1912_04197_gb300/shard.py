@@ -129,3 +129,27 @@ def sharded_leapfrog(engine, comm, pos, vel, mass, acc, dt: float, nsteps: int, 
         if kdk:
             engine.kick(vel, acc, h)
     return pos, vel, acc
+
+
+def partition_clouds(sizes, world: int) -> list[tuple[int, int]]:
+    """Independent clouds over `world` ranks: contiguous cloud ranges [k0, k1) per rank with
+    about equal cost, the cost of a cloud of N_k bodies taken as N_k log N_k (the tree walk's
+    work; the build is O(N_k)).  A cut falls at the cloud boundary nearest to each rank's
+    share of the total; clouds are never split, so no exchange is needed."""
+    import math
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    cost = [float(n) * math.log(max(float(n), 2.0)) for n in sizes]
+    total = sum(cost)
+    cuts, acc, k = [0], 0.0, 0
+    for r in range(1, world):
+        target = total * r / world
+        while k < len(cost) and acc + cost[k] <= target:
+            acc += cost[k]
+            k += 1
+        if k < len(cost) and (target - acc) > (acc + cost[k] - target):
+            acc += cost[k]                     # the nearer boundary is after this cloud
+            k += 1
+        cuts.append(max(k, cuts[-1]))
+    cuts.append(len(cost))
+    return [(cuts[r], cuts[r + 1]) for r in range(world)]

@@ -141,3 +141,23 @@ def test_two_gloo_ranks_reproduce_the_single_rank_oracle_run():
             A1, P, V, A = res[rank][scheme]
             assert np.array_equal(A1, a0)
             assert np.array_equal(P, op) and np.array_equal(V, ov) and np.array_equal(A, oa)
+
+
+def test_partition_clouds_balances_cost():
+    import math
+    from paper_1912_04197_gb300 import inputs, shard
+    off, _, _, _ = inputs.ensemble(nclouds=256, seed=100)
+    sizes = np.diff(off)
+    cost = sizes * np.log(sizes)
+    for world in (1, 2, 3, 8):
+        parts = shard.partition_clouds(sizes, world)
+        assert parts[0][0] == 0 and parts[-1][1] == len(sizes)
+        assert all(parts[r][1] == parts[r + 1][0] for r in range(world - 1))
+        loads = [cost[a:b].sum() for a, b in parts]
+        # every rank is within one (largest) cloud of its equal share
+        assert max(abs(l - cost.sum() / world) for l in loads) <= cost.max()
+    two = shard.partition_clouds([10, 10], 4)          # more ranks than clouds: empty ranges
+    assert sorted(b - a for a, b in two) == [0, 0, 1, 1]
+    with pytest.raises(ValueError):
+        shard.partition_clouds([5], 0)
+    assert math.isclose(sum(b - a for a, b in shard.partition_clouds(sizes, 5)), len(sizes))
