@@ -66,6 +66,47 @@ def test_leapfrog_gradient_matches_finite_differences_direct():
         assert abs(fd - an) <= 1e-6 * (np.abs(gx * ex).sum() + np.abs(gv * ev).sum()), (fd, an)
 
 
+@pytest.mark.parametrize("theta,leaf_max", [(0.5, 1), (0.7, 4)])
+def test_leapfrog_gradient_matches_frozen_finite_differences_tree(theta, leaf_max):
+    # theta > 0: the reverse pass differentiates with every step's opening decisions frozen
+    # (those of the trees of the unperturbed trajectory).  A forward run whose forces come
+    # from those frozen trees (tree_forces_frozen at the perturbed positions) is a smooth
+    # map, so its central differences check the whole reverse pass, decisions and all
+    pos, vel, m = inputs.rubble_pile(150, seed=18)
+    dt, ns, eps = 2e-3, 12, 5e-2
+    rng = np.random.default_rng(19)
+    cx, cv = rng.standard_normal(pos.shape), rng.standard_normal(pos.shape)
+    a0 = oracle.tree_forces(pos, m, theta, eps, leaf_max=leaf_max)
+    levels, x, v, a = [pos.copy()], pos.copy(), vel.copy(), a0
+    for _ in range(ns):
+        x, v, a = oracle.step(x, v, m, a, dt, 1, theta=theta, eps=eps, leaf_max=leaf_max)
+        levels.append(x.copy())
+    trees = [oracle.Tree(xk, m, leaf_max=leaf_max) for xk in levels]
+
+    def L(x0, v0):
+        # KDK leapfrog with each level's forces from that level's frozen tree
+        x, v = x0.copy(), v0.copy()
+        a = oracle.tree_forces_frozen(trees[0], x, theta, eps)
+        for k in range(ns):
+            v = v + (0.5 * dt) * a
+            x = x + dt * v
+            a = oracle.tree_forces_frozen(trees[k + 1], x, theta, eps)
+            v = v + (0.5 * dt) * a
+        return (cx * x).sum() + (cv * v).sum()
+
+    # at zero perturbation the frozen run is the ordinary run
+    assert abs(L(pos, vel) - ((cx * levels[-1]).sum() + (cv * v).sum())) <= 1e-12 * (
+        np.abs(cx * levels[-1]).sum() + np.abs(cv * v).sum())
+    gx, gv = oracle.leapfrog_grad(pos, vel, m, cx, cv, dt, ns, theta=theta, eps=eps,
+                                  leaf_max=leaf_max)
+    h = 1e-6
+    for _ in range(3):
+        ex, ev = rng.standard_normal(pos.shape), rng.standard_normal(pos.shape)
+        fd = (L(pos + h * ex, vel + h * ev) - L(pos - h * ex, vel - h * ev)) / (2 * h)
+        an = (gx * ex).sum() + (gv * ev).sum()
+        assert abs(fd - an) <= 1e-6 * (np.abs(gx * ex).sum() + np.abs(gv * ev).sum()), (fd, an)
+
+
 def test_vjp_absum_two_body_closed_form():
     # two bodies, d = x1 - x0: body 0 takes part in its own term (source 1, cotangent
     # u0) and as the source of body 1's term (cotangent u1), so its magnitude sum is
