@@ -234,6 +234,24 @@ def cpu_baseline_leg(pos, m, args, gpu):
                             "sample": f"tree build of all {len(pos)} bodies ({tb1:.2f} s) + walk of "
                                       f"{n1} seeded targets on one thread ({tw1:.2f} s), scaled to "
                                       f"N targets"}
+    # the smaller configurations in full: direct sum and tree (build + walk of every body),
+    # all cores (configs of the plain method and the rubble pile)
+    from paper_1912_04197_gb300 import inputs as _inp
+    small = []
+    for label, (sp, _, sm), kw, eps_s in (
+            ("plain method: 2048 bodies uniform in a sphere", _inp.uniform_sphere(2048, seed=0),
+             dict(leaf_max=1, order=0), 1e-3),
+            ("rubble pile: 100,000 bodies", _inp.rubble_pile(100_000, seed=0),
+             dict(leaf_max=16, order=2), 5e-3)):
+        t0 = time.perf_counter()
+        oracle.direct(sp, sm, eps_s)
+        t1 = time.perf_counter()
+        oracle.Tree(sp, sm, **kw).forces(args.theta, eps_s)
+        t2 = time.perf_counter()
+        small.append({"workload": label, "n": len(sp), "direct_s": t1 - t0,
+                      "direct_value": len(sp) / (t1 - t0), "tree_s": t2 - t1,
+                      "tree_value": len(sp) / (t2 - t1), "unit": UNIT, "tree": kw})
+    cpu["smaller_configs"] = small
     acc_gpu = gpu["acc"] if idx is None else gpu["acc"][idx]
     parity = parity_figures(acc_gpu, oacc, oabs)
     parity["against"] = "the oracle's walk of the same tree configuration (FP64)"
