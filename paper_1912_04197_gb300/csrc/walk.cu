@@ -95,7 +95,9 @@ struct WarpSmem {
   int32_t ltag[kListCap];         // counting / VJP: -(node+1) node term, else sorted body index
   float4 org_h, org_l;            // the warp origin (lane 0's body), hi and lo parts
   int32_t part;                   // split task: which share of the root's children
+  float band_k, band_c;           // mixed-node test: FP64 band = 2^-16 l^2 + k D^2 + c
   int32_t bitem[32];              // node id of each lane's item (mixed nodes' FP64 decisions)
+  float4 bcr[32];                 // a lane's mixed node: COM relative to the origin, l^2
   int4 lfx[32];                   // opened leaves of a batch: first body, bodies, lane mask
 };
 
@@ -652,6 +654,15 @@ k_walk(WalkArgs A) {
     // a node with l^2 >= farl2 is at least R_w / 2 from every body that accepts it
     // (D > l / theta), which bounds the far-path error of d by 5.5 * 2^-23 |d|
     const float farl2 = 0.25f * theta2f * rw2 * 1.01f;
+    if (lane == 0) {
+      // the per-lane test of a mixed node runs on warp-relative coordinates: with R_w^2 =
+      // rw2, the error of d = c_rel - x_rel is below 2^-23 (1.5 D + 2 R_w) (the origin
+      // offset being exact to 2^-24 of each coordinate), that of the FP32 D^2 below
+      // 2^-22 (3.25 D^2 + R_w^2); a result within 2^-16 l^2 + theta^2 2^-20 (D^2 + R_w^2) of
+      // the boundary (four times that bound) is taken in FP64, so the decision is exact
+      M.band_k = theta2f * 9.5367431640625e-7f;
+      M.band_c = theta2f * 9.5367431640625e-7f * rw2;
+    }
 
     Accum acc;
     int c_m2p = 0, c_p2p = 0, c_tests = 0;
@@ -795,26 +806,26 @@ k_walk(WalkArgs A) {
       unsigned mixed_bits = __ballot_sync(0xffffffffu, mixed);
       if (COUNT) w_mixed += __popc(mixed_bits);
       if (mixed_bits) {
-        if (mixed) M.bitem[lane] = item;
+        if (mixed) {                           // the node's COM relative to the warp origin
+          M.bitem[lane] = item;
+          const float4 oh = M.org_h, ol = M.org_l;
+          M.bcr[lane] = make_float4((r0.x - oh.x) + (r1.x - ol.x), (r0.y - oh.y) + (r1.y - ol.y),
+                                    (r0.z - oh.z) + (r1.z - ol.z), r1.w);
+        }
         __syncwarp();
       }
       while (mixed_bits) {
         const int j = __ffs(mixed_bits) - 1;
         mixed_bits &= mixed_bits - 1;
         const unsigned tk = __shfl_sync(0xffffffffu, tmask, j);
-        float4 c0, c1;
-        c0.x = __shfl_sync(0xffffffffu, r0.x, j); c0.y = __shfl_sync(0xffffffffu, r0.y, j);
-        c0.z = __shfl_sync(0xffffffffu, r0.z, j); c1.x = __shfl_sync(0xffffffffu, r1.x, j);
-        c1.y = __shfl_sync(0xffffffffu, r1.y, j); c1.z = __shfl_sync(0xffffffffu, r1.z, j);
-        c1.w = __shfl_sync(0xffffffffu, r1.w, j);
         bool a_i = false;
         if (tk & (1u << lane)) {
-          const float dx = (c0.x - xh) + (c1.x - xl);
-          const float dy = (c0.y - yh) + (c1.y - yl);
-          const float dz = (c0.z - zh) + (c1.z - zl);
+          const float4 c = M.bcr[j];
+          const float dx = c.x - xr, dy = c.y - yr, dz = c.z - zr;
           const float D2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          const float diff = c1.w - theta2f * D2;
-          if (fabsf(diff) <= 1.52587890625e-5f * c1.w) {    // 2^-16 band: decide in FP64
+          const float diff = c.w - theta2f * D2;
+          if (fabsf(diff) <= fmaf(M.band_k, D2, fmaf(1.52587890625e-5f, c.w, M.band_c))) {
+            // within the band of the FP32 test's error: decide in FP64
             const int node = M.bitem[j];
             const double X = A.ncom[3 * node], Y = A.ncom[3 * node + 1], Z = A.ncom[3 * node + 2];
             const double x = A.pos_s[3 * gi], y = A.pos_s[3 * gi + 1], z = A.pos_s[3 * gi + 2];
