@@ -378,9 +378,18 @@ int gravity_debug_export(gravity_ctx *ctx, int what, void *host_dst, size_t byte
  * makes the first tile of every radix-sort pass withhold its published digit counts and
  * gives each tile's look-back wait a budget of k polls, so the next tile's wait runs out
  * and GRAVITY_E_TIMEOUT is latched (the order of that build is then wrong, every index
- * still in range, nothing faults); 0 restores normal sorting.  GRAVITY_E_ARG for an
- * unknown item or value. */
-enum gravity_debug_setting { GRAVITY_DBGSET_STACK_CAP = 1, GRAVITY_DBGSET_SORT_STALL = 2 };
+ * still in range, nothing faults); 0 restores normal sorting.
+ * GRAVITY_DBGSET_MOMENTS_STALL: value k in 1 .. 2^18 keeps the moment pass from counting
+ * the nodes of the deepest internal depth and gives each of its waits (an internal depth
+ * waits for the deeper ones) a budget of k polls, so the next depth's wait runs out and
+ * GRAVITY_E_TIMEOUT is latched (that build's moments may then be wrong; every index stays
+ * in range, nothing faults); 0 restores the normal pass.  GRAVITY_E_ARG for an unknown
+ * item or value. */
+enum gravity_debug_setting {
+  GRAVITY_DBGSET_STACK_CAP = 1,
+  GRAVITY_DBGSET_SORT_STALL = 2,
+  GRAVITY_DBGSET_MOMENTS_STALL = 3
+};
 int gravity_debug_set(gravity_ctx *ctx, int what, int64_t value);
 
 /* Number of kernels this context has enqueued since it was created (host-side

@@ -269,7 +269,7 @@ int alloc_base(Ctx *c) {
   if (rc == GRAVITY_OK) c->t.geom_cap = 1;
   if (rc == GRAVITY_OK) rc = ctx_alloc(c, c->t.bbox_ticket, 1);
   if (rc == GRAVITY_OK) rc = ctx_alloc(c, c->t.nnodes, 1);
-  if (rc == GRAVITY_OK) rc = ctx_alloc(c, c->t.scalars, 128);
+  if (rc == GRAVITY_OK) rc = ctx_alloc(c, c->t.scalars, grav::kScalarWords);
   if (rc == GRAVITY_OK) rc = ctx_alloc(c, c->walk_stats, 16);
   if (rc == GRAVITY_OK) rc = ctx_alloc(c, c->walk_queues, c->num_sms + 1);
   if (rc == GRAVITY_OK) rc = cuda_status(cudaMemset(c->walk_stats, 0, 16 * sizeof(unsigned long long)));
@@ -399,6 +399,10 @@ int gravity_debug_set(gravity_ctx *h, int what, int64_t value) {
     case GRAVITY_DBGSET_SORT_STALL:
       if (value < 0 || value > (1 << 22)) return GRAVITY_E_ARG;
       h->c.sort_stall = (int)value;
+      return GRAVITY_OK;
+    case GRAVITY_DBGSET_MOMENTS_STALL:
+      if (value < 0 || value > (1 << 18)) return GRAVITY_E_ARG;
+      h->c.moments_stall = (int)value;
       return GRAVITY_OK;
     default:
       return GRAVITY_E_ARG;

@@ -11,6 +11,7 @@
 namespace grav {
 
 constexpr int kLevels = 21;          // 63-bit Morton keys: 21 levels of 3 bits
+constexpr int kScalarWords = 192;    // small device scalars of a tree (t.scalars)
 constexpr int kMaxLeaf = 64;         // largest leaf_max accepted
 
 // Latched device error bits (combined with atomicOr into ctx->d_status).
@@ -97,6 +98,7 @@ struct Ctx {
   void *alloc_user = nullptr;
   int stack_cap = 0;           // walk stack entries allowed (0 = all); failure testing
   int sort_stall = 0;          // > 0: sort passes withhold tile 0, look-back budget (testing)
+  int moments_stall = 0;       // > 0: leaves not counted, moment-pass wait budget (testing)
   int grav_since = 0;          // leapfrog_step with grav_every > 1: steps since the last force
   cudaStream_t stream = nullptr;
   int num_sms = 0;

@@ -780,11 +780,14 @@ __global__ void k_oct_parent(int cap_nodes, int nseg, const int4 *__restrict__ t
 // GB300's FP64 pipe costs the same per warp instruction however many lanes are
 // active, so the pass runs on full, uniform warps: nodes are counting-sorted into
 // buckets (leaves by body count 1 .. 16 and more, so that the lanes of a warp loop
-// equally long; then internal nodes by depth, deepest first), leaves are done in
-// one launch and each depth level in one launch after the deeper levels.
+// equally long; then internal nodes by depth, deepest first); one launch does the
+// leaves, one more every internal depth, each after the deeper ones (k_level_moments).
 constexpr int kLeafBuckets = 17;
 constexpr int kBuckets = kLeafBuckets + kLevels;   // + internal depths 20 .. 0
-constexpr int kSlotCnt = 0, kSlotFill = 40, kSlotOff = 80;   // offsets into t.scalars
+// offsets into t.scalars: bucket counts, fill cursors, done counters of the moment pass
+// and its ticket (zeroed before each build), then the bucket offsets
+constexpr int kSlotCnt = 0, kSlotFill = 40, kSlotDone = 80, kSlotTicket = 120, kSlotOff = 128;
+constexpr int kMomBlocksPerSM = 1;             // internal levels: one warp per SM sub-partition
 
 struct MomArgs {
   const int4 *topo;
@@ -884,50 +887,48 @@ __device__ void write_records(const MomArgs &A, int id, double m, const double *
   }
 }
 
-__global__ void k_leaf_moments(MomArgs A) {
-  const uint32_t b0 = A.boff[0], b1 = A.boff[kLeafBuckets];
-  for (uint32_t k = b0 + blockIdx.x * blockDim.x + threadIdx.x; k < b1;
-       k += gridDim.x * blockDim.x) {
-    const int id = A.nlist[k];
-    const int4 t = A.topo[id];
-    if (t.z < 0 || t.w > A.n || t.z >= t.w) { latch_error(A.status, kErrTree); continue; }
-    double msum, com[3], T[6] = {0, 0, 0, 0, 0, 0};
-    if (t.w - t.z == 1) {
-      msum = A.mass_s[t.z];
-      for (int a = 0; a < 3; ++a) com[a] = A.pos_s[3 * t.z + a];
-    } else {
-      double sx = 0.0, sy = 0.0, sz = 0.0;
-      msum = 0.0;
+// Moments of one leaf from its bodies, in body order (mass, then m x, COM = sum / mass,
+// then the second moments about the COM).
+__device__ void leaf_node(const MomArgs &A, int id) {
+  const int4 t = A.topo[id];
+  if (t.z < 0 || t.w > A.n || t.z >= t.w) { latch_error(A.status, kErrTree); return; }
+  double msum, com[3], T[6] = {0, 0, 0, 0, 0, 0};
+  if (t.w - t.z == 1) {
+    msum = A.mass_s[t.z];
+    for (int a = 0; a < 3; ++a) com[a] = A.pos_s[3 * t.z + a];
+  } else {
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    msum = 0.0;
+    for (int i = t.z; i < t.w; ++i) {
+      const double mi = A.mass_s[i];
+      msum = da(msum, mi);
+      sx = da(sx, dm(mi, A.pos_s[3 * i]));
+      sy = da(sy, dm(mi, A.pos_s[3 * i + 1]));
+      sz = da(sz, dm(mi, A.pos_s[3 * i + 2]));
+    }
+    com[0] = __ddiv_rn(sx, msum); com[1] = __ddiv_rn(sy, msum); com[2] = __ddiv_rn(sz, msum);
+    if (A.order >= 2) {
       for (int i = t.z; i < t.w; ++i) {
         const double mi = A.mass_s[i];
-        msum = da(msum, mi);
-        sx = da(sx, dm(mi, A.pos_s[3 * i]));
-        sy = da(sy, dm(mi, A.pos_s[3 * i + 1]));
-        sz = da(sz, dm(mi, A.pos_s[3 * i + 2]));
-      }
-      com[0] = __ddiv_rn(sx, msum); com[1] = __ddiv_rn(sy, msum); com[2] = __ddiv_rn(sz, msum);
-      if (A.order >= 2) {
-        for (int i = t.z; i < t.w; ++i) {
-          const double mi = A.mass_s[i];
-          const double y0 = A.pos_s[3 * i] - com[0], y1 = A.pos_s[3 * i + 1] - com[1],
-                       y2 = A.pos_s[3 * i + 2] - com[2];
-          const double m0 = mi * y0, m1 = mi * y1, m2 = mi * y2;
-          T[0] = fma(m0, y0, T[0]); T[1] = fma(m1, y1, T[1]); T[2] = fma(m2, y2, T[2]);
-          T[3] = fma(m0, y1, T[3]); T[4] = fma(m0, y2, T[4]); T[5] = fma(m1, y2, T[5]);
-        }
+        const double y0 = A.pos_s[3 * i] - com[0], y1 = A.pos_s[3 * i + 1] - com[1],
+                     y2 = A.pos_s[3 * i + 2] - com[2];
+        const double m0 = mi * y0, m1 = mi * y1, m2 = mi * y2;
+        T[0] = fma(m0, y0, T[0]); T[1] = fma(m1, y1, T[1]); T[2] = fma(m2, y2, T[2]);
+        T[3] = fma(m0, y1, T[3]); T[4] = fma(m0, y2, T[4]); T[5] = fma(m1, y2, T[5]);
       }
     }
-    A.nmass[id] = msum;
-    for (int a = 0; a < 3; ++a) A.ncom[3 * id + a] = com[a];
-    if (A.order >= 2)
-      for (int a = 0; a < 6; ++a) A.nsec[6 * id + a] = T[a];
-    write_records(A, id, msum, com, T, t.w - t.z == 1);
   }
+  A.nmass[id] = msum;
+  for (int a = 0; a < 3; ++a) A.ncom[3 * id + a] = com[a];
+  if (A.order >= 2)
+    for (int a = 0; a < 6; ++a) A.nsec[6 * id + a] = T[a];
+  write_records(A, id, msum, com, T, t.w - t.z == 1);
 }
 
-// Internal nodes of one depth (bucket); their children are deeper, hence done.
-// All children's values are loaded up front (at most 8 children: independent loads
-// in flight together), then combined in octant order as before.
+// An internal node from its children, combined in octant order.  All children's values
+// are loaded up front (at most 8 children: independent loads in flight together), through
+// L2: they were written by other warps of the same launch, and an SM's L1 may hold an
+// older copy of their cache lines.
 __device__ void internal_node(const MomArgs &A, int id, int nn) {
   const int4 tp = A.topo[id];
   if (tp.x <= 0 || tp.y > 8 || tp.x + tp.y > nn) { latch_error(A.status, kErrTree); return; }
@@ -936,8 +937,9 @@ __device__ void internal_node(const MomArgs &A, int id, int nn) {
   for (int j = 0; j < 8; ++j) {
     const bool in = j < tp.y;
     const int c = in ? tp.x + j : tp.x;
-    cm[j] = in ? A.nmass[c] : 0.0;
-    cx[j] = A.ncom[3 * c]; cy[j] = A.ncom[3 * c + 1]; cz[j] = A.ncom[3 * c + 2];
+    cm[j] = in ? __ldcg(A.nmass + c) : 0.0;
+    cx[j] = __ldcg(A.ncom + 3 * c); cy[j] = __ldcg(A.ncom + 3 * c + 1);
+    cz[j] = __ldcg(A.ncom + 3 * c + 2);
   }
   double pm = 0.0, px = 0.0, py = 0.0, pz = 0.0;
 #pragma unroll
@@ -959,7 +961,7 @@ __device__ void internal_node(const MomArgs &A, int id, int nn) {
       for (int j = 0; j < 4; ++j) {
         const int c = (h + j < tp.y) ? tp.x + h + j : tp.x;
 #pragma unroll
-        for (int a = 0; a < 6; ++a) Tc[j][a] = A.nsec[6 * c + a];
+        for (int a = 0; a < 6; ++a) Tc[j][a] = __ldcg(A.nsec + 6 * c + a);
       }
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
@@ -981,14 +983,89 @@ __device__ void internal_node(const MomArgs &A, int id, int nn) {
   write_records(A, id, pm, pc, T, false);
 }
 
-// Internal nodes of one depth, one node per thread.
-__global__ void __launch_bounds__(128) k_level_moments(MomArgs A, int bucket) {
-  const uint32_t b0 = A.boff[bucket], b1 = A.boff[bucket + 1];
-  if (b0 >= b1) return;
-  const int nn = min(*A.nnodes, A.cap_nodes);
+// Leaves, one per thread (leaves of equal body counts share a warp).
+__global__ void __launch_bounds__(128) k_leaf_moments(MomArgs A) {
+  const uint32_t b0 = A.boff[0], b1 = A.boff[kLeafBuckets];
   for (uint32_t k = b0 + blockIdx.x * blockDim.x + threadIdx.x; k < b1;
        k += gridDim.x * blockDim.x)
-    internal_node(A, A.nlist[k], nn);
+    leaf_node(A, A.nlist[k]);
+}
+
+// Every internal node in one launch, after the leaves.  A work unit is up to 32 nodes of
+// one depth, one per lane (full, uniform warps: the FP64 pipe's cost per instruction does
+// not depend on the active lanes).  Warps take units from an atomic ticket, deepest depth
+// first.  A unit waits until the nearest deeper non-empty depth is complete; that depth's
+// units waited likewise before they started, so every node below, and in particular every
+// child, is done.  A unit waits only on units with smaller tickets, which running warps
+// hold, so the waits end; each is still bounded (on running out, kErrTimeout is latched
+// and the unit computed anyway, so later waits do not cascade), and polls back off
+// exponentially so that the waiting warps do not crowd the counter's L2 slice.  A negative
+// budget -k (failure testing) keeps the deepest depth from being counted, so the next
+// depth's wait runs out after k polls.
+// One node is ~290 FP64 instructions, and on GB300 an FP64 warp instruction occupies an SM
+// sub-partition's FP64 unit for ~64 cycles, so a depth takes as long as the busiest
+// sub-partition's units: one block of four warps per SM puts one warp on each
+// sub-partition, so a depth of up to 4 x SMs units takes one unit's time (~9 us).
+constexpr int kMomSpin = 1 << 18;              // polls allowed per wait (> 0.1 s)
+constexpr int kMomThreads = 128;
+
+__global__ void __launch_bounds__(kMomThreads, kMomBlocksPerSM)
+k_level_moments(MomArgs A, uint32_t *__restrict__ ticket, uint32_t *__restrict__ done,
+                int spin_budget) {
+  __shared__ uint32_t s_uoff[kLevels + 1];     // first unit of each depth bucket; total units
+  __shared__ int s_widx[kLevels];              // depth bucket a bucket's units wait on (-1: none)
+  __shared__ uint32_t s_wneed[kLevels];        // and its node count
+  if (threadIdx.x == 0) {
+    uint32_t u = 0;
+    int prev = -1;                             // latest non-empty depth bucket
+    for (int i = 0; i < kLevels; ++i) {
+      const int b = kLeafBuckets + i;
+      const uint32_t sz = A.boff[b + 1] - A.boff[b];
+      s_uoff[i] = u;
+      u += (sz + 31u) / 32u;
+      s_widx[i] = prev;
+      s_wneed[i] = prev < 0 ? 0u : A.boff[kLeafBuckets + prev + 1] - A.boff[kLeafBuckets + prev];
+      if (sz) prev = i;
+    }
+    s_uoff[kLevels] = u;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const uint32_t nunits = s_uoff[kLevels];
+  const int nn = min(*A.nnodes, A.cap_nodes);
+  const int budget = abs(spin_budget);
+  for (;;) {
+    uint32_t u = 0;
+    if (lane == 0) u = atomicAdd(ticket, 1u);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    if (u >= nunits) break;
+    // depth bucket of unit u = the number of bucket starts 1 .. kLevels-1 at or before it
+    const int i = __popc(__ballot_sync(0xffffffffu, 1 + lane < kLevels && s_uoff[1 + lane] <= u));
+    const int b = kLeafBuckets + i;
+    const uint32_t k0 = A.boff[b] + (u - s_uoff[i]) * 32u;
+    const uint32_t k1 = min(k0 + 32u, A.boff[b + 1]);
+    if (s_widx[i] >= 0) {
+      // every lane polls (one coalesced load): a wait taken by lane 0 alone left the
+      // warp running as two halves afterwards, doubling the FP64 time of the unit
+      const volatile uint32_t *w = done + s_widx[i];
+      const uint32_t need = s_wneed[i];
+      unsigned ns = 32;
+      for (int spin = 0; __any_sync(0xffffffffu, *w < need); ++spin) {
+        if (spin >= budget) {
+          if (lane == 0) latch_error(A.status, kErrTimeout);
+          break;
+        }
+        __nanosleep(ns);
+        ns = min(2u * ns, 1024u);
+      }
+      __threadfence();
+    }
+    const uint32_t k = k0 + (uint32_t)lane;
+    if (k < k1) internal_node(A, A.nlist[k], nn);
+    __threadfence();                            // this unit's moments before its count
+    __syncwarp();
+    if (lane == 0 && !(spin_budget < 0 && s_widx[i] < 0)) atomicAdd(done + i, k1 - k0);
+  }
 }
 
 // Cloud id of every body (caller order), one block per cloud.
@@ -1076,6 +1153,8 @@ int tree_build(Ctx *c, int64_t n, const double *pos, const double *mass) {
   }
   // a7: moments (bucketed by depth, full warps)
   GRAV_CUDA_TRY(cudaMemsetAsync(t.scalars + kSlotCnt, 0, sizeof(uint32_t) * kSlotOff, s));
+  static_assert(kSlotDone + kLevels <= kSlotTicket && kSlotOff + kBuckets + 1 <= kScalarWords,
+                "scalar slots overlap");
   const unsigned nb_nodes = blocks_for(cap_nodes, 256);
   k_bucket_count<<<nb_nodes, 256, 0, s>>>(t.topo, t.ndepth, t.nnodes, cap_nodes, t.scalars);
   ++c->launches;
@@ -1085,13 +1164,12 @@ int tree_build(Ctx *c, int64_t n, const double *pos, const double *mass) {
   MomArgs A{t.topo, t.ndepth, t.nnodes, t.nlist, t.scalars + kSlotOff, t.pos_s, t.mass_s,
             t.geom, multi ? sg.seg_sorted : nullptr, t.nmass, t.ncom, t.nquad, t.nrec0, t.nrec1,
             t.nquadf, c->params.order, cap_nodes, (int)n, c->d_status};
-  const unsigned grid = (unsigned)(4 * c->num_sms);
-  k_leaf_moments<<<grid, 128, 0, s>>>(A);
+  k_leaf_moments<<<(unsigned)(8 * c->num_sms), 128, 0, s>>>(A);
   ++c->launches;
-  for (int d = kLevels - 1; d >= 0; --d) {
-    k_level_moments<<<grid, 128, 0, s>>>(A, kLeafBuckets + (kLevels - 1 - d));
-    ++c->launches;
-  }
+  k_level_moments<<<(unsigned)(kMomBlocksPerSM * c->num_sms), kMomThreads, 0, s>>>(
+      A, t.scalars + kSlotTicket, t.scalars + kSlotDone,
+      c->moments_stall > 0 ? -c->moments_stall : kMomSpin);
+  ++c->launches;
   return cuda_status(cudaGetLastError());
 }
 

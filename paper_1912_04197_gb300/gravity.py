@@ -27,6 +27,7 @@ GRAVITY_ADJ_END = 1
 GRAVITY_ADJ_START = 2
 GRAVITY_DBGSET_STACK_CAP = 1
 GRAVITY_DBGSET_SORT_STALL = 2
+GRAVITY_DBGSET_MOMENTS_STALL = 3
 
 # gravity_alloc_fn / gravity_free_fn
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(ctypes.c_void_p), ctypes.c_size_t,

@@ -149,3 +149,22 @@ def test_sort_lookback_wait_runs_out_and_context_recovers(gpu):
         with pytest.raises(gpu.GravityError) as e:
             gpu.gravity_debug_set(ctx, gpu.GRAVITY_DBGSET_SORT_STALL, bad)
         assert e.value.code == gpu.GRAVITY_E_ARG
+
+
+def test_moments_level_wait_runs_out_and_context_recovers(gpu):
+    # the deepest internal depth is not counted, so the next depth's bounded wait in the
+    # one-launch pass over the internal nodes runs out: GRAVITY_E_TIMEOUT, no fault; the
+    # next build on the same context is bit-identical to a fresh context's
+    pos, _, m = inputs.clumpy_plummer(100_000, seed=9, nclusters=4)
+    ref = _forces(gpu, gpu.Context(0), pos, m, order=2, leaf_max=16)
+    ctx = gpu.Context(0)
+    gpu.gravity_debug_set(ctx, gpu.GRAVITY_DBGSET_MOMENTS_STALL, 16)
+    with pytest.raises(gpu.GravityError) as e:
+        _forces(gpu, ctx, pos, m, order=2, leaf_max=16)
+    assert e.value.code == gpu.GRAVITY_E_TIMEOUT
+    gpu.gravity_debug_set(ctx, gpu.GRAVITY_DBGSET_MOMENTS_STALL, 0)
+    assert np.array_equal(_forces(gpu, ctx, pos, m, order=2, leaf_max=16), ref)
+    for bad in (-1, (1 << 18) + 1):
+        with pytest.raises(gpu.GravityError) as e:
+            gpu.gravity_debug_set(ctx, gpu.GRAVITY_DBGSET_MOMENTS_STALL, bad)
+        assert e.value.code == gpu.GRAVITY_E_ARG
