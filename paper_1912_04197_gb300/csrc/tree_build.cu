@@ -4,7 +4,8 @@
 //   -> binary radix tree over the sorted keys -> compressed octree -> node mass and
 //   centre of mass, Eq. (COMinternal), bottom-up in FP64.
 // The paper builds its octree by insertion with locks (Burtscher-Pingali design);
-// here every step is a data-parallel pass with no lock and no spin-wait.
+// here every step is a data-parallel pass with no lock; the only waits (the sort's and
+// the octree scan's look-backs, the moment pass's depth order) are bounded.
 #include <cstdio>
 
 #include "internal.cuh"
