@@ -332,6 +332,21 @@ int gravity_forces_host(gravity_ctx *ctx, int64_t n, const double *pos_host,
                         const double *mass_host, double theta, double eps,
                         const gravity_params *p, double *acc_host);
 
+/* Host-buffer evaluation of nsnap independent snapshots of n bodies each: snapshot k
+ * has positions pos_host[k] (3n doubles) and masses mass_host[k] (n doubles), and its
+ * accelerations go to acc_host[k] (3n doubles); the pointers may repeat (ideally pinned
+ * memory).  Each snapshot's result is the one gravity_forces_host gives.  The copies of a
+ * snapshot run beside the tree build and walk of its neighbours: two device slots of
+ * inputs and outputs, a host-to-device and a device-to-host copy stream of the context
+ * (created on first use), ordered against the context's stream by events.  The tree left
+ * in the context is the last snapshot's.  Returns once every copy has finished, with any
+ * latched device error (on an error the remaining snapshots are not evaluated).
+ * GRAVITY_E_ARG for a null array or pointer, a negative count or bad theta / eps. */
+int gravity_forces_host_batch(gravity_ctx *ctx, int64_t nsnap, int64_t n,
+                              const double *const *pos_host, const double *const *mass_host,
+                              double theta, double eps, const gravity_params *p,
+                              double *const *acc_host);
+
 /* Wait for the context's stream, then return (and clear) the first latched device
  * error, or a CUDA error, or GRAVITY_OK. */
 int gravity_sync(gravity_ctx *ctx);

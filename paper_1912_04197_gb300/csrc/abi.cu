@@ -303,6 +303,15 @@ void free_all(Ctx *c) {
   ctx_release(c, c->diag_buf); c->diag_cap = 0;
   ctx_release(c, c->h2d_pos); ctx_release(c, c->h2d_mass); ctx_release(c, c->h2d_acc);
   c->h2d_cap = 0;
+  for (int k = 0; k < 2; ++k) {
+    ctx_release(c, c->bat_pos[k]); ctx_release(c, c->bat_mass[k]); ctx_release(c, c->bat_acc[k]);
+    cudaEvent_t *ev[4] = {&c->ev_in[k], &c->ev_built[k], &c->ev_walked[k], &c->ev_out[k]};
+    for (cudaEvent_t *e : ev)
+      if (*e) { cudaEventDestroy(*e); *e = nullptr; }
+  }
+  c->bat_cap = 0;
+  if (c->h2d_stream) { cudaStreamDestroy(c->h2d_stream); c->h2d_stream = nullptr; }
+  if (c->d2h_stream) { cudaStreamDestroy(c->d2h_stream); c->d2h_stream = nullptr; }
   ctx_release(c, c->comp_r); ctx_release(c, c->comp_i); c->comp_cap = 0;
   if (c->graph.exec) cudaGraphExecDestroy(c->graph.exec);
   c->graph = StepGraph{};
@@ -868,6 +877,88 @@ int gravity_forces_host(gravity_ctx *h, int64_t n, const double *pos_host, const
   if (n > 0)
     GRAV_CUDA_TRY(cudaMemcpyAsync(acc_host, c.h2d_acc, sizeof(double) * 3 * n,
                                   cudaMemcpyDeviceToHost, c.stream));
+  return gravity_sync(h);
+}
+
+int gravity_forces_host_batch(gravity_ctx *h, int64_t nsnap, int64_t n,
+                              const double *const *pos_host, const double *const *mass_host,
+                              double theta, double eps, const gravity_params *p,
+                              double *const *acc_host) {
+  grav::Range range_("gravity_forces_host_batch");
+  if (!h || nsnap < 0 || n < 0 || n > grav::kMaxBodies) return GRAVITY_E_ARG;
+  if (nsnap > 0 && (!pos_host || !mass_host || !acc_host)) return GRAVITY_E_ARG;
+  for (int64_t k = 0; k < nsnap && n > 0; ++k)
+    if (!pos_host[k] || !mass_host[k] || !acc_host[k]) return GRAVITY_E_ARG;
+  if (!(theta >= 0.0) || !(eps >= 0.0) || !std::isfinite(theta) || !std::isfinite(eps))
+    return GRAVITY_E_ARG;
+  int rc = grav::check_params(p);
+  if (rc) return rc;
+  Ctx &c = h->c;
+  if ((rc = grav::set_device(c))) return rc;
+  if (nsnap == 0) return GRAVITY_OK;
+  if (!c.h2d_stream) {
+    GRAV_CUDA_TRY(cudaStreamCreateWithFlags(&c.h2d_stream, cudaStreamNonBlocking));
+    GRAV_CUDA_TRY(cudaStreamCreateWithFlags(&c.d2h_stream, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k) {
+      cudaEvent_t *ev[4] = {&c.ev_in[k], &c.ev_built[k], &c.ev_walked[k], &c.ev_out[k]};
+      for (cudaEvent_t *e : ev) GRAV_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    }
+  }
+  if (n > c.bat_cap) {
+    GRAV_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    GRAV_CUDA_TRY(cudaStreamSynchronize(c.h2d_stream));
+    GRAV_CUDA_TRY(cudaStreamSynchronize(c.d2h_stream));
+    c.bat_cap = 0;
+    for (int k = 0; k < 2; ++k) {
+      grav::ctx_release(&c, c.bat_pos[k]); grav::ctx_release(&c, c.bat_mass[k]);
+      grav::ctx_release(&c, c.bat_acc[k]);
+    }
+    for (int k = 0; k < 2; ++k) {
+      if ((rc = grav::ctx_alloc(&c, c.bat_pos[k], 3 * n))) return rc;
+      if ((rc = grav::ctx_alloc(&c, c.bat_mass[k], n))) return rc;
+      if ((rc = grav::ctx_alloc(&c, c.bat_acc[k], 3 * n))) return rc;
+    }
+    c.bat_cap = n;
+  }
+  // snapshot k uses slot s = k mod 2: its inputs are copied in once the build of snapshot
+  // k - 2 has read that slot, its walk writes the slot's output once the copy-out of
+  // snapshot k - 2 has finished; so the copies of one snapshot run beside the build and
+  // walk of its neighbours (each wait names the event's latest record, that of k - 2)
+  const size_t bp = sizeof(double) * 3 * (size_t)n, bm = sizeof(double) * (size_t)n;
+  // (an error stops the enqueueing; the copies already in flight are waited for before
+  // returning, so the caller's host buffers are no longer in use)
+#define GRAV_BATCH_TRY(x) { const cudaError_t e_ = (x); if (e_ != cudaSuccess) { rc = grav::cuda_status(e_); break; } }
+  for (int64_t k = 0; k < nsnap && rc == GRAVITY_OK; ++k) {
+    const int s = (int)(k & 1);
+    if (k >= 2) GRAV_BATCH_TRY(cudaStreamWaitEvent(c.h2d_stream, c.ev_built[s], 0));
+    if (n > 0) {
+      GRAV_BATCH_TRY(cudaMemcpyAsync(c.bat_pos[s], pos_host[k], bp, cudaMemcpyHostToDevice,
+                                     c.h2d_stream));
+      GRAV_BATCH_TRY(cudaMemcpyAsync(c.bat_mass[s], mass_host[k], bm, cudaMemcpyHostToDevice,
+                                     c.h2d_stream));
+    }
+    GRAV_BATCH_TRY(cudaEventRecord(c.ev_in[s], c.h2d_stream));
+    GRAV_BATCH_TRY(cudaStreamWaitEvent(c.stream, c.ev_in[s], 0));
+    if ((rc = gravity_tree_build(h, n, c.bat_pos[s], c.bat_mass[s], p))) break;
+    GRAV_BATCH_TRY(cudaEventRecord(c.ev_built[s], c.stream));
+    if (k >= 2) GRAV_BATCH_TRY(cudaStreamWaitEvent(c.stream, c.ev_out[s], 0));
+    if ((rc = gravity_forces(h, theta, eps, c.bat_acc[s]))) break;
+    GRAV_BATCH_TRY(cudaEventRecord(c.ev_walked[s], c.stream));
+    GRAV_BATCH_TRY(cudaStreamWaitEvent(c.d2h_stream, c.ev_walked[s], 0));
+    if (n > 0)
+      GRAV_BATCH_TRY(cudaMemcpyAsync(acc_host[k], c.bat_acc[s], bp, cudaMemcpyDeviceToHost,
+                                     c.d2h_stream));
+    GRAV_BATCH_TRY(cudaEventRecord(c.ev_out[s], c.d2h_stream));
+  }
+#undef GRAV_BATCH_TRY
+  const cudaError_t e1 = cudaStreamSynchronize(c.h2d_stream);
+  const cudaError_t e2 = cudaStreamSynchronize(c.d2h_stream);
+  if (rc) {
+    cudaStreamSynchronize(c.stream);
+    return rc;
+  }
+  if (e1 != cudaSuccess) return grav::cuda_status(e1);
+  if (e2 != cudaSuccess) return grav::cuda_status(e2);
   return gravity_sync(h);
 }
 

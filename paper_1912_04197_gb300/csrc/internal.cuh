@@ -143,6 +143,14 @@ struct Ctx {
   // host-buffer entry point staging
   double *h2d_pos = nullptr, *h2d_mass = nullptr, *h2d_acc = nullptr;
   int64_t h2d_cap = 0;
+  // batched host-buffer evaluation: two slots of device inputs and outputs, a copy stream
+  // each way, and the events that order them against the context's stream
+  double *bat_pos[2] = {nullptr, nullptr}, *bat_mass[2] = {nullptr, nullptr};
+  double *bat_acc[2] = {nullptr, nullptr};
+  int64_t bat_cap = 0;
+  cudaStream_t h2d_stream = nullptr, d2h_stream = nullptr;
+  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_built[2] = {nullptr, nullptr};
+  cudaEvent_t ev_walked[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
   // contact components: sorted radii + 3 words; parent, component minimum, root, size
   double *comp_r = nullptr;
   int *comp_i = nullptr;

@@ -76,6 +76,7 @@ def _load() -> ctypes.CDLL:
         "leapfrog_step": (I, [P, I64, P, P, P, P, D, I, D, D, PP]),
         "leapfrog_adjoint": (I, [P, I64, P, P, P, D, I, D, D, PP, I, P, P]),
         "gravity_forces_host": (I, [P, I64, P, P, D, D, PP, P]),
+        "gravity_forces_host_batch": (I, [P, I64, I64, P, P, D, D, PP, P]),
         "gravity_sync": (I, [P]),
         "gravity_debug_export": (I, [P, I, P, ctypes.c_size_t]),
         "gravity_strerror": (ctypes.c_char_p, [I]),
@@ -391,6 +392,29 @@ def gravity_forces_host(ctx: Context, pos_host: torch.Tensor, mass_host: torch.T
                                     ctypes.c_void_p(mass_host.data_ptr()), float(theta),
                                     float(eps), None if p is None else ctypes.byref(p),
                                     ctypes.c_void_p(acc_host.data_ptr())), "gravity_forces_host")
+    return acc_host
+
+
+def gravity_forces_host_batch(ctx: Context, pos_host: list, mass_host: list, theta: float,
+                              eps: float, p, acc_host: list):
+    """Snapshots k = 0 .. K-1: pos_host[k] (n, 3), mass_host[k] (n,) -> acc_host[k] (n, 3),
+    all contiguous float64 host tensors (pinned for overlap); the copies of a snapshot
+    overlap the build and walk of its neighbours."""
+    k = len(pos_host)
+    if len(mass_host) != k or len(acc_host) != k:
+        raise ValueError("pos_host, mass_host and acc_host need one tensor per snapshot")
+    n = pos_host[0].shape[0] if k else 0
+    for name, ts in (("pos_host", pos_host), ("mass_host", mass_host), ("acc_host", acc_host)):
+        for t in ts:
+            if t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous() or t.shape[0] != n:
+                raise TypeError(f"{name} must hold contiguous float64 host tensors of {n} rows")
+    arr = ctypes.c_void_p * max(k, 1)
+    pp = arr(*[t.data_ptr() for t in pos_host])
+    mp = arr(*[t.data_ptr() for t in mass_host])
+    ap = arr(*[t.data_ptr() for t in acc_host])
+    _check(_lib.gravity_forces_host_batch(ctx.handle, k, n, pp, mp, float(theta), float(eps),
+                                          None if p is None else ctypes.byref(p), ap),
+           "gravity_forces_host_batch")
     return acc_host
 
 

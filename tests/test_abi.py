@@ -23,7 +23,8 @@ def test_header_declares_the_boundary():
     names = _declared()
     for want in ("gravity_create", "gravity_destroy", "gravity_tree_build", "gravity_forces",
                  "gravity_direct", "leapfrog_step", "gravity_sync", "gravity_strerror",
-                 "gravity_debug_export", "gravity_forces_host", "gravity_forces_vjp",
+                 "gravity_debug_export", "gravity_forces_host", "gravity_forces_host_batch",
+                 "gravity_forces_vjp",
                  "leapfrog_adjoint", "gravity_diagnostics", "gravity_set_allocator",
                  "gravity_debug_set", "gravity_set_clouds", "gravity_batch_tree_build"):
         assert want in names

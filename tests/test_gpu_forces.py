@@ -177,6 +177,30 @@ def test_host_entry_point(gpu):
     assert np.array_equal(ah.numpy(), a)
 
 
+def test_host_batch_entry_point(gpu):
+    # five different snapshots through the overlapped batch call (copies on their own
+    # streams, two device slots reused): each result equals the one-snapshot call's bit for
+    # bit; a repeated input pointer is allowed, and so is an empty batch
+    n = 20_000
+    snaps = [inputs.clumpy_plummer(n, seed=30 + k, nclusters=4) for k in range(4)]
+    snaps.append(snaps[1])
+    ph = [torch.tensor(s_[0]).pin_memory() for s_ in snaps]
+    mh = [torch.tensor(s_[2]).pin_memory() for s_ in snaps]
+    ah = [torch.full((n, 3), np.nan, dtype=torch.float64).pin_memory() for _ in snaps]
+    p = gpu.params(order=2, leaf_max=16)
+    ctx = gpu.Context(0)
+    gpu.gravity_forces_host_batch(ctx, ph, mh, 0.5, 1e-3, p, ah)
+    one = gpu.Context(0)
+    ref = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    for k in range(len(snaps)):
+        gpu.gravity_forces_host(one, ph[k], mh[k], 0.5, 1e-3, p, ref)
+        assert np.array_equal(ah[k].numpy(), ref.numpy()), k
+    gpu.gravity_forces_host_batch(ctx, [], [], 0.5, 1e-3, p, [])
+    with pytest.raises(gpu.GravityError) as e:
+        gpu.gravity_forces_host_batch(ctx, ph[:1], mh[:1], -1.0, 1e-3, p, ah[:1])
+    assert e.value.code == gpu.GRAVITY_E_ARG
+
+
 @pytest.mark.parametrize("clouds", [False, True])
 def test_leapfrog_graph_replay_matches_eager(gpu, clouds):
     # on a non-default stream leapfrog_step captures one step as a CUDA graph and
