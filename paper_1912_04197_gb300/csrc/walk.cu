@@ -102,12 +102,15 @@ struct WarpSmem {
 };
 
 // Vector-Jacobian product (order 0): far-list sources and the lane-to-source
-// transposition buffer (chunks of kVjpChunk entries, rows padded to 33 floats).
+// transposition buffer (chunks of kVjpChunk entries; rows of 36 floats, so that a row
+// starts on 16 bytes and the eight rows one quarter-warp reads as float4 fall in distinct
+// banks).
 constexpr int kVjpChunk = 8;
+constexpr int kVjpRow = 36;
 struct WarpSmemV {
   WarpSmem base;
   int32_t ftag[kListCap];         // node of each far entry
-  float vt[3][kVjpChunk][33];     // per component, entry and lane: the term's gradient
+  __align__(16) float vt[3][kVjpChunk][kVjpRow];   // per component, entry and lane: gradient
 };
 
 // Quadrupole lists hold -Q (see the moments pass): (xx, yy), (zz, xy), (xz, yz).
@@ -471,9 +474,17 @@ __device__ __forceinline__ void flush_vjp(WarpSmemV &V, int cnt, int lane, float
     __syncwarp();
     const int e = lane & (kVjpChunk - 1), comp = lane / kVjpChunk;
     if (comp < 3 && e < ce) {
-      float sum = 0.f;
-#pragma unroll 8
-      for (int jj = 0; jj < 32; ++jj) sum += V.vt[comp][e][jj];
+      // the 32 lanes' terms of this entry and component, read as eight float4 and summed
+      // as two packed pairs
+      const float4 *row = reinterpret_cast<const float4 *>(V.vt[comp][e]);
+      float2 sa = dup2(0.f), sb = dup2(0.f);
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        const float4 v = row[jj];
+        sa = add2(sa, xy2(v));
+        sb = add2(sb, zw2(v));
+      }
+      const float sum = (sa.x + sa.y) + (sb.x + sb.y);
       if (sum != 0.f) {
         const int tag = FAR ? V.ftag[c0 + e] : S.ltag[c0 + e];
         double *dst = (!FAR && tag >= 0) ? g_body + 3 * (int64_t)tag
@@ -1170,16 +1181,17 @@ int launch_walk(Ctx *c, WalkArgs A) {
   // split tasks when the tree has no more of them than a full GPU of warps, in four when it
   // has no more than half as many; the decision depends only on the whole tree's task count
   // and the SM count (not on the kernel variant, the launch shape or a range), so every
-  // variant and a range walk compute what the full walk does; the VJP splits in two at most
+  // variant and a range walk compute what the full walk does; the VJP adds its parts' own-term
+  // gradients with FP64 atomics (its source scatter is order-dependent in the last bits anyway)
   const int base_tasks = A.ntasks;
   const int basis = A.split_basis > 0 ? A.split_basis : base_tasks;
   const int slots = kSplitWarpsPerSM * c->num_sms;
-  A.split = !A.mac_guard ? 1 : (2 * basis <= slots && MODE != kModeVjp) ? 4 : basis <= slots ? 2 : 1;
+  A.split = !A.mac_guard ? 1 : 2 * basis <= slots ? 4 : basis <= slots ? 2 : 1;
   A.ntasks = base_tasks * A.split;
   const int rows = A.acc_sorted ? A.nrange : A.n;
   A.rows = rows;
   A.part = nullptr;
-  if (A.split == 4) {
+  if (A.split == 4 && MODE != kModeVjp) {
     const size_t need_part = (size_t)12 * rows;
     if (need_part > c->walk_part_cap) {
       GRAV_CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -1228,7 +1240,7 @@ int launch_walk(Ctx *c, WalkArgs A) {
   kern<<<blocks, 32 * kWalkWarps, smem, c->stream>>>(A);
   ++c->launches;
   GRAV_CUDA_TRY(cudaGetLastError());
-  if (A.split == 4) {
+  if (A.split == 4 && MODE != kModeVjp) {
     k_walk_finish<<<(unsigned)((rows + 255) / 256), 256, 0, c->stream>>>(
         A.part, rows, A.perm, A.acc_sorted ? nullptr : A.acc, A.acc_sorted, kick_vel, A.kick);
     ++c->launches;
