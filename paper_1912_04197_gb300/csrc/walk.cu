@@ -572,20 +572,40 @@ k_walk(WalkArgs A) {
   asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
   const int nq = A.nqueues;
   int q = (int)(smid % (unsigned)nq);
-  int visited = 0;
+  int visited = 0;                            // queues moved past (each found exhausted)
   for (;;) {
     int task = -1;
-    if (lane == 0) {
-      while (visited < nq) {
+    while (visited < nq) {
+      if (lane == 0) {
         const int qbeg = (int)(((long long)A.ntasks * q) / nq);
         const int qend = (int)(((long long)A.ntasks * (q + 1)) / nq);
-        const int t = qbeg + (int)atomicAdd(&A.task_counter[q], 1u);
-        if (t < qend) { task = t; break; }
-        q = (q + 1 == nq) ? 0 : q + 1;
-        ++visited;
+        if (qbeg < qend) {
+          const int t = qbeg + (int)atomicAdd(&A.task_counter[q], 1u);
+          if (t < qend) task = t;
+        }
       }
+      task = __shfl_sync(0xffffffffu, task, 0);
+      if (task >= 0) break;
+      // queue q is exhausted (counters only grow): read the counters of the queues after it
+      // 32 at a time from L2, without atomics, and go on to the first that still has tasks
+      int adv = 0;
+      for (int base = 1; base < nq - visited && adv == 0; base += 32) {
+        bool live = false;
+        if (base + lane < nq - visited) {
+          int qq = q + base + lane;
+          if (qq >= nq) qq -= nq;
+          const int qb = (int)(((long long)A.ntasks * qq) / nq);
+          const int qe = (int)(((long long)A.ntasks * (qq + 1)) / nq);
+          live = qb + (int)__ldcg(&A.task_counter[qq]) < qe;
+        }
+        const unsigned lv = __ballot_sync(0xffffffffu, live);
+        if (lv) adv = base + __ffs(lv) - 1;
+      }
+      if (adv == 0) { visited = nq; break; }
+      visited += adv;
+      q += adv;
+      if (q >= nq) q -= nq;
     }
-    task = __shfl_sync(0xffffffffu, task, 0);
     if (task < 0) break;
 
     // task: up to 32 consecutive bodies of one cloud; the walk starts at the cloud root
