@@ -65,6 +65,12 @@ int ctx_malloc(Ctx *c, void **p, size_t bytes) {
 
 void ctx_free(Ctx *c, void *p) {
   if (!p) return;
+  // the captured leapfrog step may hold this buffer's address: drop it, so that the next
+  // step runs eagerly and captures again on the buffers then current
+  if (c->graph.exec) {
+    cudaGraphExecDestroy(c->graph.exec);
+    c->graph = StepGraph{};
+  }
   if (c->user_free) c->user_free(p, c->alloc_user);
   else cudaFree(p);
 }
@@ -290,6 +296,8 @@ void free_all(Ctx *c) {
   ctx_release(c, c->walk_stats); ctx_release(c, c->walk_queues);
   ctx_release(c, c->walk_gstack); c->walk_gstack_cap = 0;
   ctx_release(c, c->walk_part); c->walk_part_cap = 0;
+  ctx_release(c, c->walk_cost); ctx_release(c, c->walk_order);
+  c->walk_order_cap = 0; c->walk_order_n = 0; c->walk_order_nq = 0;
   ctx_release(c, c->vjp_own); ctx_release(c, c->vjp_body); ctx_release(c, c->vjp_node);
   c->vjp_cap = 0;
   ctx_release(c, c->adj_levels); ctx_release(c, c->adj_work);

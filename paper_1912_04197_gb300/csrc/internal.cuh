@@ -116,6 +116,13 @@ struct Ctx {
   size_t walk_gstack_cap = 0;                 // in 8-byte entries
   double *walk_part = nullptr;                // four-way split walk: partial sums
   size_t walk_part_cap = 0;                   // in doubles
+  // walk task order: the SM clock cycles each task took in the last full force walk, and
+  // each task queue's tasks in decreasing order of that cost for the next one
+  uint32_t *walk_cost = nullptr;
+  int32_t *walk_order = nullptr;
+  int64_t walk_order_cap = 0;                 // tasks the two arrays hold
+  int walk_order_n = 0;                       // tasks (after splitting) the order is for
+  int walk_order_nq = 0;                      // and the queues it is for
   // vector-Jacobian product scratch (sorted order; nodes 2 cap)
   double *vjp_own = nullptr, *vjp_body = nullptr, *vjp_node = nullptr;
   int64_t vjp_cap = 0;

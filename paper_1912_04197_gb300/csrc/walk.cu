@@ -167,6 +167,8 @@ struct WalkArgs {
   unsigned *status;
   int max_iter;
   unsigned *task_counter;         // [nqueues] per-queue counters, zeroed before the launch
+  const int32_t *order;           // full force walk: the task of each queue slot (else null)
+  uint32_t *cost;                 // full force walk: SM clock cycles each task took (else null)
   int nqueues;
   int flush_at;
   int stack_cap;                  // stack entries allowed (<= kStackCap)
@@ -607,6 +609,9 @@ k_walk(WalkArgs A) {
       if (q >= nq) q -= nq;
     }
     if (task < 0) break;
+    if (A.order) task = A.order[task];          // the queue's tasks, costliest first
+    const int slot_task = task;
+    const long long t_task = A.cost ? clock64() : 0;
 
     // task: up to 32 consecutive bodies of one cloud; the walk starts at the cloud root
     const int part = A.split > 1 ? task % A.split : 0;
@@ -1131,6 +1136,8 @@ k_walk(WalkArgs A) {
         A.counts[3 * ci + 2] = c_tests;
       }
     }
+    if (A.cost && lane == 0)
+      A.cost[slot_task] = (uint32_t)min(clock64() - t_task, (long long)0xFFFFFFFFu);
   }
 }
 
@@ -1164,6 +1171,54 @@ __global__ void k_walk_finish(const double *__restrict__ part, int rows,
     vel[3 * ci] = __dadd_rn(vel[3 * ci], __dmul_rn(kick, a[0]));
     vel[3 * ci + 1] = __dadd_rn(vel[3 * ci + 1], __dmul_rn(kick, a[1]));
     vel[3 * ci + 2] = __dadd_rn(vel[3 * ci + 2], __dmul_rn(kick, a[2]));
+  }
+}
+
+// Task order of the next full force walk: the tasks of each queue (the queues' contiguous
+// ranges of the task list) sorted by the cycles they took in the last one, costliest first
+// (ties by task index), so that the long tasks start early and the queue ends with short
+// ones.  The order decides only which warp takes a task when: every task computes the same
+// result wherever it runs.  A queue of more than kOrderMax tasks keeps its order.
+constexpr int kOrderMax = 4096;
+__global__ void __launch_bounds__(512) k_order_tasks(const uint32_t *__restrict__ cost,
+                                                     int32_t *__restrict__ order, int ntasks,
+                                                     int nq) {
+  __shared__ unsigned long long key[kOrderMax];
+  const int q = blockIdx.x;
+  const int qbeg = (int)(((long long)ntasks * q) / nq);
+  const int qend = (int)(((long long)ntasks * (q + 1)) / nq);
+  const int m = qend - qbeg;
+  if (m <= 1 || m > kOrderMax) return;
+  int p2 = 1;
+  while (p2 < m) p2 <<= 1;
+  // key: cost in the high word, the complement of the task index in the low word (so that
+  // a descending sort puts equal costs in ascending index order); pads are 0 and sort last
+  for (int i = threadIdx.x; i < p2; i += blockDim.x)
+    key[i] = i < m ? ((unsigned long long)cost[qbeg + i] << 32) | (0xFFFFFFFFu - (unsigned)(qbeg + i))
+                   : 0ull;
+  __syncthreads();
+  for (int k = 2; k <= p2; k <<= 1) {              // bitonic sort, descending
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < p2; i += blockDim.x) {
+        const int l = i ^ j;
+        if (l > i) {
+          const unsigned long long a = key[i], b = key[l];
+          const bool desc = (i & k) == 0;
+          if (desc ? a < b : a > b) { key[i] = b; key[l] = a; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < m; i += blockDim.x)
+    order[qbeg + i] = (int32_t)(0xFFFFFFFFu - (unsigned)(key[i] & 0xFFFFFFFFull));
+}
+
+// Identity task order and zero costs (a new task count or queue count).
+__global__ void k_order_reset(int32_t *__restrict__ order, uint32_t *__restrict__ cost, int ntasks) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ntasks; i += gridDim.x * blockDim.x) {
+    order[i] = i;
+    cost[i] = 0u;
   }
 }
 
@@ -1257,9 +1312,44 @@ int launch_walk(Ctx *c, WalkArgs A) {
   A.gstack = reinterpret_cast<uint2 *>(c->walk_gstack);
   A.nqueues = shape.one_queue ? 1 : c->num_sms;
   GRAV_CUDA_TRY(cudaMemsetAsync(A.task_counter, 0, sizeof(unsigned) * A.nqueues, c->stream));
+  // a full force walk takes its tasks in the order the last one's costs give and records
+  // its own; the range, counted and VJP walks take them in index order
+  A.order = nullptr;
+  A.cost = nullptr;
+  const bool ordered = MODE == kModeForce && A.task0 == 0 && !A.acc_sorted;
+  if (ordered) {
+    if (A.ntasks > c->walk_order_cap) {
+      GRAV_CUDA_TRY(cudaStreamSynchronize(c->stream));
+      ctx_release(c, c->walk_cost);
+      ctx_release(c, c->walk_order);
+      c->walk_order_cap = 0;
+      c->walk_order_n = 0;
+      int rc = ctx_alloc(c, c->walk_cost, (int64_t)A.ntasks);
+      if (rc == GRAVITY_OK) rc = ctx_alloc(c, c->walk_order, (int64_t)A.ntasks);
+      if (rc) return rc;
+      c->walk_order_cap = A.ntasks;
+    }
+    if (c->walk_order_n != A.ntasks || c->walk_order_nq != A.nqueues) {
+      const int tb = 256;
+      const int gb = (int)std::min<int64_t>((A.ntasks + tb - 1) / tb, 4 * (int64_t)c->num_sms);
+      k_order_reset<<<gb > 0 ? gb : 1, tb, 0, c->stream>>>(c->walk_order, c->walk_cost, A.ntasks);
+      ++c->launches;
+      GRAV_CUDA_TRY(cudaGetLastError());
+      c->walk_order_n = A.ntasks;
+      c->walk_order_nq = A.nqueues;
+    }
+    A.order = c->walk_order;
+    A.cost = c->walk_cost;
+  }
   kern<<<blocks, 32 * kWalkWarps, smem, c->stream>>>(A);
   ++c->launches;
   GRAV_CUDA_TRY(cudaGetLastError());
+  if (ordered) {
+    k_order_tasks<<<A.nqueues, 512, 0, c->stream>>>(c->walk_cost, c->walk_order, A.ntasks,
+                                                    A.nqueues);
+    ++c->launches;
+    GRAV_CUDA_TRY(cudaGetLastError());
+  }
   if (A.split == 4 && MODE != kModeVjp) {
     k_walk_finish<<<(unsigned)((rows + 255) / 256), 256, 0, c->stream>>>(
         A.part, rows, A.perm, A.acc_sorted ? nullptr : A.acc, A.acc_sorted, kick_vel, A.kick);

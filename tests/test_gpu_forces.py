@@ -233,6 +233,66 @@ def test_leapfrog_graph_replay_matches_eager(gpu, clouds):
         assert np.array_equal(x, y)
 
 
+def test_task_order_from_costs_keeps_results(gpu):
+    # a full force walk takes each task queue's tasks in the order of the cycles they took
+    # in the previous walk (costliest first): which warp runs a task, and when, must change
+    # no result, so later walks equal the first (index-order) walk bit for bit, and so does
+    # the counted walk (which keeps index order)
+    pos, _, m = inputs.clumpy_plummer(200_000, seed=3, nclusters=16)
+    ctx = gpu.Context(0)
+    P = torch.tensor(pos, device="cuda")
+    M = torch.tensor(m, device="cuda")
+    gpu.gravity_tree_build(ctx, P, M, gpu.params(order=2, leaf_max=16))
+    first = None
+    for _ in range(3):
+        A = torch.full_like(P, float("nan"))
+        gpu.gravity_forces(ctx, 0.5, 1e-3, A)
+        gpu.gravity_sync(ctx)
+        if first is None:
+            first = A.cpu().numpy()
+            assert np.isfinite(first).all()
+        else:
+            assert np.array_equal(A.cpu().numpy(), first)
+    A = torch.full_like(P, float("nan"))
+    C = torch.empty((len(pos), 3), dtype=torch.int32, device="cuda")
+    gpu.gravity_forces_counted(ctx, 0.5, 1e-3, A, C)
+    gpu.gravity_sync(ctx)
+    assert np.array_equal(A.cpu().numpy(), first)
+
+
+def test_leapfrog_graph_dropped_when_buffers_grow(gpu):
+    # a larger tree on the same context reallocates the buffers a captured leapfrog step
+    # refers to; the captured step must be dropped (and captured again), so that stepping
+    # the first problem afterwards equals stepping it without the interleaved call
+    pos, vel, m = inputs.rubble_pile(5_000, seed=4)
+    big, _, mbig = inputs.clumpy_plummer(120_000, seed=5, nclusters=8)
+    out = []
+    for interleave in (False, True):
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            ctx = gpu.Context(0)
+            P = torch.tensor(pos, device="cuda")
+            V = torch.tensor(vel, device="cuda")
+            M = torch.tensor(m, device="cuda")
+            A = torch.empty_like(P)
+            p = gpu.params(order=2, leaf_max=16, use_graph=1)
+            gpu.gravity_tree_build(ctx, P, M, p)
+            gpu.gravity_forces(ctx, 0.5, 1e-3, A)
+            gpu.leapfrog_step(ctx, P, V, M, A, 1e-3, 6, 0.5, 1e-3, p)    # captures a step
+            if interleave:
+                PB = torch.tensor(big, device="cuda")
+                MB = torch.tensor(mbig, device="cuda")
+                AB = torch.empty_like(PB)
+                gpu.gravity_tree_build(ctx, PB, MB, p)                # buffers grow
+                gpu.gravity_forces(ctx, 0.5, 1e-3, AB)
+            gpu.leapfrog_step(ctx, P, V, M, A, 1e-3, 6, 0.5, 1e-3, p)
+            gpu.gravity_sync(ctx)
+        stream.synchronize()
+        out.append((P.cpu().numpy(), V.cpu().numpy(), A.cpu().numpy()))
+    for x, y in zip(out[0], out[1]):
+        assert np.array_equal(x, y)
+
+
 @pytest.mark.parametrize("mac_guard", [1, 0])
 def test_opening_band_on_a_lattice(gpu, mac_guard):
     # A 17^3 lattice on [0, 1]^3 (root side 1): depth-3 cells (side 1/8) hold 2x2x2 bodies
