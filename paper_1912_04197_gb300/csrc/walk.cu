@@ -29,8 +29,10 @@
 //     add and multiply of sm_100 and later: one issue slot for two operations);
 //   * each flushed list's partial sum enters a (hi, lo) two-sum accumulator (or an
 //     FP64 one).
-// The kernel is persistent: each warp takes 32-body tasks from an atomic counter,
-// and owns an overflow area in global memory for the deep part of its stack.  When
+// The kernel is persistent: each warp takes 32-body tasks from per-SM task queues (atomic
+// counters; the queues of a full force walk hold their tasks costliest first, by the cycles
+// each took in the previous one), and owns an overflow area in global memory for the deep
+// part of its stack.  When
 // there are too few tasks to fill the GPU (small N), each task is split in two or four:
 // warps walk the same 32 bodies, each from its share of the root's children (the root
 // contains every body, so the guard opens it for all of them); two partial sums are added
