@@ -375,6 +375,84 @@ k_rs_sweep(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
   }
 }
 
+// The same sort for at most one tile (n <= kRsTile): one block runs every pass in shared
+// memory, ranking each pass exactly as a tile of k_rs_sweep does (warp match on the digit,
+// items in index order), so the result is the same stable permutation without the
+// per-pass launches and look-backs.  (keys, idx) are sorted in place.
+__global__ void __launch_bounds__(kRsThreads)
+k_rs_small(uint64_t *__restrict__ keys, uint32_t *__restrict__ idx, int n, int cloud_passes,
+           const int32_t *__restrict__ seg_of) {
+  constexpr int W = kRsThreads / 32;
+  __shared__ uint32_t s_w[W][256];      // per-warp digit counts, then exclusive bases
+  __shared__ uint32_t s_tloc[256];      // exclusive digit offsets of the tile
+  __shared__ uint32_t s_tmp[W];
+  __shared__ uint64_t s_key[kRsTile];
+  __shared__ uint32_t s_val[kRsTile];
+  const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
+  const unsigned lt = (1u << l) - 1u;
+  for (int i = tid; i < n; i += kRsThreads) {
+    s_key[i] = keys[i];
+    s_val[i] = idx[i];
+  }
+  const int np = 8 + cloud_passes;
+  for (int pass = 0; pass < np; ++pass) {
+    const bool cl = pass >= 8;
+    const int shift = cl ? 8 * (pass - 8) : 8 * pass;
+    for (int ww = 0; ww < W; ++ww) s_w[ww][tid] = 0;
+    __syncthreads();
+    uint64_t key[kRsItems];
+    uint32_t val[kRsItems], pos[kRsItems];
+    unsigned dig[kRsItems];
+#pragma unroll
+    for (int k = 0; k < kRsItems; ++k) {
+      const int i = w * (32 * kRsItems) + k * 32 + l;
+      const bool valid = i < n;
+      key[k] = valid ? s_key[i] : 0ull;
+      val[k] = valid ? s_val[i] : 0u;
+      dig[k] = valid ? rs_digit(key[k], val[k], shift, cl ? seg_of : nullptr) : 256u;
+    }
+#pragma unroll
+    for (int k = 0; k < kRsItems; ++k) {
+      const unsigned d = dig[k];
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      const int leader = __ffs(peers) - 1;
+      uint32_t before = 0;
+      if (l == leader && d < 256u) {
+        before = s_w[w][d];
+        s_w[w][d] = before + __popc(peers);
+      }
+      before = __shfl_sync(0xffffffffu, before, leader);
+      pos[k] = before + __popc(peers & lt);
+      __syncwarp();
+    }
+    __syncthreads();
+    uint32_t run = 0;                           // thread = digit: warp bases, tile count
+    for (int ww = 0; ww < W; ++ww) {
+      const uint32_t c = s_w[ww][tid];
+      s_w[ww][tid] = run;
+      run += c;
+    }
+    s_tloc[tid] = block_excl_scan256(run, s_tmp);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kRsItems; ++k) {
+      const unsigned d = dig[k];
+      if (d < 256u) {
+        const uint32_t lp = s_tloc[d] + s_w[w][d] + pos[k];
+        if (lp < (uint32_t)kRsTile) {          // always true for consistent counts
+          s_key[lp] = key[k];
+          s_val[lp] = val[k];
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < n; i += kRsThreads) {
+    keys[i] = s_key[i];
+    idx[i] = s_val[i];
+  }
+}
+
 // 8 passes over the 63-bit keys, then (several clouds) stable passes over the cloud
 // ids, so the order is by cloud, then key, then caller index.  Sorts (keys, idx) in
 // place; keys_alt / idx_alt are the other halves of the ping-pong, hist the counts
@@ -394,6 +472,11 @@ int radix_sort_buffers(Ctx *c, int64_t n, uint64_t *keys, uint64_t *keys_alt, ui
                                 sizeof(uint32_t) * ((size_t)(256 + 1) * kRsMaxPasses +
                                                     (size_t)np * ntiles * 256 +
                                                     (size_t)extra_zero_words), c->stream));
+  if (n <= kRsTile && c->sort_stall == 0) {   // one tile: every pass in one block
+    k_rs_small<<<1, kRsThreads, 0, c->stream>>>(keys, idx, (int)n, cloud_passes, seg_of);
+    ++c->launches;
+    return cuda_status(cudaGetLastError());
+  }
   int cb = (int)((n + kRsThreads - 1) / kRsThreads);
   if (cb > 2 * c->num_sms) cb = 2 * c->num_sms;
   k_rs_count<<<cb, kRsThreads, 0, c->stream>>>(keys, n, 8, cloud_passes, seg_of, ghist, vb);

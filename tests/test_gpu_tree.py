@@ -26,17 +26,20 @@ def _cases():
         "sphere2085": inputs.uniform_sphere(2085, seed=1),          # ragged tail
         "clumpy100k": inputs.clumpy_plummer(100_003, seed=2, nclusters=16),
         "cube_dups": _dups(),
+        "cube_dups_1tile": _dups(1500),                            # the one-block sort
+        "sphere17": inputs.uniform_sphere(17, seed=4),
     }
 
 
-def _dups():
-    pos, vel, m = inputs.uniform_cube(5000, seed=3)
+def _dups(n=5000):
+    pos, vel, m = inputs.uniform_cube(n, seed=3)
     pos[100:400] = pos[7]                                          # identical keys
-    pos[1000:1003] = pos[2000]
+    pos[1000:1003] = pos[n - 7]
     return pos, vel, m
 
 
-@pytest.mark.parametrize("case", ["sphere2048", "sphere2085", "clumpy100k", "cube_dups"])
+@pytest.mark.parametrize("case", ["sphere2048", "sphere2085", "clumpy100k", "cube_dups",
+                                  "cube_dups_1tile", "sphere17"])
 def test_keys_and_order_bitexact(gpu, case):
     pos, _, m = _cases()[case]
     ctx = _build(gpu, pos, m)
@@ -52,7 +55,7 @@ def test_keys_and_order_bitexact(gpu, case):
     assert np.array_equal(keys, okeys[operm])
 
 
-@pytest.mark.parametrize("case", ["sphere2085", "clumpy100k", "cube_dups"])
+@pytest.mark.parametrize("case", ["sphere2085", "clumpy100k", "cube_dups", "cube_dups_1tile"])
 @pytest.mark.parametrize("leaf_max", [1, 8, 16])
 def test_topology_bitexact(gpu, case, leaf_max):
     pos, _, m = _cases()[case]
@@ -75,7 +78,7 @@ def test_topology_bitexact(gpu, case, leaf_max):
     assert parent[0] == -1
 
 
-@pytest.mark.parametrize("case", ["sphere2085", "clumpy100k", "cube_dups"])
+@pytest.mark.parametrize("case", ["sphere2085", "clumpy100k", "cube_dups", "cube_dups_1tile"])
 @pytest.mark.parametrize("leaf_max,order", [(1, 0), (8, 2), (16, 2)])
 def test_moments_bitexact(gpu, case, leaf_max, order):
     pos, _, m = _cases()[case]
