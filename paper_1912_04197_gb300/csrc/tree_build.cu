@@ -378,27 +378,25 @@ k_rs_sweep(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
 // The same sort for at most one tile (n <= kRsTile): one block runs every pass in shared
 // memory, ranking each pass exactly as a tile of k_rs_sweep does (warp match on the digit,
 // items in index order), so the result is the same stable permutation without the
-// per-pass launches and look-backs.  (keys, idx) are sorted in place.
-__global__ void __launch_bounds__(kRsThreads)
-k_rs_small(uint64_t *__restrict__ keys, uint32_t *__restrict__ idx, int n, int cloud_passes,
-           const int32_t *__restrict__ seg_of) {
+// per-pass launches and look-backs.  The (key, value) pairs are in s_key / s_val on entry
+// and on exit.
+struct RsSmall {
+  uint32_t w[kRsThreads / 32][256];     // per-warp digit counts, then exclusive bases
+  uint32_t tloc[256];                   // exclusive digit offsets of the tile
+  uint32_t tmp[kRsThreads / 32];
+  uint64_t key[kRsTile];
+  uint32_t val[kRsTile];
+};
+__device__ void rs_small_passes(RsSmall &S, int n, int cloud_passes,
+                                const int32_t *__restrict__ seg_of) {
   constexpr int W = kRsThreads / 32;
-  __shared__ uint32_t s_w[W][256];      // per-warp digit counts, then exclusive bases
-  __shared__ uint32_t s_tloc[256];      // exclusive digit offsets of the tile
-  __shared__ uint32_t s_tmp[W];
-  __shared__ uint64_t s_key[kRsTile];
-  __shared__ uint32_t s_val[kRsTile];
   const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
   const unsigned lt = (1u << l) - 1u;
-  for (int i = tid; i < n; i += kRsThreads) {
-    s_key[i] = keys[i];
-    s_val[i] = idx[i];
-  }
   const int np = 8 + cloud_passes;
   for (int pass = 0; pass < np; ++pass) {
     const bool cl = pass >= 8;
     const int shift = cl ? 8 * (pass - 8) : 8 * pass;
-    for (int ww = 0; ww < W; ++ww) s_w[ww][tid] = 0;
+    for (int ww = 0; ww < W; ++ww) S.w[ww][tid] = 0;
     __syncthreads();
     uint64_t key[kRsItems];
     uint32_t val[kRsItems], pos[kRsItems];
@@ -407,8 +405,8 @@ k_rs_small(uint64_t *__restrict__ keys, uint32_t *__restrict__ idx, int n, int c
     for (int k = 0; k < kRsItems; ++k) {
       const int i = w * (32 * kRsItems) + k * 32 + l;
       const bool valid = i < n;
-      key[k] = valid ? s_key[i] : 0ull;
-      val[k] = valid ? s_val[i] : 0u;
+      key[k] = valid ? S.key[i] : 0ull;
+      val[k] = valid ? S.val[i] : 0u;
       dig[k] = valid ? rs_digit(key[k], val[k], shift, cl ? seg_of : nullptr) : 256u;
     }
 #pragma unroll
@@ -418,8 +416,8 @@ k_rs_small(uint64_t *__restrict__ keys, uint32_t *__restrict__ idx, int n, int c
       const int leader = __ffs(peers) - 1;
       uint32_t before = 0;
       if (l == leader && d < 256u) {
-        before = s_w[w][d];
-        s_w[w][d] = before + __popc(peers);
+        before = S.w[w][d];
+        S.w[w][d] = before + __popc(peers);
       }
       before = __shfl_sync(0xffffffffu, before, leader);
       pos[k] = before + __popc(peers & lt);
@@ -428,28 +426,88 @@ k_rs_small(uint64_t *__restrict__ keys, uint32_t *__restrict__ idx, int n, int c
     __syncthreads();
     uint32_t run = 0;                           // thread = digit: warp bases, tile count
     for (int ww = 0; ww < W; ++ww) {
-      const uint32_t c = s_w[ww][tid];
-      s_w[ww][tid] = run;
+      const uint32_t c = S.w[ww][tid];
+      S.w[ww][tid] = run;
       run += c;
     }
-    s_tloc[tid] = block_excl_scan256(run, s_tmp);
+    S.tloc[tid] = block_excl_scan256(run, S.tmp);
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < kRsItems; ++k) {
       const unsigned d = dig[k];
       if (d < 256u) {
-        const uint32_t lp = s_tloc[d] + s_w[w][d] + pos[k];
+        const uint32_t lp = S.tloc[d] + S.w[w][d] + pos[k];
         if (lp < (uint32_t)kRsTile) {          // always true for consistent counts
-          s_key[lp] = key[k];
-          s_val[lp] = val[k];
+          S.key[lp] = key[k];
+          S.val[lp] = val[k];
         }
       }
     }
     __syncthreads();
   }
-  for (int i = tid; i < n; i += kRsThreads) {
-    keys[i] = s_key[i];
-    idx[i] = s_val[i];
+}
+
+// Sort of (keys, idx) in place when n <= kRsTile (several clouds: cloud_passes > 0).
+__global__ void __launch_bounds__(kRsThreads)
+k_rs_small(uint64_t *__restrict__ keys, uint32_t *__restrict__ idx, int n, int cloud_passes,
+           const int32_t *__restrict__ seg_of) {
+  __shared__ RsSmall S;
+  for (int i = threadIdx.x; i < n; i += kRsThreads) {
+    S.key[i] = keys[i];
+    S.val[i] = idx[i];
+  }
+  rs_small_passes(S, n, cloud_passes, seg_of);
+  for (int i = threadIdx.x; i < n; i += kRsThreads) {
+    keys[i] = S.key[i];
+    idx[i] = S.val[i];
+  }
+}
+
+// One cloud of n <= kRsTile bodies: root cube (as k_bbox: per-axis min / max of the
+// coordinates' order-preserving integer images, the side and scale by the same IEEE
+// operations, non-finite coordinates latched), Morton keys (as k_keys) and the sort, in one
+// block.
+__global__ void __launch_bounds__(kRsThreads)
+k_order_small(const double *__restrict__ pos, int n, double *__restrict__ geom,
+              uint64_t *__restrict__ keys, uint32_t *__restrict__ idx, unsigned *status) {
+  __shared__ RsSmall S;
+  __shared__ double s_geom[5];
+  unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
+  bool bad = false;
+  const unsigned long long *p64 = reinterpret_cast<const unsigned long long *>(pos);
+  for (int i = threadIdx.x; i < 3 * n; i += kRsThreads) {
+    const unsigned long long v = p64[i];
+    bad |= ((v >> 52) & 0x7FFull) == 0x7FFull;
+    const unsigned long long k = (v >> 63) ? ~v : (v | 0x8000000000000000ull);
+    const int a = i % 3;
+    lo[a] = umin64(lo[a], k);
+    hi[a] = umax64(hi[a], k);
+  }
+  bad = __syncthreads_or(bad);
+  block_minmax(lo, hi);
+  if (threadIdx.x == 0) {
+    if (bad) latch_error(status, kErrNonFinite);
+    double glo[3], ghi[3];
+    for (int a = 0; a < 3; ++a) { glo[a] = of_ord(lo[a]); ghi[a] = of_ord(hi[a]); }
+    double side = 0.0;
+    for (int a = 0; a < 3; ++a) side = fmax(side, __dsub_rn(ghi[a], glo[a]));
+    if (n <= 1 || !(side > 0.0) || !isfinite(side)) side = 1.0;
+    for (int a = 0; a < 3; ++a) s_geom[a] = geom[a] = isfinite(glo[a]) ? glo[a] : 0.0;
+    s_geom[3] = geom[3] = side;
+    s_geom[4] = geom[4] = __ddiv_rn(2097152.0, side);   // 2^21 / side, one IEEE division
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += kRsThreads) {
+    const uint32_t qx = grid_coord(pos[3 * i + 0], s_geom[0], s_geom[4]);
+    const uint32_t qy = grid_coord(pos[3 * i + 1], s_geom[1], s_geom[4]);
+    const uint32_t qz = grid_coord(pos[3 * i + 2], s_geom[2], s_geom[4]);
+    S.key[i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+    S.val[i] = (uint32_t)i;
+  }
+  rs_small_passes(S, n, 0, nullptr);
+  for (int i = threadIdx.x; i < n; i += kRsThreads) {
+    keys[i] = S.key[i];
+    idx[i] = S.val[i];
   }
 }
 
@@ -1184,21 +1242,30 @@ int tree_build(Ctx *c, int64_t n, const double *pos, const double *mass) {
   cudaStream_t s = c->stream;
   const int leaf_max = c->params.leaf_max;
   const bool multi = sg.nseg > 1;
-  // a1: root cube of each cloud (also validates the coordinates)
-  if (!multi) {
-    launch_bbox(c, pos, n, reinterpret_cast<unsigned long long *>(t.bbox_part), t.bbox_ticket,
-                t.geom);
-  } else {
-    k_bbox_seg<<<sg.nseg, kBBoxThreads, 0, s>>>(pos, sg.off, t.geom, c->d_status);
+  int rc = GRAVITY_OK;
+  if (!multi && n <= kRsTile && c->sort_stall == 0) {
+    // a1-a3 for one cloud that fits one sort tile: root cube, keys and sort in one block
+    // (the octree scan's tile states, kept after the sort's words, are cleared here)
+    GRAV_CUDA_TRY(cudaMemsetAsync(oct_scan_state(c, n), 0, sizeof(uint32_t) * oct_scan_words(n), s));
+    k_order_small<<<1, kRsThreads, 0, s>>>(pos, (int)n, t.geom, t.keys, t.idx, c->d_status);
     ++c->launches;
+  } else {
+    // a1: root cube of each cloud (also validates the coordinates)
+    if (!multi) {
+      launch_bbox(c, pos, n, reinterpret_cast<unsigned long long *>(t.bbox_part), t.bbox_ticket,
+                  t.geom);
+    } else {
+      k_bbox_seg<<<sg.nseg, kBBoxThreads, 0, s>>>(pos, sg.off, t.geom, c->d_status);
+      ++c->launches;
+    }
+    // a2: keys
+    k_keys<<<blocks_for(n, 256), 256, 0, s>>>(pos, n, t.geom, multi ? sg.seg_of : nullptr,
+                                               t.keys, t.idx);
+    ++c->launches;
+    // a3: sort (by cloud, then key, then caller index)
+    rc = radix_sort(c, n);
+    if (rc) return rc;
   }
-  // a2: keys
-  k_keys<<<blocks_for(n, 256), 256, 0, s>>>(pos, n, t.geom, multi ? sg.seg_of : nullptr, t.keys,
-                                             t.idx);
-  ++c->launches;
-  // a3: sort (by cloud, then key, then caller index)
-  int rc = radix_sort(c, n);
-  if (rc) return rc;
   // a4: gather sorted bodies
   k_gather<<<blocks_for(n, 256), 256, 0, s>>>(pos, mass, t.idx, n, t.pos_s, t.mass_s, t.body_hi,
                                                t.body_lo, multi ? sg.seg_of : nullptr,
