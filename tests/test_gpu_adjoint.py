@@ -1,6 +1,8 @@
 """Adjoint on the GPU: the frozen-tree vector-Jacobian product against the oracle's,
 the checkpointed leapfrog reverse pass against the oracle's reverse pass on the same
-positions, and the gradient of the axis-ratio loss against finite differences.
+positions, the whole adjoint against central differences of the frozen-decision map around
+the GPU trajectory (theta > 0), and the gradient of the axis-ratio loss against finite
+differences.
 
 Tolerances.  The product's terms are FP32 (hi/lo or warp-relative coordinates, as the
 forces), summed per body with two-sum compensation and per source by a 32-lane FP32
@@ -12,6 +14,7 @@ import pytest
 import torch
 
 import oracle
+from util import PARITY_RECORDS
 from paper_1912_04197_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -201,3 +204,56 @@ def test_loss_gradient_vs_finite_differences(gpu, theta):
         rel = np.abs(fd - ad) / scale
         assert np.all(rel <= 1e-4), (rel, fd, ad)
         assert abs(fd[-1] - ad[-1]) <= 1e-3 * abs(ad[-1])   # along the gradient, plain relative
+
+
+@pytest.mark.parametrize("theta,leaf_max", [(0.5, 1), (0.7, 8)])
+def test_adjoint_matches_frozen_differences_on_gpu_trajectory(gpu, theta, leaf_max):
+    # The GPU adjoint differentiates the GPU leapfrog with every step's opening decisions
+    # frozen at that step's tree.  The oracle builds the same trees from the GPU levels (the
+    # GPU's decisions are the FP64 ones, so they are the same decisions), and a KDK run whose
+    # forces come from those frozen trees at the perturbed positions is a smooth map of
+    # (x0, v0): its central differences are the derivative the adjoint must give, with no
+    # decision flips in between.  The GPU products carry FP32 term rounding (<= 5e-6 of
+    # each product's magnitudes), so the directional derivatives must agree to 1e-4 of
+    # their own size along the gradient, and to 1e-5 of the magnitude sum along random
+    # directions.
+    from paper_1912_04197_gb300.adjoint import leapfrog
+    pos, vel, m = inputs.rubble_pile(1500, seed=33)
+    dt, eps, nsteps = 1e-3, 5e-3, 12
+    levels, _, _ = _levels_gpu(gpu, pos, vel, m, dt, nsteps, theta, eps, leaf_max)
+    rng = np.random.default_rng(34)
+    cx, cv = rng.standard_normal(pos.shape), rng.standard_normal(pos.shape)
+    x0 = torch.tensor(pos, device="cuda", requires_grad=True)
+    v0 = torch.tensor(vel, device="cuda", requires_grad=True)
+    M = torch.tensor(m, device="cuda")
+    x, v = leapfrog(x0, v0, M, dt, nsteps, theta=theta, eps=eps, leaf_max=leaf_max,
+                    checkpoint_every=5)
+    gx, gv = torch.autograd.grad((x, v), (x0, v0), (torch.tensor(cx, device="cuda"),
+                                                    torch.tensor(cv, device="cuda")))
+    gx, gv = gx.cpu().numpy(), gv.cpu().numpy()
+    trees = [oracle.Tree(xk, m, leaf_max=leaf_max) for xk in levels]
+
+    def L(xa, va):
+        xa, va = xa.copy(), va.copy()
+        a = oracle.tree_forces_frozen(trees[0], xa, theta, eps)
+        for k in range(nsteps):
+            va = va + (0.5 * dt) * a
+            xa = xa + dt * va
+            a = oracle.tree_forces_frozen(trees[k + 1], xa, theta, eps)
+            va = va + (0.5 * dt) * a
+        return (cx * xa).sum() + (cv * va).sum()
+
+    h = 1e-6
+    dirs = [(rng.standard_normal(pos.shape), rng.standard_normal(pos.shape)) for _ in range(3)]
+    dirs.append((gx, gv))
+    rels = []
+    PARITY_RECORDS[f"adjoint_vs_frozen_differences_theta{theta}_leaf{leaf_max}"] = rels
+    for k, (ex, ev) in enumerate(dirs):
+        fd = (L(pos + h * ex, vel + h * ev) - L(pos - h * ex, vel - h * ev)) / (2 * h)
+        an = (gx * ex).sum() + (gv * ev).sum()
+        if k == len(dirs) - 1:
+            rels.append(abs(fd - an) / abs(an))
+            assert rels[-1] <= 1e-4, (rels, fd, an)
+        else:
+            rels.append(abs(fd - an) / (np.abs(gx * ex).sum() + np.abs(gv * ev).sum()))
+            assert rels[-1] <= 1e-5, (rels, fd, an)
