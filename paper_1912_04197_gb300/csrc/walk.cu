@@ -33,11 +33,11 @@
 // counters; the queues of a full force walk hold their tasks costliest first, by the cycles
 // each took in the previous one), and owns an overflow area in global memory for the deep
 // part of its stack.  When
-// there are too few tasks to fill the GPU (small N), each task is split in two or four:
-// warps walk the same 32 bodies, each from its share of the root's children (the root
+// there are too few tasks to fill the GPU (small N), each task is split in two, four or
+// eight: warps walk the same 32 bodies, each from its share of the root's children (the root
 // contains every body, so the guard opens it for all of them); two partial sums are added
 // to the zeroed output with FP64 atomics (two addends: the result does not depend on their
-// order), four are written to scratch and added in a fixed order by a closing pass.
+// order), four or eight are written to scratch and added in a fixed order by a closing pass.
 // A second mode computes the vector-Jacobian product of the accelerations on the
 // same decisions (see flush_vjp and k_vjp_finish); a third counts decisions and
 // collects walk statistics.
@@ -154,7 +154,7 @@ struct WalkArgs {
   int n;
   int ntasks;                     // tasks after splitting (base tasks x split)
   int split;                      // 1, 2 or 4 warps per base task (see above)
-  double *part;                   // split 4: partial sums [4][rows][3] (rows = n or nrange)
+  double *part;                   // split 4 or 8: partial sums [split][rows][3] (rows = n or nrange)
   int rows;
   float theta2f;
   double theta2d;
@@ -1143,10 +1143,10 @@ k_walk(WalkArgs A) {
   }
 }
 
-// Four-way split: the parts' partial sums added in a fixed order (so results do not depend
+// Four- or eight-way split: the parts' partial sums added in a fixed order (so results do not depend
 // on which warp finished first), written in caller order (or as range rows), with the
 // leapfrog's closing kick when asked for.
-__global__ void k_walk_finish(const double *__restrict__ part, int rows,
+__global__ void k_walk_finish(const double *__restrict__ part, int rows, int nparts,
                               const uint32_t *__restrict__ perm, double *__restrict__ acc,
                               double *__restrict__ acc_sorted, double *__restrict__ vel,
                               double kick) {
@@ -1156,8 +1156,9 @@ __global__ void k_walk_finish(const double *__restrict__ part, int rows,
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const double *p = part + 3 * (int64_t)i + k;
-    a[k] = __dadd_rn(__dadd_rn(__dadd_rn(p[0], p[3 * (int64_t)rows]), p[6 * (int64_t)rows]),
-                     p[9 * (int64_t)rows]);
+    double sum = p[0];
+    for (int q = 1; q < nparts; ++q) sum = __dadd_rn(sum, p[3 * (int64_t)q * rows]);
+    a[k] = sum;
   }
   if (acc_sorted) {
     acc_sorted[3 * (int64_t)i] = a[0];
@@ -1256,20 +1257,21 @@ int launch_walk(Ctx *c, WalkArgs A) {
   if (bps < 1) bps = 1;
   int blocks = bps * c->num_sms;
   // split tasks when the tree has no more of them than a full GPU of warps, in four when it
-  // has no more than half as many; the decision depends only on the whole tree's task count
+  // has no more than half as many, in eight when no more than a quarter; the decision
+  // depends only on the whole tree's task count
   // and the SM count (not on the kernel variant, the launch shape or a range), so every
   // variant and a range walk compute what the full walk does; the VJP adds its parts' own-term
   // gradients with FP64 atomics (its source scatter is order-dependent in the last bits anyway)
   const int base_tasks = A.ntasks;
   const int basis = A.split_basis > 0 ? A.split_basis : base_tasks;
   const int slots = kSplitWarpsPerSM * c->num_sms;
-  A.split = !A.mac_guard ? 1 : 2 * basis <= slots ? 4 : basis <= slots ? 2 : 1;
+  A.split = !A.mac_guard ? 1 : 4 * basis <= slots ? 8 : 2 * basis <= slots ? 4 : basis <= slots ? 2 : 1;
   A.ntasks = base_tasks * A.split;
   const int rows = A.acc_sorted ? A.nrange : A.n;
   A.rows = rows;
   A.part = nullptr;
-  if (A.split == 4 && MODE != kModeVjp) {
-    const size_t need_part = (size_t)12 * rows;
+  if (A.split >= 4 && MODE != kModeVjp) {
+    const size_t need_part = (size_t)3 * A.split * rows;
     if (need_part > c->walk_part_cap) {
       GRAV_CUDA_TRY(cudaStreamSynchronize(c->stream));
       ctx_release(c, c->walk_part);
@@ -1352,9 +1354,10 @@ int launch_walk(Ctx *c, WalkArgs A) {
     ++c->launches;
     GRAV_CUDA_TRY(cudaGetLastError());
   }
-  if (A.split == 4 && MODE != kModeVjp) {
+  if (A.split >= 4 && MODE != kModeVjp) {
     k_walk_finish<<<(unsigned)((rows + 255) / 256), 256, 0, c->stream>>>(
-        A.part, rows, A.perm, A.acc_sorted ? nullptr : A.acc, A.acc_sorted, kick_vel, A.kick);
+        A.part, rows, A.split, A.perm, A.acc_sorted ? nullptr : A.acc, A.acc_sorted, kick_vel,
+        A.kick);
     ++c->launches;
     return cuda_status(cudaGetLastError());
   }
