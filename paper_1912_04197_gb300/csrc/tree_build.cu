@@ -466,7 +466,8 @@ k_rs_small(uint64_t *__restrict__ keys, uint32_t *__restrict__ idx, int n, int c
 // One cloud of n <= kRsTile bodies: root cube (as k_bbox: per-axis min / max of the
 // coordinates' order-preserving integer images, the side and scale by the same IEEE
 // operations, non-finite coordinates latched), Morton keys (as k_keys) and the sort, in one
-// block.
+// block.  The sort is a bitonic network on (key, caller index): the pairs are distinct, so
+// their ascending order is exactly the stable order by key.
 __global__ void __launch_bounds__(kRsThreads)
 k_order_small(const double *__restrict__ pos, int n, double *__restrict__ geom,
               uint64_t *__restrict__ keys, uint32_t *__restrict__ idx, unsigned *status) {
@@ -504,7 +505,30 @@ k_order_small(const double *__restrict__ pos, int n, double *__restrict__ geom,
     S.key[i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
     S.val[i] = (uint32_t)i;
   }
-  rs_small_passes(S, n, 0, nullptr);
+  int p2 = 1;
+  while (p2 < n) p2 <<= 1;
+  for (int i = n + threadIdx.x; i < p2; i += kRsThreads) {   // pads sort last
+    S.key[i] = ~0ull;
+    S.val[i] = ~0u;
+  }
+  __syncthreads();
+  for (int k = 2; k <= p2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < p2; i += kRsThreads) {
+        const int l = i ^ j;
+        if (l > i) {
+          const uint64_t ka = S.key[i], kb = S.key[l];
+          const uint32_t va = S.val[i], vb = S.val[l];
+          const bool gt = ka > kb || (ka == kb && va > vb);
+          if (gt == ((i & k) == 0)) {             // ascending where bit k of i is 0
+            S.key[i] = kb; S.key[l] = ka;
+            S.val[i] = vb; S.val[l] = va;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
   for (int i = threadIdx.x; i < n; i += kRsThreads) {
     keys[i] = S.key[i];
     idx[i] = S.val[i];
