@@ -72,7 +72,9 @@ typedef struct gravity_params {
                           table of walk launch shapes (autotuner use) */
   int32_t use_graph;   /* leapfrog_step with nsteps > 2 on a non-default stream: 1 (default)
                           = capture one step as a CUDA graph and replay it, 0 = launch
-                          every kernel of every step */
+                          every kernel of every step.  The captured step is dropped, and
+                          captured again by the next call, whenever the context frees a
+                          device buffer (a larger tree, another call's scratch) */
   int32_t grav_every;  /* leapfrog_step only: evaluate gravity every grav_every-th step and hold
                           the last acceleration in between (the two time steps of Sec. 4.1:
                           a stepper at the contact step dt with gravity every Delta t_g, Eq.
