@@ -15,8 +15,8 @@ from util import check_parity, oracle_node_order, preorder_from_oracle, preorder
 pytestmark = pytest.mark.gpu
 
 
-def _ensemble(seed=3):
-    off, pos, vel, m = inputs.ensemble(nclouds=21, seed=seed, nmin=64, nmax=4096)
+def _ensemble(seed=3, nclouds=21, nmax=4096):
+    off, pos, vel, m = inputs.ensemble(nclouds=nclouds, seed=seed, nmin=64, nmax=nmax)
     # odd cases: a one-body cloud, a two-body cloud, a cloud of coincident bodies
     extra = [np.array([[0.3, -0.2, 0.1]]), np.array([[0.0, 0.0, 0.0], [0.5, 0.5, 0.5]]),
              np.tile([[1.0, 2.0, 3.0]], (40, 1))]
@@ -36,9 +36,11 @@ def _build(g, off, pos, m, **kw):
     return ctx
 
 
-@pytest.mark.parametrize("leaf_max,order", [(1, 0), (8, 2)])
-def test_batch_tree_per_cloud_bitexact(gpu, leaf_max, order):
-    off, pos, _, m = _ensemble()
+@pytest.mark.parametrize("leaf_max,order,small", [(1, 0, False), (8, 2, False), (1, 0, True)])
+def test_batch_tree_per_cloud_bitexact(gpu, leaf_max, order, small):
+    # small: 8 clouds of fewer than 2048 bodies in all, sorted by one block (cloud passes too)
+    off, pos, _, m = _ensemble(nclouds=8, nmax=300) if small else _ensemble()
+    assert (len(pos) <= 2048) == small
     K = len(off) - 1
     ctx = _build(gpu, off, pos, m, leaf_max=leaf_max, order=order)
     n = len(pos)
