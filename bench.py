@@ -664,7 +664,8 @@ def run_ours(args, rank, world, local_rank):
                "h2d_bytes_per_step": int(ph[0].nbytes + mh[0].nbytes),
                "d2h_bytes_per_step": int(ah[0].nbytes), "ms_per_step": 1e3 * te, "steps": ke,
                "api": "gravity_forces_host_batch (%d snapshots in pinned host buffers; each step's "
-                      "copies overlap its neighbours' build and walk)" % ke,
+                      "copies overlap its neighbours' build and walk, and the context and its "
+                      "internal twin take alternate snapshots)" % ke,
                "single_call": {"value": whole_job_value(n, world, 1e3 * t1), "ms_per_step": 1e3 * t1,
                                "api": "gravity_forces_host (copy in, build, walk, copy out, wait)"}}
 

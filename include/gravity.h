@@ -340,9 +340,14 @@ int gravity_forces_host(gravity_ctx *ctx, int64_t n, const double *pos_host,
  * memory).  Each snapshot's result is the one gravity_forces_host gives.  The copies of a
  * snapshot run beside the tree build and walk of its neighbours: two device slots of
  * inputs and outputs, a host-to-device and a device-to-host copy stream of the context
- * (created on first use), ordered against the context's stream by events.  The tree left
- * in the context is the last snapshot's.  Returns once every copy has finished, with any
- * latched device error (on an error the remaining snapshots are not evaluated).
+ * (created on first use), ordered against the compute streams by events.  With two
+ * snapshots or more (one cloud), every other snapshot is evaluated by a second context
+ * that this one creates on first use, with its own tree, walk buffers and stream and the
+ * same allocator: one snapshot's build runs while the other's walk finishes (the twin
+ * holds as much device memory as this context; it is released by gravity_destroy and
+ * gravity_set_allocator).  The tree left in the context is the last snapshot's.  Returns
+ * once every copy has finished, with any latched device error of either context (on an
+ * error the remaining snapshots are not evaluated).
  * GRAVITY_E_ARG for a null array or pointer, a negative count or bad theta / eps. */
 int gravity_forces_host_batch(gravity_ctx *ctx, int64_t nsnap, int64_t n,
                               const double *const *pos_host, const double *const *mass_host,

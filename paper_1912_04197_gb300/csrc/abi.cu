@@ -12,6 +12,11 @@
 
 struct gravity_ctx {
   grav::Ctx c;
+  // gravity_forces_host_batch: a second context with its own tree and stream, created on
+  // first use, that evaluates every other snapshot, so that one snapshot's build and the
+  // start of its walk run while the other's walk finishes
+  gravity_ctx *twin = nullptr;
+  cudaStream_t twin_stream = nullptr;
 };
 
 namespace grav {
@@ -369,10 +374,22 @@ int gravity_create(gravity_ctx **out, int device, void *cuda_stream) {
   return GRAVITY_OK;
 }
 
+static void drop_twin(gravity_ctx *h) {
+  if (h->twin) {
+    gravity_destroy(h->twin);
+    h->twin = nullptr;
+  }
+  if (h->twin_stream) {
+    cudaStreamDestroy(h->twin_stream);
+    h->twin_stream = nullptr;
+  }
+}
+
 int gravity_destroy(gravity_ctx *h) {
   if (!h) return GRAVITY_OK;
   Ctx &c = h->c;
   cudaSetDevice(c.device);
+  drop_twin(h);
   cudaStreamSynchronize(c.stream);
   grav::free_all(&c);
   cudaGetLastError();
@@ -387,6 +404,7 @@ int gravity_set_allocator(gravity_ctx *h, gravity_alloc_fn alloc, gravity_free_f
   int rc = grav::set_device(c);
   if (rc) return rc;
   GRAV_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  drop_twin(h);                             // made again, on the new allocator, when needed
   grav::free_all(&c);                       // with the allocator that made each buffer
   const gravity_alloc_fn old_alloc = c.user_alloc;
   const gravity_free_fn old_free = c.user_free;
@@ -928,10 +946,30 @@ int gravity_forces_host_batch(gravity_ctx *h, int64_t nsnap, int64_t n,
     }
     c.bat_cap = n;
   }
-  // snapshot k uses slot s = k mod 2: its inputs are copied in once the build of snapshot
-  // k - 2 has read that slot, its walk writes the slot's output once the copy-out of
-  // snapshot k - 2 has finished; so the copies of one snapshot run beside the build and
-  // walk of its neighbours (each wait names the event's latest record, that of k - 2)
+  // two engines take turns (one cloud, two snapshots or more): this context and its twin,
+  // each with its own tree, walk buffers and stream; the last snapshot goes to this context,
+  // so the tree left here is the last snapshot's
+  gravity_ctx *eng[2] = {h, h};
+  if (nsnap >= 2 && n > 0 && c.seg.nseg <= 1) {
+    if (!h->twin) {
+      if (!h->twin_stream)
+        GRAV_CUDA_TRY(cudaStreamCreateWithFlags(&h->twin_stream, cudaStreamNonBlocking));
+      gravity_ctx *t = nullptr;
+      if ((rc = gravity_create(&t, c.device, h->twin_stream))) return rc;
+      if (c.user_alloc && (rc = gravity_set_allocator(t, c.user_alloc, c.user_free, c.alloc_user))) {
+        gravity_destroy(t);
+        return rc;
+      }
+      h->twin = t;
+    }
+    eng[(nsnap - 1) & 1] = h;                 // slot of the last snapshot
+    eng[nsnap & 1] = h->twin;
+  }
+  // snapshot k uses slot s = k mod 2 and engine eng[s]: its inputs are copied in once the
+  // build of snapshot k - 2 has read that slot, its walk writes the slot's output once the
+  // copy-out of snapshot k - 2 has finished; so the copies of one snapshot run beside the
+  // build and walk of its neighbours (each wait names the event's latest record, that of
+  // k - 2)
   const size_t bp = sizeof(double) * 3 * (size_t)n, bm = sizeof(double) * (size_t)n;
   // (an error stops the enqueueing; the copies already in flight are waited for before
   // returning, so the caller's host buffers are no longer in use)
@@ -945,13 +983,15 @@ int gravity_forces_host_batch(gravity_ctx *h, int64_t nsnap, int64_t n,
       GRAV_BATCH_TRY(cudaMemcpyAsync(c.bat_mass[s], mass_host[k], bm, cudaMemcpyHostToDevice,
                                      c.h2d_stream));
     }
+    gravity_ctx *e = eng[s];
+    const cudaStream_t cs = e->c.stream;
     GRAV_BATCH_TRY(cudaEventRecord(c.ev_in[s], c.h2d_stream));
-    GRAV_BATCH_TRY(cudaStreamWaitEvent(c.stream, c.ev_in[s], 0));
-    if ((rc = gravity_tree_build(h, n, c.bat_pos[s], c.bat_mass[s], p))) break;
-    GRAV_BATCH_TRY(cudaEventRecord(c.ev_built[s], c.stream));
-    if (k >= 2) GRAV_BATCH_TRY(cudaStreamWaitEvent(c.stream, c.ev_out[s], 0));
-    if ((rc = gravity_forces(h, theta, eps, c.bat_acc[s]))) break;
-    GRAV_BATCH_TRY(cudaEventRecord(c.ev_walked[s], c.stream));
+    GRAV_BATCH_TRY(cudaStreamWaitEvent(cs, c.ev_in[s], 0));
+    if ((rc = gravity_tree_build(e, n, c.bat_pos[s], c.bat_mass[s], p))) break;
+    GRAV_BATCH_TRY(cudaEventRecord(c.ev_built[s], cs));
+    if (k >= 2) GRAV_BATCH_TRY(cudaStreamWaitEvent(cs, c.ev_out[s], 0));
+    if ((rc = gravity_forces(e, theta, eps, c.bat_acc[s]))) break;
+    GRAV_BATCH_TRY(cudaEventRecord(c.ev_walked[s], cs));
     GRAV_BATCH_TRY(cudaStreamWaitEvent(c.d2h_stream, c.ev_walked[s], 0));
     if (n > 0)
       GRAV_BATCH_TRY(cudaMemcpyAsync(acc_host[k], c.bat_acc[s], bp, cudaMemcpyDeviceToHost,
@@ -963,10 +1003,15 @@ int gravity_forces_host_batch(gravity_ctx *h, int64_t nsnap, int64_t n,
   const cudaError_t e2 = cudaStreamSynchronize(c.d2h_stream);
   if (rc) {
     cudaStreamSynchronize(c.stream);
+    if (eng[0] != eng[1]) cudaStreamSynchronize(h->twin_stream);
     return rc;
   }
   if (e1 != cudaSuccess) return grav::cuda_status(e1);
   if (e2 != cudaSuccess) return grav::cuda_status(e2);
+  if (eng[0] != eng[1] && (rc = gravity_sync(h->twin))) {
+    gravity_sync(h);
+    return rc;
+  }
   return gravity_sync(h);
 }
 

@@ -179,8 +179,9 @@ def test_host_entry_point(gpu):
 
 def test_host_batch_entry_point(gpu):
     # five different snapshots through the overlapped batch call (copies on their own
-    # streams, two device slots reused): each result equals the one-snapshot call's bit for
-    # bit; a repeated input pointer is allowed, and so is an empty batch
+    # streams, two device slots reused, two engines taking turns): each result equals the
+    # one-snapshot call's bit for bit; a repeated input pointer is allowed, and so is an
+    # empty batch
     n = 20_000
     snaps = [inputs.clumpy_plummer(n, seed=30 + k, nclusters=4) for k in range(4)]
     snaps.append(snaps[1])
@@ -195,6 +196,16 @@ def test_host_batch_entry_point(gpu):
     for k in range(len(snaps)):
         gpu.gravity_forces_host(one, ph[k], mh[k], 0.5, 1e-3, p, ref)
         assert np.array_equal(ah[k].numpy(), ref.numpy()), k
+    # every other snapshot runs on the context's internal twin; the tree left in the
+    # context is the last snapshot's, for an odd and an even count
+    keys = lambda c: gpu.gravity_debug_export(c, gpu.DBG_KEYS, n)
+    assert np.array_equal(keys(ctx), keys(one))
+    ah4 = [torch.full((n, 3), np.nan, dtype=torch.float64).pin_memory() for _ in range(4)]
+    gpu.gravity_forces_host_batch(ctx, ph[:4], mh[:4], 0.5, 1e-3, p, ah4)
+    for k in range(4):
+        assert np.array_equal(ah4[k].numpy(), ah[k].numpy()), k
+    gpu.gravity_forces_host(one, ph[3], mh[3], 0.5, 1e-3, p, ref)
+    assert np.array_equal(keys(ctx), keys(one))
     gpu.gravity_forces_host_batch(ctx, [], [], 0.5, 1e-3, p, [])
     with pytest.raises(gpu.GravityError) as e:
         gpu.gravity_forces_host_batch(ctx, ph[:1], mh[:1], -1.0, 1e-3, p, ah[:1])
