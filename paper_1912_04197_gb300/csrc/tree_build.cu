@@ -17,9 +17,7 @@ constexpr int kBBoxThreads = 256;
 constexpr int kRsThreads = 256;
 constexpr int kRsItems = 8;
 constexpr int kRsTile = kRsThreads * kRsItems;   // keys per radix tile
-constexpr int kOctThreads = 256;                 // octree count + scan: threads per tile,
-constexpr int kOctItems = 4;                     //   nodes per thread,
-constexpr int kOctTile = kOctThreads * kOctItems;  //   binary nodes per tile
+constexpr int kOctTile = 1024;                   // octree count + scan: binary nodes per tile
 
 __device__ __forceinline__ int cap_depth(int plen) {
   int d = plen / 3;
@@ -732,7 +730,9 @@ __device__ __forceinline__ int cdepth(int plen, int cbits) {
 
 // Children count of every binary node (0 unless it is an internal octree cell), fused with
 // the exclusive scan that gives each cell the first octree id of its children: each block
-// claims the next tile of kOctTile binary nodes in order (kOctItems per thread), scans it,
+// claims the next tile of kOctTile binary nodes in order (ITEMS consecutive nodes per thread:
+// 4 for many tiles, 1 for a few, where the latency of each thread's chain of dependent loads
+// is the kernel's time), scans it,
 // publishes its total, and its first warp finds the sum of the earlier tiles by a decoupled
 // look-back, 32 predecessors per round (a bounded wait on tiles not yet published: those
 // were claimed earlier by running blocks, which publish before they wait themselves).  The
@@ -766,7 +766,8 @@ __device__ __forceinline__ uint32_t oct_children(int X, int n, int leaf_max, int
   return (uint32_t)f.count;
 }
 
-__global__ void __launch_bounds__(kOctThreads)
+template <int ITEMS>
+__global__ void __launch_bounds__(kOctTile / ITEMS)
 k_oct_count(int n, int leaf_max, int cbits, const int32_t *__restrict__ child,
             const int32_t *__restrict__ parent, const int32_t *__restrict__ first,
             const int32_t *__restrict__ last, const int32_t *__restrict__ plen,
@@ -774,16 +775,17 @@ k_oct_count(int n, int leaf_max, int cbits, const int32_t *__restrict__ child,
             uint32_t *__restrict__ tstate, unsigned *__restrict__ tile_counter, int ntiles,
             unsigned *status) {
   __shared__ int s_tile;
+  constexpr int kOctThreads = kOctTile / ITEMS;
   __shared__ uint32_t s_warp[kOctThreads / 32];
   __shared__ uint32_t s_excl;
   if (threadIdx.x == 0) s_tile = (int)atomicAdd(tile_counter, 1u);
   __syncthreads();
   const int tile = s_tile;
   if (tile >= ntiles) return;
-  const int X0 = tile * kOctTile + threadIdx.x * kOctItems;   // kOctItems consecutive nodes
-  uint32_t cnt[kOctItems], sum = 0;
+  const int X0 = tile * kOctTile + threadIdx.x * ITEMS;   // ITEMS consecutive nodes
+  uint32_t cnt[ITEMS], sum = 0;
 #pragma unroll
-  for (int k = 0; k < kOctItems; ++k) {
+  for (int k = 0; k < ITEMS; ++k) {
     const int X = X0 + k;
     cnt[k] = X < n - 1 ? oct_children(X, n, leaf_max, cbits, child, parent, first, last, plen,
                                       status) : 0u;
@@ -842,7 +844,7 @@ k_oct_count(int n, int leaf_max, int cbits, const int32_t *__restrict__ child,
   __syncthreads();
   uint32_t pre = s_excl + s_warp[w] + inc - sum;
 #pragma unroll
-  for (int k = 0; k < kOctItems; ++k) {
+  for (int k = 0; k < ITEMS; ++k) {
     const int X = X0 + k;
     if (X < n - 1) base[X] = pre;
     pre += cnt[k];
@@ -1313,9 +1315,11 @@ int tree_build(Ctx *c, int64_t n, const double *pos, const double *mass) {
     uint32_t *total = t.scalars;             // number of octree nodes below the cloud roots
     uint32_t *oct_state = oct_scan_state(c, n);
     const int otiles = (int)((ni + kOctTile - 1) / kOctTile);
-    k_oct_count<<<otiles, kOctThreads, 0, s>>>((int)n, leaf_max, kv.cbits, t.bchild, t.bparent,
-                                            t.bfirst, t.blast, t.bplen, t.bnchild, base, total,
-                                            oct_state + 1, oct_state, otiles, c->d_status);
+    const bool few = otiles <= 32;
+    auto oct_count = few ? k_oct_count<1> : k_oct_count<4>;
+    oct_count<<<otiles, few ? kOctTile : kOctTile / 4, 0, s>>>(
+        (int)n, leaf_max, kv.cbits, t.bchild, t.bparent, t.bfirst, t.blast, t.bplen, t.bnchild,
+        base, total, oct_state + 1, oct_state, otiles, c->d_status);
     ++c->launches;
     OctWriteArgs W{(int)n, leaf_max, kv.cbits, sg.nseg, cap_nodes, t.bchild, t.bfirst, t.blast,
                    t.bplen, kv.seg, t.bnchild, base, total, t.topo, t.ndepth, t.nnodes,
