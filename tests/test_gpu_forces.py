@@ -138,6 +138,22 @@ def test_direct_vs_oracle(gpu, n, eps, G):
     _check(acc.cpu().numpy(), ref, absum, f"direct/sphere{n}/eps{eps}", rel_tol=DIRECT_REL_TOL)
 
 
+@pytest.mark.parametrize("leaf_max,order", [(1, 0), (16, 2)])
+def test_tiny_clouds_vs_oracle(gpu, leaf_max, order):
+    # 1 .. 64 bodies: one-block build, tasks split eight ways, a walk of a few nodes; counts
+    # exact and every body within the parity rule
+    for n in (1, 2, 3, 5, 8, 17, 33, 64):
+        pos, _, m = inputs.uniform_sphere(n, seed=60 + n)
+        a, cnt = _gpu_forces(gpu, pos, m, 0.5, 1e-3, counted=True, leaf_max=leaf_max, order=order)
+        ref, absum, ocnt = oracle.Tree(pos, m, leaf_max=leaf_max, order=order).forces(0.5, 1e-3)
+        assert np.array_equal(cnt[:, 0], ocnt[:, 1]) and np.array_equal(cnt[:, 1], ocnt[:, 2]), n
+        assert np.array_equal(cnt[:, 2], ocnt[:, 0]), n
+        if n > 1:
+            _check(a, ref, absum, f"tiny/n{n}/leaf{leaf_max}/order{order}")
+        else:
+            assert np.array_equal(a, np.zeros((1, 3)))
+
+
 def test_two_body_closed_form(gpu):
     pos = np.array([[0.0, 0.0, 0.0], [3.0, 4.0, 0.0]])
     m = np.array([1.0, 3.0])

@@ -117,11 +117,12 @@ def test_single_and_coincident(gpu):
     assert root[3] == 1.0
 
 
-def test_nonfinite_is_reported(gpu):
-    pos, _, m = inputs.uniform_sphere(3000, seed=5)
+@pytest.mark.parametrize("n", [3000, 500])             # several tiles; one block (n <= 2048)
+def test_nonfinite_is_reported(gpu, n):
+    pos, _, m = inputs.uniform_sphere(n, seed=5)
     for bad in (np.nan, np.inf, -np.inf):
         p = pos.copy()
-        p[1234, 1] = bad
+        p[n // 3, 1] = bad
         ctx = gpu.Context(0)
         gpu.gravity_tree_build(ctx, torch.tensor(p, device="cuda"), torch.tensor(m, device="cuda"))
         with pytest.raises(gpu.GravityError) as e:
