@@ -239,6 +239,39 @@ k_rs_count(const uint64_t *__restrict__ keys, int64_t n, int key_passes, int clo
     if (cnt[p][threadIdx.x]) atomicAdd(&ghist[256 * p + threadIdx.x], cnt[p][threadIdx.x]);
 }
 
+// Morton keys (as k_keys) and the digit counts of every sort pass (as k_rs_count) in one
+// read of the positions: keys[i], idx[i] = i and the first pass's other value buffer
+// vinit[i] = i are written, and the counts are added to ghist.
+__global__ void __launch_bounds__(kRsThreads)
+k_keys_count(const double *__restrict__ pos, int64_t n, const double *__restrict__ geom0,
+             const int32_t *__restrict__ seg_of, uint64_t *__restrict__ keys,
+             uint32_t *__restrict__ idx, uint32_t *__restrict__ vinit, int cloud_passes,
+             uint32_t *__restrict__ ghist) {
+  __shared__ uint32_t cnt[kRsMaxPasses][256];
+  const int np = 8 + cloud_passes;
+  for (int p = 0; p < np; ++p) cnt[p][threadIdx.x] = 0;
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)kRsThreads + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kRsThreads) {
+    const int sg = seg_of ? seg_of[i] : 0;
+    const double *geom = geom0 + 8 * (int64_t)sg;           // the body's cloud
+    const double scale = geom[4];
+    const uint32_t qx = grid_coord(pos[3 * i + 0], geom[0], scale);
+    const uint32_t qy = grid_coord(pos[3 * i + 1], geom[1], scale);
+    const uint32_t qz = grid_coord(pos[3 * i + 2], geom[2], scale);
+    const uint64_t k = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+    keys[i] = k;
+    idx[i] = (uint32_t)i;
+    vinit[i] = (uint32_t)i;
+    for (int p = 0; p < 8; ++p) atomicAdd(&cnt[p][(unsigned)(k >> (8 * p)) & 255u], 1u);
+    for (int p = 0; p < cloud_passes; ++p)
+      atomicAdd(&cnt[8 + p][((unsigned)sg >> (8 * p)) & 255u], 1u);
+  }
+  __syncthreads();
+  for (int p = 0; p < np; ++p)
+    if (cnt[p][threadIdx.x]) atomicAdd(&ghist[256 * p + threadIdx.x], cnt[p][threadIdx.x]);
+}
+
 // Exclusive scan of one value per thread over a 256-thread block.
 __device__ __forceinline__ uint32_t block_excl_scan256(uint32_t v, uint32_t *s_tmp) {
   const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -537,9 +570,22 @@ k_order_small(const double *__restrict__ pos, int n, double *__restrict__ geom,
 // ids, so the order is by cloud, then key, then caller index.  Sorts (keys, idx) in
 // place; keys_alt / idx_alt are the other halves of the ping-pong, hist the counts
 // and tile states (257 * kRsMaxPasses + passes * tiles * 256 words).
+// With counted, the caller has cleared hist (radix_sort_clear) and launched k_keys_count,
+// which gives the keys, the identity value buffers and the digit counts.
+int radix_sort_clear(Ctx *c, int64_t n, uint32_t *hist, int cloud_passes,
+                     int64_t extra_zero_words) {
+  const int ntiles = (int)((n + kRsTile - 1) / kRsTile);
+  const int np = 8 + cloud_passes;
+  GRAV_CUDA_TRY(cudaMemsetAsync(hist, 0,
+                                sizeof(uint32_t) * ((size_t)(256 + 1) * kRsMaxPasses +
+                                                    (size_t)np * ntiles * 256 +
+                                                    (size_t)extra_zero_words), c->stream));
+  return GRAVITY_OK;
+}
+
 int radix_sort_buffers(Ctx *c, int64_t n, uint64_t *keys, uint64_t *keys_alt, uint32_t *idx,
                        uint32_t *idx_alt, uint32_t *hist, int cloud_passes,
-                       const int32_t *seg_of, int64_t extra_zero_words) {
+                       const int32_t *seg_of, int64_t extra_zero_words, bool counted = false) {
   const int ntiles = (int)((n + kRsTile - 1) / kRsTile);
   uint64_t *ka = keys, *kb = keys_alt;
   uint32_t *va = idx, *vb = idx_alt;
@@ -548,19 +594,21 @@ int radix_sort_buffers(Ctx *c, int64_t n, uint64_t *keys, uint64_t *keys_alt, ui
   // then [kRsMaxPasses][ntiles][256] published tile counts
   uint32_t *ghist = hist, *counters = hist + 256 * kRsMaxPasses;
   uint32_t *status = counters + kRsMaxPasses;
-  GRAV_CUDA_TRY(cudaMemsetAsync(hist, 0,
-                                sizeof(uint32_t) * ((size_t)(256 + 1) * kRsMaxPasses +
-                                                    (size_t)np * ntiles * 256 +
-                                                    (size_t)extra_zero_words), c->stream));
+  if (!counted) {
+    const int rc = radix_sort_clear(c, n, hist, cloud_passes, extra_zero_words);
+    if (rc) return rc;
+  }
   if (n <= kRsTile && c->sort_stall == 0) {   // one tile: every pass in one block
     k_rs_small<<<1, kRsThreads, 0, c->stream>>>(keys, idx, (int)n, cloud_passes, seg_of);
     ++c->launches;
     return cuda_status(cudaGetLastError());
   }
-  int cb = (int)((n + kRsThreads - 1) / kRsThreads);
-  if (cb > 2 * c->num_sms) cb = 2 * c->num_sms;
-  k_rs_count<<<cb, kRsThreads, 0, c->stream>>>(keys, n, 8, cloud_passes, seg_of, ghist, vb);
-  ++c->launches;
+  if (!counted) {
+    int cb = (int)((n + kRsThreads - 1) / kRsThreads);
+    if (cb > 2 * c->num_sms) cb = 2 * c->num_sms;
+    k_rs_count<<<cb, kRsThreads, 0, c->stream>>>(keys, n, 8, cloud_passes, seg_of, ghist, vb);
+    ++c->launches;
+  }
   for (int pass = 0; pass < np; ++pass) {
     const bool cl = pass >= 8;
     const int shift = cl ? 8 * (pass - 8) : 8 * pass;
@@ -590,11 +638,11 @@ uint32_t *oct_scan_state(Ctx *c, int64_t n) {
   return c->t.hist + (int64_t)(256 + 1) * kRsMaxPasses + (int64_t)np * ntiles * 256;
 }
 
-int radix_sort(Ctx *c, int64_t n) {
+int radix_sort(Ctx *c, int64_t n, bool counted) {
   Tree &t = c->t;
   const int cloud_passes = c->seg.nseg > 1 ? (c->seg.cbits + 7) / 8 : 0;
   return radix_sort_buffers(c, n, t.keys, t.keys_alt, t.idx, t.idx_alt, t.hist, cloud_passes,
-                            c->seg.seg_of, oct_scan_words(n));
+                            c->seg.seg_of, oct_scan_words(n), counted);
 }
 
 // Launch of k_bbox over one cloud of n bodies (grid a multiple of 3, see k_bbox).
@@ -1284,12 +1332,16 @@ int tree_build(Ctx *c, int64_t n, const double *pos, const double *mass) {
       k_bbox_seg<<<sg.nseg, kBBoxThreads, 0, s>>>(pos, sg.off, t.geom, c->d_status);
       ++c->launches;
     }
-    // a2: keys
-    k_keys<<<blocks_for(n, 256), 256, 0, s>>>(pos, n, t.geom, multi ? sg.seg_of : nullptr,
-                                               t.keys, t.idx);
+    // a2: keys, with the digit counts of every sort pass (one read of the positions)
+    const int cloud_passes = multi ? (sg.cbits + 7) / 8 : 0;
+    if ((rc = radix_sort_clear(c, n, t.hist, cloud_passes, oct_scan_words(n)))) return rc;
+    int cb = (int)((n + kRsThreads - 1) / kRsThreads);
+    if (cb > 2 * c->num_sms) cb = 2 * c->num_sms;
+    k_keys_count<<<cb, kRsThreads, 0, s>>>(pos, n, t.geom, multi ? sg.seg_of : nullptr, t.keys,
+                                           t.idx, t.idx_alt, cloud_passes, t.hist);
     ++c->launches;
     // a3: sort (by cloud, then key, then caller index)
-    rc = radix_sort(c, n);
+    rc = radix_sort(c, n, true);
     if (rc) return rc;
   }
   // a4: gather sorted bodies
