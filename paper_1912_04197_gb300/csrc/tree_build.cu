@@ -904,12 +904,21 @@ struct OctWriteArgs {
   const int32_t *child, *first, *last, *plen, *seg_sorted;
   const uint32_t *nchild, *base, *total;
   int4 *topo;
-  int32_t *depth, *nnodes;
+  int32_t *depth, *nnodes, *nparent;
   unsigned *status;
 };
 
+// Parent of the octree children of binary node c (an internal octree cell written at
+// octree id `id`): its children take ids nseg + base[c] .. + nchild[c] - 1.
+__device__ __forceinline__ void write_parent_of_children(const OctWriteArgs &A, int c, int id) {
+  const int n0 = A.nseg + (int)A.base[c], cnt = (int)A.nchild[c];
+  if (n0 < A.nseg || n0 + cnt > A.cap_nodes) { latch_error(A.status, kErrTree); return; }
+  for (int j = 0; j < cnt; ++j) A.nparent[n0 + j] = id;
+}
+
 // Record of a cloud root (binary internal node c, or body ~c) at octree id `id`.
 __device__ __forceinline__ void write_root(const OctWriteArgs &A, int c, int id) {
+  A.nparent[id] = -1;
   if (c < 0) {
     const int b = ~c;
     A.topo[id] = make_int4(-1, 0, b, b + 1);
@@ -920,6 +929,7 @@ __device__ __forceinline__ void write_root(const OctWriteArgs &A, int c, int id)
   if (A.nchild[c] > 0) {
     A.topo[id] = make_int4(A.nseg + (int)A.base[c], (int)A.nchild[c], b, e);
     A.depth[id] = cdepth(A.plen[c], A.cbits);
+    write_parent_of_children(A, c, id);
   } else {
     A.topo[id] = make_int4(-1, 0, b, e);
     A.depth[id] = (e - b <= A.leaf_max) ? 0 : kLevels;
@@ -962,25 +972,13 @@ __global__ void k_oct_write(OctWriteArgs A) {
       if (A.nchild[c] > 0) {
         A.topo[id] = make_int4(A.nseg + (int)A.base[c], (int)A.nchild[c], b, e);
         A.depth[id] = cdepth(A.plen[c], A.cbits);
+        write_parent_of_children(A, c, id);
       } else {
         A.topo[id] = make_int4(-1, 0, b, e);
         A.depth[id] = (e - b <= A.leaf_max) ? d + 1 : kLevels;
       }
     }
   }
-}
-
-__global__ void k_oct_parent(int cap_nodes, int nseg, const int4 *__restrict__ topo,
-                             const int32_t *__restrict__ nnodes, int32_t *__restrict__ nparent,
-                             unsigned *status) {
-  int id = blockIdx.x * blockDim.x + threadIdx.x;
-  int nn = *nnodes;
-  if (id >= nn || id >= cap_nodes) return;
-  if (id < nseg) nparent[id] = -1;                        // cloud roots
-  int4 t = topo[id];
-  if (t.x < 0) return;
-  if (t.x < nseg || t.x + t.y > nn) { latch_error(status, kErrTree); return; }
-  for (int k = 0; k < t.y; ++k) nparent[t.x + k] = id;
 }
 
 // ------------------------------------------------------------------ a7: moments
@@ -1373,13 +1371,12 @@ int tree_build(Ctx *c, int64_t n, const double *pos, const double *mass) {
         (int)n, leaf_max, kv.cbits, t.bchild, t.bparent, t.bfirst, t.blast, t.bplen, t.bnchild,
         base, total, oct_state + 1, oct_state, otiles, c->d_status);
     ++c->launches;
+    // (with the parent of every node: a cell writes its children's records and the parent
+    // of their children)
     OctWriteArgs W{(int)n, leaf_max, kv.cbits, sg.nseg, cap_nodes, t.bchild, t.bfirst, t.blast,
                    t.bplen, kv.seg, t.bnchild, base, total, t.topo, t.ndepth, t.nnodes,
-                   c->d_status};
+                   t.nparent, c->d_status};
     k_oct_write<<<blocks_for(ni, 256), 256, 0, s>>>(W);
-    ++c->launches;
-    k_oct_parent<<<blocks_for(cap_nodes, 256), 256, 0, s>>>(cap_nodes, sg.nseg, t.topo, t.nnodes,
-                                                            t.nparent, c->d_status);
     ++c->launches;
   }
   // a7: moments (bucketed by depth, full warps)
