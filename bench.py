@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--experiment", choices=["accuracy", "sweep"], default=None,
+    ap.add_argument("--experiment", choices=["accuracy", "sweep", "vjp"], default=None,
                     help="run one of the paper's Sec. 3.2 experiments instead of the benchmark")
     ap.add_argument("--n", type=int, default=1_048_576)
     ap.add_argument("--theta", type=float, default=0.5)
@@ -1029,6 +1029,34 @@ def experiment_sweep(args):
     return 0
 
 
+def experiment_vjp(args):
+    """The vector-Jacobian product alone on the headline aggregate's tree (monopole, leaf 16):
+    a few warm-up products, then --steps timed ones (CUDA events); the launch to profile."""
+    import torch
+    from paper_1912_04197_gb300 import gravity as g
+    dev = torch.device("cuda", 0)
+    pos, _, m = gen(args, 0)
+    P = torch.tensor(pos, device=dev)
+    M = torch.tensor(m, device=dev)
+    lam = torch.tensor(np.random.default_rng(args.seed + 7).standard_normal(pos.shape), device=dev)
+    out = torch.empty_like(P)
+    ctx = g.Context(dev)
+    g.gravity_tree_build(ctx, P, M, g.params(order=0, leaf_max=16))
+    for _ in range(max(1, args.warmup)):
+        g.gravity_forces_vjp(ctx, args.theta, args.eps, lam, out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        g.gravity_forces_vjp(ctx, args.theta, args.eps, lam, out)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    g.gravity_sync(ctx)
+    print(json.dumps({"experiment": "vjp", "n": len(pos), "theta": args.theta, "eps": args.eps,
+                      "ms_per_product": e0.elapsed_time(e1) / args.steps,
+                      "workload": "clumpy aggregate, monopole, leaf 16, one tree"}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -1038,6 +1066,8 @@ def main():
         return experiment_accuracy(args)
     if args.experiment == "sweep":
         return experiment_sweep(args)
+    if args.experiment == "vjp":
+        return experiment_vjp(args)
     if args.impl == "reference":
         return run_reference(args, rank, world)
     if world > 1:
