@@ -75,6 +75,12 @@ def parse():
                     help="skip the two-stream throughput of independent evaluations")
     ap.add_argument("--no-components", action="store_true",
                     help="skip the aggregate-identification leg")
+    ap.add_argument("--sweep-sizes", default="",
+                    help="--experiment sweep: comma-separated body counts (default 10 .. 1e7)")
+    ap.add_argument("--sweep-thetas", default="0.1,0.25,0.5,0.75",
+                    help="--experiment sweep: opening angles of the tree rows")
+    ap.add_argument("--sweep-steps", type=int, default=50,
+                    help="--experiment sweep: timed steps per row up to 1e6 bodies (10 above)")
     ap.add_argument("--no-sweep", action="store_true",
                     help="skip the theta / order / accumulator sweep (runs with the direct-sum leg)")
     ap.add_argument("--fp64-sample", type=int, default=65536,
@@ -986,6 +992,9 @@ def experiment_sweep(args):
     rows = []
     sizes = [10, 30, 100, 300, 1000, 3000, 10_000, 30_000, 100_000, 300_000, 1_000_000,
              3_000_000, 10_000_000]
+    if args.sweep_sizes:
+        sizes = [int(float(v)) for v in args.sweep_sizes.split(",")]
+    thetas = [float(v) for v in args.sweep_thetas.split(",")]
     with torch.cuda.stream(stream):
         ctx = g.Context(dev)
         for n in sizes:
@@ -993,8 +1002,8 @@ def experiment_sweep(args):
             P0 = torch.tensor(pos, device=dev)
             M = torch.tensor(m, device=dev)
             row = {"n": n}
-            steps = 50 if n <= 1_000_000 else 10
-            for theta in (0.1, 0.25, 0.5, 0.75):
+            steps = args.sweep_steps if n <= 1_000_000 else min(args.sweep_steps, 10)
+            for theta in thetas:
                 P, V = P0.clone(), torch.zeros_like(P0)
                 A = torch.empty_like(P)
                 p = g.params(order=0, leaf_max=1)

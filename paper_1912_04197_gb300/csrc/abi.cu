@@ -136,7 +136,7 @@ int ensure_capacity(Ctx *c, int64_t n) {
   GRAV_ALLOC(t.bbase, cap);
   GRAV_ALLOC(t.topo, nodes); GRAV_ALLOC(t.nparent, nodes); GRAV_ALLOC(t.ndepth, nodes);
   GRAV_ALLOC(t.nlist, nodes);
-  GRAV_ALLOC(t.nmass, nodes); GRAV_ALLOC(t.ncom, 3 * nodes); GRAV_ALLOC(t.nquad, 6 * nodes);
+  GRAV_ALLOC(t.nmass, nodes); GRAV_ALLOC(t.ncom, 3 * nodes); GRAV_ALLOC(t.nquad, 3 * nodes);
   GRAV_ALLOC(t.nrec0, nodes); GRAV_ALLOC(t.nrec1, nodes); GRAV_ALLOC(t.nquadf, 2 * nodes);
 #undef GRAV_ALLOC
   if (rc != GRAVITY_OK) {
@@ -1046,22 +1046,30 @@ int gravity_debug_export(gravity_ctx *h, int what, void *dst, size_t bytes) {
     case GRAVITY_DBG_PARENT: src = t.nparent; need = sizeof(int32_t) * nn; break;
     case GRAVITY_DBG_MASS: src = t.nmass; need = sizeof(double) * nn; break;
     case GRAVITY_DBG_COM: src = t.ncom; need = 3 * sizeof(double) * nn; break;
-    case GRAVITY_DBG_QUAD: src = t.nquad; need = 6 * sizeof(double) * nn; break;
+    case GRAVITY_DBG_QUAD: {
+      // stored as T = sum m y y^T in double-float pairs; exported as Q = 3T - tr(T) I, FP64
+      if (bytes < 6 * sizeof(double) * (size_t)nn) return GRAVITY_E_ARG;
+      if (nn == 0) return GRAVITY_OK;
+      std::vector<float> sec((size_t)12 * nn);
+      GRAV_CUDA_TRY(cudaMemcpy(sec.data(), t.nquad, sizeof(float) * sec.size(),
+                               cudaMemcpyDeviceToHost));
+      double *q = static_cast<double *>(dst);
+      for (int32_t k = 0; k < nn; ++k) {
+        double T[6];
+        for (int a = 0; a < 6; ++a)
+          T[a] = (double)sec[12 * (size_t)k + 2 * a] + (double)sec[12 * (size_t)k + 2 * a + 1];
+        const double tr = T[0] + T[1] + T[2];
+        for (int a = 0; a < 3; ++a) q[6 * (size_t)k + a] = 3.0 * T[a] - tr;
+        for (int a = 3; a < 6; ++a) q[6 * (size_t)k + a] = 3.0 * T[a];
+      }
+      return GRAVITY_OK;
+    }
     case GRAVITY_DBG_WALKSTATS: src = c.walk_stats; need = 16 * sizeof(unsigned long long); break;
     default: return GRAVITY_E_ARG;
   }
   if (bytes < need) return GRAVITY_E_ARG;
   if (need == 0) return GRAVITY_OK;
   GRAV_CUDA_TRY(cudaMemcpy(dst, src, need, cudaMemcpyDeviceToHost));
-  if (what == GRAVITY_DBG_QUAD) {             // stored as T = sum m y y^T; export Q = 3T - tr(T) I
-    double *q = static_cast<double *>(dst);
-    for (int32_t k = 0; k < nn; ++k) {
-      double *T = q + 6 * k;
-      const double tr = T[0] + T[1] + T[2];
-      for (int a = 0; a < 3; ++a) T[a] = 3.0 * T[a] - tr;
-      for (int a = 3; a < 6; ++a) T[a] = 3.0 * T[a];
-    }
-  }
   return GRAVITY_OK;
 }
 

@@ -55,7 +55,7 @@ struct Tree {
   int32_t *nnodes = nullptr;                    // device scalar
   double *nmass = nullptr;                      // FP64 moments
   double *ncom = nullptr;                       // (k,3)
-  double *nquad = nullptr;                      // (k,6) second moments T about the COM
+  float4 *nquad = nullptr;                      // (k,3) second moments T about the COM, (hi, lo) pairs
   float4 *nrec0 = nullptr;                      // (com_hi xyz, m)
   float4 *nrec1 = nullptr;                      // (com_lo xyz, l^2)
   float4 *nquadf = nullptr;                     // 2 per node, of -Q: (xx,yy,zz,xy), (xz,yz,0,0)

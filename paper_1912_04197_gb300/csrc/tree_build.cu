@@ -45,9 +45,11 @@ __device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsig
   return a > b ? a : b;
 }
 
-// Block-wide min (lo[3]) / max (hi[3]) of ordered keys; result valid in thread 0.
+// Block-wide min (lo[3]) / max (hi[3]) of ordered keys over NT threads; result valid in
+// thread 0.
+template <int NT = kBBoxThreads>
 __device__ __forceinline__ void block_minmax(unsigned long long lo[3], unsigned long long hi[3]) {
-  __shared__ unsigned long long s[kBBoxThreads / 32][6];
+  __shared__ unsigned long long s[NT / 32][6];
   for (int o = 16; o > 0; o >>= 1)
     for (int a = 0; a < 3; ++a) {
       lo[a] = umin64(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
@@ -58,7 +60,7 @@ __device__ __forceinline__ void block_minmax(unsigned long long lo[3], unsigned 
     for (int a = 0; a < 3; ++a) { s[w][a] = lo[a]; s[w][3 + a] = hi[a]; }
   __syncthreads();
   if (threadIdx.x == 0)
-    for (int ww = 1; ww < kBBoxThreads / 32; ++ww)
+    for (int ww = 1; ww < NT / 32; ++ww)
       for (int a = 0; a < 3; ++a) {
         lo[a] = umin64(lo[a], s[ww][a]);
         hi[a] = umax64(hi[a], s[ww][3 + a]);
@@ -498,25 +500,59 @@ k_rs_small(uint64_t *__restrict__ keys, uint32_t *__restrict__ idx, int n, int c
 // coordinates' order-preserving integer images, the side and scale by the same IEEE
 // operations, non-finite coordinates latched), Morton keys (as k_keys) and the sort, in one
 // block.  The sort is a bitonic network on (key, caller index): the pairs are distinct, so
-// their ascending order is exactly the stable order by key.
-__global__ void __launch_bounds__(kRsThreads)
+// their ascending order is exactly the stable order by key.  Thread t holds positions t
+// and t + 1024 in registers; a step whose partner lies in the same warp exchanges through
+// shuffles, one across warps through shared memory, and the step between the two halves
+// stays in the thread.
+constexpr int kOrdThreads = 1024;
+static_assert(2 * kOrdThreads == kRsTile, "two positions per thread cover one tile");
+
+__device__ __forceinline__ bool pair_gt(uint64_t ka, uint32_t va, uint64_t kb, uint32_t vb) {
+  return ka > kb || (ka == kb && va > vb);
+}
+
+// One compare-exchange of the network seen from position i (pair (k, v)), whose partner
+// i ^ j holds (pk, pv), in a merge of blocks of kk positions: the lower position of an
+// ascending pair keeps the smaller pair, of a descending one the larger.
+__device__ __forceinline__ void bitonic_keep(int i, int j, int kk, uint64_t &k, uint32_t &v,
+                                             uint64_t pk, uint32_t pv) {
+  const bool take_min = ((i & j) == 0) == ((i & kk) == 0);
+  if (take_min == pair_gt(k, v, pk, pv)) {
+    k = pk;
+    v = pv;
+  }
+}
+
+// Morton key of body i (as k_keys): geom = (lo xyz, side, 2^21 / side).
+__device__ __forceinline__ uint64_t morton_of(const double *__restrict__ pos, int i,
+                                              const double *geom) {
+  const uint32_t qx = grid_coord(pos[3 * i + 0], geom[0], geom[4]);
+  const uint32_t qy = grid_coord(pos[3 * i + 1], geom[1], geom[4]);
+  const uint32_t qz = grid_coord(pos[3 * i + 2], geom[2], geom[4]);
+  return (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+}
+
+__global__ void __launch_bounds__(kOrdThreads)
 k_order_small(const double *__restrict__ pos, int n, double *__restrict__ geom,
               uint64_t *__restrict__ keys, uint32_t *__restrict__ idx, unsigned *status) {
-  __shared__ RsSmall S;
+  __shared__ uint64_t s_key[kRsTile];
+  __shared__ uint32_t s_val[kRsTile];
   __shared__ double s_geom[5];
   unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
   bool bad = false;
   const unsigned long long *p64 = reinterpret_cast<const unsigned long long *>(pos);
-  for (int i = threadIdx.x; i < 3 * n; i += kRsThreads) {
-    const unsigned long long v = p64[i];
-    bad |= ((v >> 52) & 0x7FFull) == 0x7FFull;
-    const unsigned long long k = (v >> 63) ? ~v : (v | 0x8000000000000000ull);
-    const int a = i % 3;
-    lo[a] = umin64(lo[a], k);
-    hi[a] = umax64(hi[a], k);
+  for (int i = threadIdx.x; i < n; i += kOrdThreads) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const unsigned long long v = p64[3 * i + a];
+      bad |= ((v >> 52) & 0x7FFull) == 0x7FFull;
+      const unsigned long long k = (v >> 63) ? ~v : (v | 0x8000000000000000ull);
+      lo[a] = umin64(lo[a], k);
+      hi[a] = umax64(hi[a], k);
+    }
   }
   bad = __syncthreads_or(bad);
-  block_minmax(lo, hi);
+  block_minmax<kOrdThreads>(lo, hi);
   if (threadIdx.x == 0) {
     if (bad) latch_error(status, kErrNonFinite);
     double glo[3], ghi[3];
@@ -529,41 +565,47 @@ k_order_small(const double *__restrict__ pos, int n, double *__restrict__ geom,
     s_geom[4] = geom[4] = __ddiv_rn(2097152.0, side);   // 2^21 / side, one IEEE division
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < n; i += kRsThreads) {
-    const uint32_t qx = grid_coord(pos[3 * i + 0], s_geom[0], s_geom[4]);
-    const uint32_t qy = grid_coord(pos[3 * i + 1], s_geom[1], s_geom[4]);
-    const uint32_t qz = grid_coord(pos[3 * i + 2], s_geom[2], s_geom[4]);
-    S.key[i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
-    S.val[i] = (uint32_t)i;
-  }
+  const int t = threadIdx.x, tb = t + kOrdThreads;
+  uint64_t ka = ~0ull, kb = ~0ull;             // positions t and tb; pads sort last
+  uint32_t va = ~0u, vb = ~0u;
+  if (t < n) { ka = morton_of(pos, t, s_geom); va = (uint32_t)t; }
+  if (tb < n) { kb = morton_of(pos, tb, s_geom); vb = (uint32_t)tb; }
+  const bool upper = n > kOrdThreads;           // the upper half holds only pads otherwise
   int p2 = 1;
   while (p2 < n) p2 <<= 1;
-  for (int i = n + threadIdx.x; i < p2; i += kRsThreads) {   // pads sort last
-    S.key[i] = ~0ull;
-    S.val[i] = ~0u;
-  }
-  __syncthreads();
-  for (int k = 2; k <= p2; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < p2; i += kRsThreads) {
-        const int l = i ^ j;
-        if (l > i) {
-          const uint64_t ka = S.key[i], kb = S.key[l];
-          const uint32_t va = S.val[i], vb = S.val[l];
-          const bool gt = ka > kb || (ka == kb && va > vb);
-          if (gt == ((i & k) == 0)) {             // ascending where bit k of i is 0
-            S.key[i] = kb; S.key[l] = ka;
-            S.val[i] = vb; S.val[l] = va;
-          }
+  for (int kk = 2; kk <= p2; kk <<= 1) {
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      if (j == kOrdThreads) {                   // positions t and tb: ascending (kk = 2048)
+        if (pair_gt(ka, va, kb, vb)) {
+          const uint64_t tk = ka; ka = kb; kb = tk;
+          const uint32_t tv = va; va = vb; vb = tv;
+        }
+      } else if (j >= 32) {                     // partner in another warp
+        s_key[t] = ka; s_val[t] = va;
+        if (upper) { s_key[tb] = kb; s_val[tb] = vb; }
+        __syncthreads();
+        const uint64_t pka = s_key[t ^ j];
+        const uint32_t pva = s_val[t ^ j];
+        uint64_t pkb = 0ull;
+        uint32_t pvb = 0u;
+        if (upper) { pkb = s_key[tb ^ j]; pvb = s_val[tb ^ j]; }
+        __syncthreads();
+        bitonic_keep(t, j, kk, ka, va, pka, pva);
+        if (upper) bitonic_keep(tb, j, kk, kb, vb, pkb, pvb);
+      } else {                                  // partner in this warp
+        const uint64_t pka = __shfl_xor_sync(0xffffffffu, ka, j);
+        const uint32_t pva = __shfl_xor_sync(0xffffffffu, va, j);
+        bitonic_keep(t, j, kk, ka, va, pka, pva);
+        if (upper) {
+          const uint64_t pkb = __shfl_xor_sync(0xffffffffu, kb, j);
+          const uint32_t pvb = __shfl_xor_sync(0xffffffffu, vb, j);
+          bitonic_keep(tb, j, kk, kb, vb, pkb, pvb);
         }
       }
-      __syncthreads();
     }
   }
-  for (int i = threadIdx.x; i < n; i += kRsThreads) {
-    keys[i] = S.key[i];
-    idx[i] = S.val[i];
-  }
+  if (t < n) { keys[t] = ka; idx[t] = va; }
+  if (tb < n) { keys[tb] = kb; idx[tb] = vb; }
 }
 
 // 8 passes over the 63-bit keys, then (several clouds) stable passes over the cloud
@@ -988,8 +1030,12 @@ __global__ void k_oct_write(OctWriteArgs A) {
 // IEEE roundings (no contraction) so m and COM are reproducible bit for bit.
 // Quadrupole (order 2): the second moment T = sum m y y^T about the node's COM is
 // carried up with the parallel-axis rule T_p = sum_c (T_c + m_c d_c d_c^T),
-// d_c = COM_c - COM_p (FP64, fused multiply-adds); the walk uses the traceless
+// d_c = COM_c - COM_p (an FP64 difference); the walk uses the traceless
 // Q = 3 T - tr(T) I, identical in exact arithmetic to sum m (3 y y^T - |y|^2 I).
+// The products and sums of T run in double-float arithmetic (Dbl2 below, ~47
+// significant bits), not FP64: on GB300 an FP32 warp instruction issues in one cycle
+// of a sub-partition and an FP64 one holds its unit ~64 cycles, so this halves the
+// pass's FP64 instructions; T stays within ~1e-14 m l^2 of the FP64 value.
 //
 // GB300's FP64 pipe costs the same per warp instruction however many lanes are
 // active, so the pass runs on full, uniform warps: nodes are counting-sorted into
@@ -1015,7 +1061,8 @@ struct MomArgs {
   const int32_t *seg_sorted;   // cloud of each sorted body, or nullptr (one cloud)
   double *nmass;
   double *ncom;
-  double *nsec;                // second moments T (xx, yy, zz, xy, xz, yz)
+  float4 *nsec;                // second moments T, double-float (hi, lo) pairs, 3 per node:
+                               // (xx, yy), (zz, xy), (xz, yz)
   float4 *rec0;
   float4 *rec1;
   float4 *quadf;
@@ -1028,6 +1075,62 @@ struct MomArgs {
 __device__ __forceinline__ double dm(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double da(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double ds(double a, double b) { return __dsub_rn(a, b); }
+
+// A double-float value hi + lo (two FP32 numbers, |lo| <= ulp(hi) / 2 after every
+// operation).  The operations are the classical error-free transforms (Dekker's
+// product through a fused multiply-add, Knuth's two-sum) with explicit roundings, so
+// no contraction can break them.
+struct Dbl2 {
+  float hi, lo;
+};
+
+// x as hi + lo from its FP64 bit fields, on the integer units (no FP64 instruction):
+// hi = the leading 24 significant bits, lo = the next ones of the remaining 29,
+// truncated to 24; |x - hi - lo| < 2^-47 |x|.  A lo below FP32's normal range is
+// dropped; outside that range for hi (|x| < 2^-126 or >= 2^128), hi = x rounded to
+// FP32 and lo = 0.
+__device__ __forceinline__ Dbl2 dbl2_split(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)(u >> 52) & 0x7FF;
+  if (e < 897 || e > 1150) return {__double2float_rn(x), 0.f};
+  const uint32_t sign = (uint32_t)(u >> 32) & 0x80000000u;
+  const float hi =
+      __uint_as_float(sign | ((uint32_t)(e - 896) << 23) | ((uint32_t)(u >> 29) & 0x7FFFFFu));
+  const uint32_t low = (uint32_t)u & 0x1FFFFFFFu;       // weight of bit 0: 2^(e - 1075)
+  float lo = 0.f;
+  if (low) {
+    const int p = 31 - __clz(low);                     // leading bit of the low part
+    const uint32_t mant = p >= 23 ? low >> (p - 23) : low << (23 - p);
+    const int be = e - 948 + p;                        // FP32 biased exponent
+    if (be > 0) lo = __uint_as_float(sign | ((uint32_t)be << 23) | (mant & 0x7FFFFFu));
+  }
+  return {hi, lo};
+}
+
+__device__ __forceinline__ Dbl2 dbl2_mul(Dbl2 a, Dbl2 b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);                 // exact error of p
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const float s = __fadd_rn(p, e);
+  return {s, __fsub_rn(e, __fsub_rn(s, p))};
+}
+
+__device__ __forceinline__ Dbl2 dbl2_add(Dbl2 a, Dbl2 b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));   // exact error of s
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  const float h = __fadd_rn(s, e);
+  return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+
+// T (6 double-float entries) to and from its 3 float4 records.
+__device__ __forceinline__ void store_sec(float4 *dst, const Dbl2 *T) {
+  dst[0] = make_float4(T[0].hi, T[0].lo, T[1].hi, T[1].lo);
+  dst[1] = make_float4(T[2].hi, T[2].lo, T[3].hi, T[3].lo);
+  dst[2] = make_float4(T[4].hi, T[4].lo, T[5].hi, T[5].lo);
+}
 
 __device__ __forceinline__ int bucket_of(int4 t, int depth) {
   const int b = t.x < 0 ? min(t.w - t.z, kLeafBuckets) - 1 : kLeafBuckets + (kLevels - 1 - depth);
@@ -1077,11 +1180,25 @@ __global__ void k_bucket_fill(const int4 *__restrict__ topo, const int32_t *__re
   if (id < nn) nlist[off[b] + base[b] + local] = id;
 }
 
+// Quadrupole record: Q in double-float, then rounded to FP32 (the hi part of a
+// normalised pair), stored negated.
+__device__ void write_quad_record(const MomArgs &A, int id, const Dbl2 *T) {
+  const Dbl2 tr = dbl2_add(dbl2_add(T[0], T[1]), T[2]), ntr = {-tr.hi, -tr.lo};
+  const Dbl2 three = {3.f, 0.f};
+  float q[6];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) q[a] = dbl2_add(dbl2_mul(three, T[a]), ntr).hi;
+#pragma unroll
+  for (int a = 3; a < 6; ++a) q[a] = dbl2_mul(three, T[a]).hi;
+  A.quadf[2 * id] = make_float4(-q[0], -q[1], -q[2], -q[3]);
+  A.quadf[2 * id + 1] = make_float4(-q[4], -q[5], 0.f, 0.f);
+}
+
 // Walk records: (COM hi, m) and (COM lo, l^2); l^2 = -1 marks a one-body leaf
 // (always a body-to-body term).  Quadrupole record: -Q = -(3T - tr(T) I) as FP32 (the
 // walk's term is written with the negated tensor, which needs no negation there).
 __device__ void write_records(const MomArgs &A, int id, double m, const double *com,
-                              const double *T, bool single_body) {
+                              const Dbl2 *T, bool single_body) {
   float h[3], lo[3];
   for (int a = 0; a < 3; ++a) split_df(com[a], h[a], lo[a]);
   const int4 t = A.topo[id];
@@ -1090,15 +1207,7 @@ __device__ void write_records(const MomArgs &A, int id, double m, const double *
   float l2 = single_body ? -1.0f : __double2float_rn(dm(l, l));
   A.rec0[id] = make_float4(h[0], h[1], h[2], __double2float_rn(m));
   A.rec1[id] = make_float4(lo[0], lo[1], lo[2], l2);
-  if (A.order >= 2) {
-    double tr = T[0] + T[1] + T[2];
-    A.quadf[2 * id] = make_float4(-__double2float_rn(fma(3.0, T[0], -tr)),
-                                  -__double2float_rn(fma(3.0, T[1], -tr)),
-                                  -__double2float_rn(fma(3.0, T[2], -tr)),
-                                  -__double2float_rn(3.0 * T[3]));
-    A.quadf[2 * id + 1] = make_float4(-__double2float_rn(3.0 * T[4]),
-                                      -__double2float_rn(3.0 * T[5]), 0.f, 0.f);
-  }
+  if (A.order >= 2) write_quad_record(A, id, T);
 }
 
 // Moments of one leaf from its bodies, in body order (mass, then m x, COM = sum / mass,
@@ -1106,7 +1215,8 @@ __device__ void write_records(const MomArgs &A, int id, double m, const double *
 __device__ void leaf_node(const MomArgs &A, int id) {
   const int4 t = A.topo[id];
   if (t.z < 0 || t.w > A.n || t.z >= t.w) { latch_error(A.status, kErrTree); return; }
-  double msum, com[3], T[6] = {0, 0, 0, 0, 0, 0};
+  double msum, com[3];
+  Dbl2 T[6] = {};
   if (t.w - t.z == 1) {
     msum = A.mass_s[t.z];
     for (int a = 0; a < 3; ++a) com[a] = A.pos_s[3 * t.z + a];
@@ -1123,28 +1233,28 @@ __device__ void leaf_node(const MomArgs &A, int id) {
     com[0] = __ddiv_rn(sx, msum); com[1] = __ddiv_rn(sy, msum); com[2] = __ddiv_rn(sz, msum);
     if (A.order >= 2) {
       for (int i = t.z; i < t.w; ++i) {
-        const double mi = A.mass_s[i];
-        const double y0 = A.pos_s[3 * i] - com[0], y1 = A.pos_s[3 * i + 1] - com[1],
-                     y2 = A.pos_s[3 * i + 2] - com[2];
-        const double m0 = mi * y0, m1 = mi * y1, m2 = mi * y2;
-        T[0] = fma(m0, y0, T[0]); T[1] = fma(m1, y1, T[1]); T[2] = fma(m2, y2, T[2]);
-        T[3] = fma(m0, y1, T[3]); T[4] = fma(m0, y2, T[4]); T[5] = fma(m1, y2, T[5]);
+        const Dbl2 mi = dbl2_split(A.mass_s[i]);
+        const Dbl2 y0 = dbl2_split(ds(A.pos_s[3 * i], com[0])),
+                   y1 = dbl2_split(ds(A.pos_s[3 * i + 1], com[1])),
+                   y2 = dbl2_split(ds(A.pos_s[3 * i + 2], com[2]));
+        const Dbl2 m0 = dbl2_mul(mi, y0), m1 = dbl2_mul(mi, y1), m2 = dbl2_mul(mi, y2);
+        T[0] = dbl2_add(T[0], dbl2_mul(m0, y0)); T[1] = dbl2_add(T[1], dbl2_mul(m1, y1));
+        T[2] = dbl2_add(T[2], dbl2_mul(m2, y2)); T[3] = dbl2_add(T[3], dbl2_mul(m0, y1));
+        T[4] = dbl2_add(T[4], dbl2_mul(m0, y2)); T[5] = dbl2_add(T[5], dbl2_mul(m1, y2));
       }
     }
   }
   A.nmass[id] = msum;
   for (int a = 0; a < 3; ++a) A.ncom[3 * id + a] = com[a];
-  if (A.order >= 2)
-    for (int a = 0; a < 6; ++a) A.nsec[6 * id + a] = T[a];
+  if (A.order >= 2) store_sec(A.nsec + 3 * id, T);
   write_records(A, id, msum, com, T, t.w - t.z == 1);
 }
 
-// An internal node from its children, combined in octant order.  All children's values
-// are loaded up front (at most 8 children: independent loads in flight together), through
-// L2: they were written by other warps of the same launch, and an SM's L1 may hold an
-// older copy of their cache lines.
-__device__ void internal_node(const MomArgs &A, int id, int nn) {
-  const int4 tp = A.topo[id];
+// An internal node from its children, combined in octant order (tp = its topology
+// record).  All children's values are loaded up front (at most 8 children: independent
+// loads in flight together), through L2: they were written by other warps of the same
+// launch, and an SM's L1 may hold an older copy of their cache lines.
+__device__ void internal_node(const MomArgs &A, int id, int4 tp, int nn) {
   if (tp.x <= 0 || tp.y > 8 || tp.x + tp.y > nn) { latch_error(A.status, kErrTree); return; }
   double cm[8], cx[8], cy[8], cz[8];
 #pragma unroll
@@ -1166,35 +1276,117 @@ __device__ void internal_node(const MomArgs &A, int id, int nn) {
     }
   }
   const double pc[3] = {__ddiv_rn(px, pm), __ddiv_rn(py, pm), __ddiv_rn(pz, pm)};
-  double T[6] = {0, 0, 0, 0, 0, 0};
+  Dbl2 T[6] = {};
   if (A.order >= 2) {
 #pragma unroll
     for (int h = 0; h < 8; h += 4) {
-      double Tc[4][6];
+      float4 Tc[4][3];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int c = (h + j < tp.y) ? tp.x + h + j : tp.x;
 #pragma unroll
-        for (int a = 0; a < 6; ++a) Tc[j][a] = __ldcg(A.nsec + 6 * c + a);
+        for (int q = 0; q < 3; ++q) Tc[j][q] = __ldcg(A.nsec + 3 * c + q);
       }
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         if (h + j < tp.y) {
-          const double mc = cm[h + j];
-          const double d0 = cx[h + j] - pc[0], d1 = cy[h + j] - pc[1], d2 = cz[h + j] - pc[2];
-          const double m0 = mc * d0, m1 = mc * d1, m2 = mc * d2;
-          T[0] += fma(m0, d0, Tc[j][0]); T[1] += fma(m1, d1, Tc[j][1]);
-          T[2] += fma(m2, d2, Tc[j][2]); T[3] += fma(m0, d1, Tc[j][3]);
-          T[4] += fma(m0, d2, Tc[j][4]); T[5] += fma(m1, d2, Tc[j][5]);
+          const Dbl2 mc = dbl2_split(cm[h + j]);
+          const Dbl2 d0 = dbl2_split(ds(cx[h + j], pc[0])), d1 = dbl2_split(ds(cy[h + j], pc[1])),
+                     d2 = dbl2_split(ds(cz[h + j], pc[2]));
+          const Dbl2 m0 = dbl2_mul(mc, d0), m1 = dbl2_mul(mc, d1), m2 = dbl2_mul(mc, d2);
+          const Dbl2 t[6] = {dbl2_mul(m0, d0), dbl2_mul(m1, d1), dbl2_mul(m2, d2),
+                             dbl2_mul(m0, d1), dbl2_mul(m0, d2), dbl2_mul(m1, d2)};
+          const Dbl2 tc[6] = {{Tc[j][0].x, Tc[j][0].y}, {Tc[j][0].z, Tc[j][0].w},
+                              {Tc[j][1].x, Tc[j][1].y}, {Tc[j][1].z, Tc[j][1].w},
+                              {Tc[j][2].x, Tc[j][2].y}, {Tc[j][2].z, Tc[j][2].w}};
+#pragma unroll
+          for (int a = 0; a < 6; ++a) T[a] = dbl2_add(T[a], dbl2_add(tc[a], t[a]));
         }
       }
     }
   }
   A.nmass[id] = pm;
   for (int a = 0; a < 3; ++a) A.ncom[3 * id + a] = pc[a];
-  if (A.order >= 2)
-    for (int a = 0; a < 6; ++a) A.nsec[6 * id + a] = T[a];
+  if (A.order >= 2) store_sec(A.nsec + 3 * id, T);
   write_records(A, id, pm, pc, T, false);
+}
+
+// The same node computed by a group of 8 lanes (lane j of the group holds child j), for
+// depths with few nodes.  The products m_c x_c run once per child, in parallel; every lane
+// of the group then folds them in octant order with the same IEEE operations as
+// internal_node, so m and COM are bitwise the same; lanes 0-2 of the group divide one COM
+// component each and split it for the record; the second moments are summed over the
+// group by a butterfly (another rounding order than internal_node's, the same ~1e-14 m l^2
+// accuracy).  About half the FP64 instructions of a 32-node unit, for 4 nodes: the form
+// pays when a depth's groups fit one warp per SM sub-partition.  Every lane of the warp
+// calls this (full-warp shuffles); valid is false in lanes of a group with no node.
+__device__ void internal_node_group(const MomArgs &A, int id, int4 tp, bool valid, int nn) {
+  constexpr unsigned kAll = 0xffffffffu;
+  const int lane = threadIdx.x & 31, j = lane & 7, base = lane & ~7;
+  if (valid && (tp.x <= 0 || tp.y > 8 || tp.x + tp.y > nn)) {
+    if (j == 0) latch_error(A.status, kErrTree);
+    valid = false;
+  }
+  const bool has = valid && j < tp.y;
+  const int c = has ? tp.x + j : 0;
+  double cm = 0.0, cx = 0.0, cy = 0.0, cz = 0.0;
+  if (has) {
+    cm = __ldcg(A.nmass + c);
+    cx = __ldcg(A.ncom + 3 * c); cy = __ldcg(A.ncom + 3 * c + 1); cz = __ldcg(A.ncom + 3 * c + 2);
+  }
+  const double mx = dm(cx, cm), my = dm(cy, cm), mz = dm(cz, cm);
+  const int nc = valid ? tp.y : 0;
+  double pm = 0.0, px = 0.0, py = 0.0, pz = 0.0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const double qm = __shfl_sync(kAll, cm, base + q), qx = __shfl_sync(kAll, mx, base + q);
+    const double qy = __shfl_sync(kAll, my, base + q), qz = __shfl_sync(kAll, mz, base + q);
+    if (q < nc) {
+      pm = da(pm, qm);
+      px = da(px, qx); py = da(py, qy); pz = da(pz, qz);
+    }
+  }
+  const double num = j == 0 ? px : j == 1 ? py : pz;
+  const double quo = __ddiv_rn(num, valid ? pm : 1.0);
+  float h, l;
+  split_df(quo, h, l);                          // lanes 0-2: one COM component each
+  const double pc[3] = {__shfl_sync(kAll, quo, base), __shfl_sync(kAll, quo, base + 1),
+                        __shfl_sync(kAll, quo, base + 2)};
+  const float hx = __shfl_sync(kAll, h, base), hy = __shfl_sync(kAll, h, base + 1),
+              hz = __shfl_sync(kAll, h, base + 2);
+  const float lx = __shfl_sync(kAll, l, base), ly = __shfl_sync(kAll, l, base + 1),
+              lz = __shfl_sync(kAll, l, base + 2);
+  Dbl2 T[6] = {};
+  if (A.order >= 2) {
+    if (has) {
+      const float4 t0 = __ldcg(A.nsec + 3 * c), t1 = __ldcg(A.nsec + 3 * c + 1),
+                   t2 = __ldcg(A.nsec + 3 * c + 2);
+      const Dbl2 mc = dbl2_split(cm);
+      const Dbl2 d0 = dbl2_split(ds(cx, pc[0])), d1 = dbl2_split(ds(cy, pc[1])),
+                 d2 = dbl2_split(ds(cz, pc[2]));
+      const Dbl2 m0 = dbl2_mul(mc, d0), m1 = dbl2_mul(mc, d1), m2 = dbl2_mul(mc, d2);
+      T[0] = dbl2_add({t0.x, t0.y}, dbl2_mul(m0, d0));
+      T[1] = dbl2_add({t0.z, t0.w}, dbl2_mul(m1, d1));
+      T[2] = dbl2_add({t1.x, t1.y}, dbl2_mul(m2, d2));
+      T[3] = dbl2_add({t1.z, t1.w}, dbl2_mul(m0, d1));
+      T[4] = dbl2_add({t2.x, t2.y}, dbl2_mul(m0, d2));
+      T[5] = dbl2_add({t2.z, t2.w}, dbl2_mul(m1, d2));
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1)
+#pragma unroll
+      for (int a = 0; a < 6; ++a)
+        T[a] = dbl2_add(T[a], {__shfl_xor_sync(kAll, T[a].hi, o), __shfl_xor_sync(kAll, T[a].lo, o)});
+  }
+  if (!valid || j != 0) return;
+  A.nmass[id] = pm;
+  for (int a = 0; a < 3; ++a) A.ncom[3 * id + a] = pc[a];
+  if (A.order >= 2) store_sec(A.nsec + 3 * id, T);
+  const double side = A.geom[8 * (A.seg_sorted ? A.seg_sorted[tp.z] : 0) + 3];
+  const double ln = dm(side, pow2_neg(A.ndepth[id]));
+  A.rec0[id] = make_float4(hx, hy, hz, __double2float_rn(pm));
+  A.rec1[id] = make_float4(lx, ly, lz, __double2float_rn(dm(ln, ln)));
+  if (A.order >= 2) write_quad_record(A, id, T);
 }
 
 // Leaves, one per thread (leaves of equal body counts share a warp).
@@ -1207,7 +1399,9 @@ __global__ void __launch_bounds__(128) k_leaf_moments(MomArgs A) {
 
 // Every internal node in one launch, after the leaves.  A work unit is up to 32 nodes of
 // one depth, one per lane (full, uniform warps: the FP64 pipe's cost per instruction does
-// not depend on the active lanes).  Warps take units from an atomic ticket, deepest depth
+// not depend on the active lanes); a depth whose nodes fit the grid's warps 4 to a warp
+// runs 4 nodes per unit instead, 8 lanes per node (internal_node_group), so its time is
+// the shorter FP64 chain of that form.  Warps take units from an atomic ticket, deepest depth
 // first.  A unit waits until the nearest deeper non-empty depth is complete; that depth's
 // units waited likewise before they started, so every node below, and in particular every
 // child, is done.  A unit waits only on units with smaller tickets, which running warps
@@ -1229,14 +1423,17 @@ k_level_moments(MomArgs A, uint32_t *__restrict__ ticket, uint32_t *__restrict__
   __shared__ uint32_t s_uoff[kLevels + 1];     // first unit of each depth bucket; total units
   __shared__ int s_widx[kLevels];              // depth bucket a bucket's units wait on (-1: none)
   __shared__ uint32_t s_wneed[kLevels];        // and its node count
+  __shared__ uint32_t s_per[kLevels];          // nodes per unit: 32, or 4 (8 lanes per node)
   if (threadIdx.x == 0) {
     uint32_t u = 0;
     int prev = -1;                             // latest non-empty depth bucket
+    const uint32_t warps = gridDim.x * (kMomThreads / 32);
     for (int i = 0; i < kLevels; ++i) {
       const int b = kLeafBuckets + i;
       const uint32_t sz = A.boff[b + 1] - A.boff[b];
       s_uoff[i] = u;
-      u += (sz + 31u) / 32u;
+      s_per[i] = (sz + 3u) / 4u <= warps ? 4u : 32u;
+      u += (sz + s_per[i] - 1u) / s_per[i];
       s_widx[i] = prev;
       s_wneed[i] = prev < 0 ? 0u : A.boff[kLeafBuckets + prev + 1] - A.boff[kLeafBuckets + prev];
       if (sz) prev = i;
@@ -1256,8 +1453,18 @@ k_level_moments(MomArgs A, uint32_t *__restrict__ ticket, uint32_t *__restrict__
     // depth bucket of unit u = the number of bucket starts 1 .. kLevels-1 at or before it
     const int i = __popc(__ballot_sync(0xffffffffu, 1 + lane < kLevels && s_uoff[1 + lane] <= u));
     const int b = kLeafBuckets + i;
-    const uint32_t k0 = A.boff[b] + (u - s_uoff[i]) * 32u;
-    const uint32_t k1 = min(k0 + 32u, A.boff[b + 1]);
+    const uint32_t per = s_per[i];
+    const uint32_t k0 = A.boff[b] + (u - s_uoff[i]) * per;
+    const uint32_t k1 = min(k0 + per, A.boff[b + 1]);
+    const uint32_t k = k0 + (uint32_t)(per == 4u ? lane >> 3 : lane);
+    // the unit's node ids and topology come from earlier launches: load them before the
+    // wait, so that only the children's moments are loaded after it
+    int id = 0;
+    int4 tp = make_int4(0, 0, 0, 0);
+    if (k < k1) {
+      id = __ldg(A.nlist + k);
+      tp = __ldg(A.topo + id);
+    }
     if (s_widx[i] >= 0) {
       // every lane polls (one coalesced load): a wait taken by lane 0 alone left the
       // warp running as two halves afterwards, doubling the FP64 time of the unit
@@ -1274,8 +1481,10 @@ k_level_moments(MomArgs A, uint32_t *__restrict__ ticket, uint32_t *__restrict__
       }
       __threadfence();
     }
-    const uint32_t k = k0 + (uint32_t)lane;
-    if (k < k1) internal_node(A, A.nlist[k], nn);
+    if (per == 4u)
+      internal_node_group(A, id, tp, k < k1, nn);
+    else if (k < k1)
+      internal_node(A, id, tp, nn);
     __threadfence();                            // this unit's moments before its count
     __syncwarp();
     if (lane == 0 && !(spin_budget < 0 && s_widx[i] < 0)) atomicAdd(done + i, k1 - k0);
@@ -1319,7 +1528,7 @@ int tree_build(Ctx *c, int64_t n, const double *pos, const double *mass) {
     // a1-a3 for one cloud that fits one sort tile: root cube, keys and sort in one block
     // (the octree scan's tile states, kept after the sort's words, are cleared here)
     GRAV_CUDA_TRY(cudaMemsetAsync(oct_scan_state(c, n), 0, sizeof(uint32_t) * oct_scan_words(n), s));
-    k_order_small<<<1, kRsThreads, 0, s>>>(pos, (int)n, t.geom, t.keys, t.idx, c->d_status);
+    k_order_small<<<1, kOrdThreads, 0, s>>>(pos, (int)n, t.geom, t.keys, t.idx, c->d_status);
     ++c->launches;
   } else {
     // a1: root cube of each cloud (also validates the coordinates)
