@@ -699,12 +699,31 @@ void launch_bbox(Ctx *c, const double *pos, int64_t n, unsigned long long *part,
   ++c->launches;
 }
 
+// ------------------------------------------------------------------ moment buckets
+// The moment pass takes nodes bucketed so that every warp's lanes run equal loops:
+// leaves by body count (1 .. 16 and more), then internal nodes by depth, deepest first.
+// The octree write counts the buckets; t.scalars holds, from kSlotCnt, the bucket
+// counts, fill cursors, the moment pass's done counters and its ticket (cleared by the
+// gather of each build), then the bucket offsets.  Word 0 is the octree total.
+constexpr int kLeafBuckets = 17;
+constexpr int kBuckets = kLeafBuckets + kLevels;   // + internal depths 20 .. 0
+constexpr int kSlotCnt = 1, kSlotFill = 40, kSlotDone = 80, kSlotTicket = 120, kSlotOff = 128;
+static_assert(kSlotCnt + kBuckets <= kSlotFill && kSlotFill + kBuckets <= kSlotDone &&
+              kSlotOff - kSlotCnt <= 256, "scalar slots");
+
+__device__ __forceinline__ int bucket_of(int4 t, int depth) {
+  const int b = t.x < 0 ? min(t.w - t.z, kLeafBuckets) - 1 : kLeafBuckets + (kLevels - 1 - depth);
+  return min(max(b, 0), kBuckets - 1);
+}
+
 // ------------------------------------------------------------------ a4: gather
+// (block 0 also clears the moment pass's counters, slots [kSlotCnt, kSlotOff))
 __global__ void k_gather(const double *__restrict__ pos, const double *__restrict__ mass,
                          const uint32_t *__restrict__ perm, int64_t n, double *__restrict__ pos_s,
                          double *__restrict__ mass_s, float4 *__restrict__ bhi,
                          float4 *__restrict__ blo, const int32_t *__restrict__ seg_of,
-                         int32_t *__restrict__ seg_sorted) {
+                         int32_t *__restrict__ seg_sorted, uint32_t *__restrict__ slots) {
+  if (blockIdx.x == 0 && threadIdx.x < kSlotOff - kSlotCnt) slots[kSlotCnt + threadIdx.x] = 0;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   int64_t j = perm[i];
@@ -947,6 +966,7 @@ struct OctWriteArgs {
   const uint32_t *nchild, *base, *total;
   int4 *topo;
   int32_t *depth, *nnodes, *nparent;
+  uint32_t *slots;             // moment bucket counts at kSlotCnt (cleared by the gather)
   unsigned *status;
 };
 
@@ -958,41 +978,40 @@ __device__ __forceinline__ void write_parent_of_children(const OctWriteArgs &A, 
   for (int j = 0; j < cnt; ++j) A.nparent[n0 + j] = id;
 }
 
+// Node record (topology, depth) at octree id `id`, counted in its moment bucket (cnt: the
+// block's counters in shared memory).
+__device__ __forceinline__ void put_node(const OctWriteArgs &A, int id, int4 t, int depth,
+                                         uint32_t *cnt) {
+  A.topo[id] = t;
+  A.depth[id] = depth;
+  atomicAdd(&cnt[bucket_of(t, depth)], 1u);
+}
+
 // Record of a cloud root (binary internal node c, or body ~c) at octree id `id`.
-__device__ __forceinline__ void write_root(const OctWriteArgs &A, int c, int id) {
+__device__ __forceinline__ void write_root(const OctWriteArgs &A, int c, int id, uint32_t *cnt) {
   A.nparent[id] = -1;
   if (c < 0) {
     const int b = ~c;
-    A.topo[id] = make_int4(-1, 0, b, b + 1);
-    A.depth[id] = 0;
+    put_node(A, id, make_int4(-1, 0, b, b + 1), 0, cnt);
     return;
   }
   const int b = A.first[c], e = A.last[c] + 1;
   if (A.nchild[c] > 0) {
-    A.topo[id] = make_int4(A.nseg + (int)A.base[c], (int)A.nchild[c], b, e);
-    A.depth[id] = cdepth(A.plen[c], A.cbits);
+    put_node(A, id, make_int4(A.nseg + (int)A.base[c], (int)A.nchild[c], b, e),
+             cdepth(A.plen[c], A.cbits), cnt);
     write_parent_of_children(A, c, id);
   } else {
-    A.topo[id] = make_int4(-1, 0, b, e);
-    A.depth[id] = (e - b <= A.leaf_max) ? 0 : kLevels;
+    put_node(A, id, make_int4(-1, 0, b, e), (e - b <= A.leaf_max) ? 0 : kLevels, cnt);
   }
 }
 
-__global__ void k_oct_write(OctWriteArgs A) {
-  const int X = blockIdx.x * blockDim.x + threadIdx.x;
-  if (X == 0) {
-    int nn = A.nseg + (int)*A.total;
-    if (nn > A.cap_nodes) { latch_error(A.status, kErrTree); nn = A.nseg; }
-    *A.nnodes = nn;
-    if (A.cbits == 0) write_root(A, 0, 0);                // one cloud: binary node 0 is the root
-  }
-  if (X >= A.n - 1) return;
+__device__ void oct_write_node(const OctWriteArgs &A, int X, uint32_t *cnt) {
   if (A.plen[X] < A.cbits) {                              // connector: place the cloud roots below
     for (int h = 0; h < 2; ++h) {
       const int c = A.child[2 * X + h];
       if (c < 0 || A.plen[c] >= A.cbits) {
         const int b = c < 0 ? ~c : A.first[c];
-        write_root(A, c, A.seg_sorted[b]);
+        write_root(A, c, A.seg_sorted[b], cnt);
       }
     }
     return;
@@ -1007,20 +1026,38 @@ __global__ void k_oct_write(OctWriteArgs A) {
     const int c = f.item[k], id = id0 + k;
     if (c < 0) {
       const int b = ~c;
-      A.topo[id] = make_int4(-1, 0, b, b + 1);
-      A.depth[id] = d + 1;
+      put_node(A, id, make_int4(-1, 0, b, b + 1), d + 1, cnt);
     } else {
       const int b = A.first[c], e = A.last[c] + 1;
       if (A.nchild[c] > 0) {
-        A.topo[id] = make_int4(A.nseg + (int)A.base[c], (int)A.nchild[c], b, e);
-        A.depth[id] = cdepth(A.plen[c], A.cbits);
+        put_node(A, id, make_int4(A.nseg + (int)A.base[c], (int)A.nchild[c], b, e),
+                 cdepth(A.plen[c], A.cbits), cnt);
         write_parent_of_children(A, c, id);
       } else {
-        A.topo[id] = make_int4(-1, 0, b, e);
-        A.depth[id] = (e - b <= A.leaf_max) ? d + 1 : kLevels;
+        put_node(A, id, make_int4(-1, 0, b, e), (e - b <= A.leaf_max) ? d + 1 : kLevels, cnt);
       }
     }
   }
+}
+
+// Writes the octree records: each binary node that starts an octree cell writes the
+// records of that cell's children (and the parent of their children), counting every
+// node in its moment bucket (per block in shared memory, then added to the global counts).
+__global__ void __launch_bounds__(256) k_oct_write(OctWriteArgs A) {
+  __shared__ uint32_t cnt[kBuckets];
+  if (threadIdx.x < kBuckets) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int X = blockIdx.x * blockDim.x + threadIdx.x;
+  if (X == 0) {
+    int nn = A.nseg + (int)*A.total;
+    if (nn > A.cap_nodes) { latch_error(A.status, kErrTree); nn = A.nseg; }
+    *A.nnodes = nn;
+    if (A.cbits == 0) write_root(A, 0, 0, cnt);           // one cloud: binary node 0 is the root
+  }
+  if (X < A.n - 1) oct_write_node(A, X, cnt);
+  __syncthreads();
+  if (threadIdx.x < kBuckets && cnt[threadIdx.x])
+    atomicAdd(&A.slots[kSlotCnt + threadIdx.x], cnt[threadIdx.x]);
 }
 
 // ------------------------------------------------------------------ a7: moments
@@ -1042,11 +1079,6 @@ __global__ void k_oct_write(OctWriteArgs A) {
 // buckets (leaves by body count 1 .. 16 and more, so that the lanes of a warp loop
 // equally long; then internal nodes by depth, deepest first); one launch does the
 // leaves, one more every internal depth, each after the deeper ones (k_level_moments).
-constexpr int kLeafBuckets = 17;
-constexpr int kBuckets = kLeafBuckets + kLevels;   // + internal depths 20 .. 0
-// offsets into t.scalars: bucket counts, fill cursors, done counters of the moment pass
-// and its ticket (zeroed before each build), then the bucket offsets
-constexpr int kSlotCnt = 0, kSlotFill = 40, kSlotDone = 80, kSlotTicket = 120, kSlotOff = 128;
 constexpr int kMomBlocksPerSM = 1;             // internal levels: one warp per SM sub-partition
 
 struct MomArgs {
@@ -1132,24 +1164,6 @@ __device__ __forceinline__ void store_sec(float4 *dst, const Dbl2 *T) {
   dst[2] = make_float4(T[4].hi, T[4].lo, T[5].hi, T[5].lo);
 }
 
-__device__ __forceinline__ int bucket_of(int4 t, int depth) {
-  const int b = t.x < 0 ? min(t.w - t.z, kLeafBuckets) - 1 : kLeafBuckets + (kLevels - 1 - depth);
-  return min(max(b, 0), kBuckets - 1);
-}
-
-__global__ void k_bucket_count(const int4 *__restrict__ topo, const int32_t *__restrict__ ndepth,
-                               const int32_t *__restrict__ nnodes, int cap_nodes,
-                               uint32_t *__restrict__ slots) {
-  __shared__ uint32_t cnt[kBuckets];
-  if (threadIdx.x < kBuckets) cnt[threadIdx.x] = 0;
-  __syncthreads();
-  const int id = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nn = min(*nnodes, cap_nodes);
-  if (id < nn) atomicAdd(&cnt[bucket_of(topo[id], ndepth[id])], 1u);
-  __syncthreads();
-  if (threadIdx.x < kBuckets && cnt[threadIdx.x])
-    atomicAdd(&slots[kSlotCnt + threadIdx.x], cnt[threadIdx.x]);
-}
 
 // Scatter node ids into their buckets (order inside a bucket is irrelevant: every
 // node is computed from its children only).
@@ -1497,12 +1511,14 @@ __global__ void k_fill_seg(const int64_t *__restrict__ off, int32_t *__restrict_
   for (int64_t i = off[k] + threadIdx.x; i < off[k + 1]; i += blockDim.x) seg_of[i] = k;
 }
 
-// Root of a single body: node 0 is a leaf at depth 0.
-__global__ void k_single_root(int4 *topo, int32_t *depth, int32_t *nparent, int32_t *nnodes) {
+// Root of a single body: node 0 is a leaf at depth 0 (moment bucket 0: one body).
+__global__ void k_single_root(int4 *topo, int32_t *depth, int32_t *nparent, int32_t *nnodes,
+                              uint32_t *slots) {
   topo[0] = make_int4(-1, 0, 0, 1);
   depth[0] = 0;
   nparent[0] = -1;
   *nnodes = 1;
+  slots[kSlotCnt + bucket_of(topo[0], 0)] = 1;
 }
 
 inline unsigned blocks_for(int64_t n, int threads) {
@@ -1554,11 +1570,11 @@ int tree_build(Ctx *c, int64_t n, const double *pos, const double *mass) {
   // a4: gather sorted bodies
   k_gather<<<blocks_for(n, 256), 256, 0, s>>>(pos, mass, t.idx, n, t.pos_s, t.mass_s, t.body_hi,
                                                t.body_lo, multi ? sg.seg_of : nullptr,
-                                               sg.seg_sorted);
+                                               sg.seg_sorted, t.scalars);
   ++c->launches;
   const int cap_nodes = (int)(2 * c->cap);
   if (n == 1) {
-    k_single_root<<<1, 1, 0, s>>>(t.topo, t.ndepth, t.nparent, t.nnodes);
+    k_single_root<<<1, 1, 0, s>>>(t.topo, t.ndepth, t.nparent, t.nnodes, t.scalars);
     ++c->launches;
   } else {
     const int ni = (int)(n - 1);
@@ -1584,17 +1600,14 @@ int tree_build(Ctx *c, int64_t n, const double *pos, const double *mass) {
     // of their children)
     OctWriteArgs W{(int)n, leaf_max, kv.cbits, sg.nseg, cap_nodes, t.bchild, t.bfirst, t.blast,
                    t.bplen, kv.seg, t.bnchild, base, total, t.topo, t.ndepth, t.nnodes,
-                   t.nparent, c->d_status};
+                   t.nparent, t.scalars, c->d_status};
     k_oct_write<<<blocks_for(ni, 256), 256, 0, s>>>(W);
     ++c->launches;
   }
-  // a7: moments (bucketed by depth, full warps)
-  GRAV_CUDA_TRY(cudaMemsetAsync(t.scalars + kSlotCnt, 0, sizeof(uint32_t) * kSlotOff, s));
+  // a7: moments (nodes bucketed by the octree write's counts; full warps)
   static_assert(kSlotDone + kLevels <= kSlotTicket && kSlotOff + kBuckets + 1 <= kScalarWords,
                 "scalar slots overlap");
   const unsigned nb_nodes = blocks_for(cap_nodes, 256);
-  k_bucket_count<<<nb_nodes, 256, 0, s>>>(t.topo, t.ndepth, t.nnodes, cap_nodes, t.scalars);
-  ++c->launches;
   k_bucket_fill<<<nb_nodes, 256, 0, s>>>(t.topo, t.ndepth, t.nnodes, cap_nodes, t.scalars,
                                          t.nlist);
   ++c->launches;

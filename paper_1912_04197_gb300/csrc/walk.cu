@@ -37,7 +37,9 @@
 // eight: warps walk the same 32 bodies, each from its share of the root's children (the root
 // contains every body, so the guard opens it for all of them); two partial sums are added
 // to the zeroed output with FP64 atomics (two addends: the result does not depend on their
-// order), four or eight are written to scratch and added in a fixed order by a closing pass.
+// order), more are written to scratch and added in a fixed order by a closing pass.  Very
+// small trees split in 64: eight parts per root child decide it alike, and each walks an
+// eighth of its children; only the first takes the child's own term or its bodies.
 // A second mode computes the vector-Jacobian product of the accelerations on the
 // same decisions (see flush_vjp and k_vjp_finish); a third counts decisions and
 // collects walk statistics.
@@ -153,8 +155,8 @@ struct WalkArgs {
   const int32_t *nnodes;
   int n;
   int ntasks;                     // tasks after splitting (base tasks x split)
-  int split;                      // 1, 2 or 4 warps per base task (see above)
-  double *part;                   // split 4 or 8: partial sums [split][rows][3] (rows = n or nrange)
+  int split;                      // 1, 2, 4, 8 or 64 warps per base task (see above)
+  double *part;                   // split >= 4: partial sums [split][rows][3] (rows = n or nrange)
   int rows;
   float theta2f;
   double theta2d;
@@ -548,7 +550,55 @@ struct Stack {
 // The force mode is held to 6 (quadrupole: 80 registers; the shared memory of its lists
 // allows no more) or 7 (monopole: 72 registers) resident blocks of 4 warps per SM, the VJP
 // mode to 6 (80 registers); the counted mode is not held to any.
-template <int ORDER, bool EPS0, int MODE>
+// 64-way split: the start of part `sub` of a task (see the kernel).  The root child c
+// (first_entry) is decided per lane by the FP64 test the walk's exact decisions equal (a
+// body inside c opens it under the guard).  Share 0 keeps c for the accepting lanes (the walk
+// takes their term, and counts their test, when it pops c) and counts the opening lanes'
+// test; every share walks its eighth of c's children for the opening lanes.  A leaf c is
+// walked whole by share 0.  Returns the number of stack entries set.  Not inlined: its FP64
+// registers stay out of the walk's register budget.
+template <bool COUNT>
+__device__ __noinline__ int split64_start(const WalkArgs &A, const Stack &st, uint32_t first_entry,
+                                          int sub, int gi, bool valid, unsigned vm, int root,
+                                          int &c_tests) {
+  const int lane = threadIdx.x & 31;
+  const int cnode = (int)(first_entry & kFirstMask);
+  const int4 ct = A.topo[cnode];
+  if (ct.x < 0) {
+    if (sub != 0) return 0;
+    if (lane == 0) st.set(0, first_entry, vm);
+    return 1;
+  }
+  bool op = false;
+  if (valid) {
+    op = A.mac_guard && ct.z <= gi && gi < ct.w;
+    if (!op) {
+      const double X = A.ncom[3 * cnode], Y = A.ncom[3 * cnode + 1], Z = A.ncom[3 * cnode + 2];
+      const double x = A.pos_s[3 * gi], y = A.pos_s[3 * gi + 1], z = A.pos_s[3 * gi + 2];
+      const double ddx = __dsub_rn(X, x), ddy = __dsub_rn(Y, y), ddz = __dsub_rn(Z, z);
+      const double D2d = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)),
+                                   __dmul_rn(ddz, ddz));
+      const double l = __dmul_rn(A.geom[8 * root + 3], pow2_neg(A.ndepth[cnode]));
+      op = !(__dmul_rn(l, l) < __dmul_rn(A.theta2d, D2d));
+      if (COUNT && op && sub == 0) ++c_tests;
+    }
+  }
+  const unsigned openv = __ballot_sync(0xffffffffu, valid && op);
+  const unsigned accv = vm & ~openv;
+  const int h2 = (ct.y + 7) >> 3, f2 = sub * h2, c2 = min(h2, ct.y - f2);
+  int sp = 0;
+  if (sub == 0 && accv) {
+    if (lane == 0) st.set(sp, first_entry, accv);
+    ++sp;
+  }
+  if (openv && c2 > 0) {
+    if (lane == 0) st.set(sp, (uint32_t)(ct.x + f2) | ((uint32_t)(c2 - 1) << kCntShift), openv);
+    ++sp;
+  }
+  return sp;
+}
+
+template <int ORDER, bool EPS0, int MODE, bool S64>
 __global__ void __launch_bounds__(32 * kWalkWarps, MODE == kModeCount ? 1 : (ORDER == 2 || MODE == kModeVjp ? 6 : 7))
 k_walk(WalkArgs A) {
   constexpr bool COUNT = MODE == kModeCount;
@@ -621,17 +671,19 @@ k_walk(WalkArgs A) {
     const int wbeg = A.task_begin ? A.task_begin[task] : task * 32;
     const int wend = min(A.task_begin ? A.task_end[task] : n, wbeg + 32);
     const int root = A.task_seg ? A.task_seg[task] : 0;
-    // first stack entry: the root, or (split) this part's share of the root's children
+    // first stack entry: the root, or (split) this part's share of the root's children;
+    // 64 parts (S64): root child part / 8, of whose children the part walks share part % 8
     uint32_t first_entry = (uint32_t)root;
     if (A.split > 1) {
       const int4 rt = A.topo[root];
       if (rt.x < 0) {                           // a one-leaf tree: part 0 takes it whole
         if (part != 0) continue;
       } else {
-        const int h = (rt.y + A.split - 1) / A.split;
-        const int cnt = min(h, rt.y - part * h);
+        const int p1 = S64 ? part >> 3 : part;
+        const int h = (rt.y + (S64 ? 8 : A.split) - 1) / (S64 ? 8 : A.split);
+        const int cnt = min(h, rt.y - p1 * h);
         if (cnt <= 0) continue;
-        first_entry = (uint32_t)(rt.x + part * h) | ((uint32_t)(cnt - 1) << kCntShift);
+        first_entry = (uint32_t)(rt.x + p1 * h) | ((uint32_t)(cnt - 1) << kCntShift);
       }
     }
     const int gi = wbeg + lane;
@@ -713,7 +765,11 @@ k_walk(WalkArgs A) {
     bool abort = false;
     {
       const unsigned vm = __ballot_sync(0xffffffffu, valid);
-      if (lane == 0) st.set(0, first_entry, vm);      // root (or half of its children)
+      if constexpr (S64) {
+        sp = split64_start<COUNT>(A, st, first_entry, part & 7, gi, valid, vm, root, c_tests);
+      } else {
+        if (lane == 0) st.set(0, first_entry, vm);    // root (or a share of its children)
+      }
     }
     __syncwarp();
 
@@ -1089,7 +1145,7 @@ k_walk(WalkArgs A) {
       double ax, ay, az;
       acc.get(acc64, ax, ay, az);
       double *dst;
-      if (A.part) {                             // four parts: added in a fixed order later
+      if (A.part) {                             // four or more parts: added in a fixed order later
         dst = A.part + 3 * ((int64_t)M.part * A.rows + (gi - A.body0));
       } else {                                  // two parts: two addends, order-free
         dst = A.acc_sorted ? A.acc_sorted + 3 * (int64_t)(gi - A.body0)
@@ -1143,23 +1199,12 @@ k_walk(WalkArgs A) {
   }
 }
 
-// Four- or eight-way split: the parts' partial sums added in a fixed order (so results do not depend
-// on which warp finished first), written in caller order (or as range rows), with the
-// leapfrog's closing kick when asked for.
-__global__ void k_walk_finish(const double *__restrict__ part, int rows, int nparts,
-                              const uint32_t *__restrict__ perm, double *__restrict__ acc,
-                              double *__restrict__ acc_sorted, double *__restrict__ vel,
-                              double kick) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= rows) return;
-  double a[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const double *p = part + 3 * (int64_t)i + k;
-    double sum = p[0];
-    for (int q = 1; q < nparts; ++q) sum = __dadd_rn(sum, p[3 * (int64_t)q * rows]);
-    a[k] = sum;
-  }
+// Split in four or more: the parts' partial sums added in a fixed order (so results do not
+// depend on which warp finished first), written in caller order (or as range rows), with
+// the leapfrog's closing kick when asked for.
+__device__ __forceinline__ void finish_row(int i, const double *a, const uint32_t *__restrict__ perm,
+                                           double *__restrict__ acc, double *__restrict__ acc_sorted,
+                                           double *__restrict__ vel, double kick) {
   if (acc_sorted) {
     acc_sorted[3 * (int64_t)i] = a[0];
     acc_sorted[3 * (int64_t)i + 1] = a[1];
@@ -1175,6 +1220,62 @@ __global__ void k_walk_finish(const double *__restrict__ part, int rows, int npa
     vel[3 * ci + 1] = __dadd_rn(vel[3 * ci + 1], __dmul_rn(kick, a[1]));
     vel[3 * ci + 2] = __dadd_rn(vel[3 * ci + 2], __dmul_rn(kick, a[2]));
   }
+}
+
+// Up to 8 parts: one thread per row, every part loaded before the sums (part by part).
+__global__ void k_walk_finish(const double *__restrict__ part, int rows, int nparts,
+                              const uint32_t *__restrict__ perm, double *__restrict__ acc,
+                              double *__restrict__ acc_sorted, double *__restrict__ vel,
+                              double kick) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  double v[8][3];
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v[q][k] = q < nparts ? part[3 * ((int64_t)q * rows + i) + k] : 0.0;
+  double a[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double sum = v[0][k];
+#pragma unroll
+    for (int q = 1; q < 8; ++q)
+      if (q < nparts) sum = __dadd_rn(sum, v[q][k]);
+    a[k] = sum;
+  }
+  finish_row(i, a, perm, acc, acc_sorted, vel, kick);
+}
+
+// 64 parts: 8 lanes per row, lane g summing parts 8g .. 8g+7 in order, then a butterfly
+// over the row's lanes (every lane ends with the same sum, a + b and b + a being equal).
+__global__ void __launch_bounds__(256) k_walk_finish64(const double *__restrict__ part, int rows,
+                                                       const uint32_t *__restrict__ perm,
+                                                       double *__restrict__ acc,
+                                                       double *__restrict__ acc_sorted,
+                                                       double *__restrict__ vel, double kick) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = t >> 3, g = t & 7;
+  const bool in = i < rows;                    // alike in the 8 lanes of a row
+  double a[3] = {0.0, 0.0, 0.0};
+  if (in) {
+    double v[8][3];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) v[q][k] = part[3 * ((int64_t)(8 * g + q) * rows + i) + k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      double sum = v[0][k];
+#pragma unroll
+      for (int q = 1; q < 8; ++q) sum = __dadd_rn(sum, v[q][k]);
+      a[k] = sum;
+    }
+  }
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) a[k] = __dadd_rn(a[k], __shfl_xor_sync(0xffffffffu, a[k], o));
+  if (in && g == 0) finish_row(i, a, perm, acc, acc_sorted, vel, kick);
 }
 
 // Task order of the next full force walk: the tasks of each queue (the queues' contiguous
@@ -1225,13 +1326,28 @@ __global__ void k_order_reset(int32_t *__restrict__ order, uint32_t *__restrict_
   }
 }
 
-template <int ORDER, bool EPS0, int MODE>
-int launch_walk(Ctx *c, WalkArgs A) {
+// Warps per base task: split tasks when the tree has no more of them than a full GPU of
+// warps, in four when it has no more than half as many, in eight when no more than a
+// quarter, in 64 when no more than a 32nd (force and counted walks; each root child's
+// children shared by eight parts).  The decision depends only on the whole tree's task count
+// and the SM count (not on the kernel variant, the launch shape or a range), so every
+// variant and a range walk compute what the full walk does; the VJP adds its parts' own-term
+// gradients with FP64 atomics (its source scatter is order-dependent in the last bits anyway).
+int walk_split(const Ctx *c, const WalkArgs &A, bool allow64) {
+  const int basis = A.split_basis > 0 ? A.split_basis : A.ntasks;
+  const int slots = kSplitWarpsPerSM * c->num_sms;
+  if (!A.mac_guard) return 1;
+  if (allow64 && 32 * basis <= slots) return 64;
+  return 4 * basis <= slots ? 8 : 2 * basis <= slots ? 4 : basis <= slots ? 2 : 1;
+}
+
+template <int ORDER, bool EPS0, int MODE, bool S64>
+int launch_walk_s(Ctx *c, WalkArgs A) {
   using Smem = typename std::conditional<
       ORDER == 2, WarpSmemQ,
       typename std::conditional<MODE == kModeVjp, WarpSmemV, WarpSmem>::type>::type;
   const size_t smem = sizeof(Smem) * kWalkWarps;
-  auto kern = k_walk<ORDER, EPS0, MODE>;
+  auto kern = k_walk<ORDER, EPS0, MODE, S64>;
   static int blocks_per_sm[64] = {0};
   const int dev = c->device < 64 ? c->device : 63;
   if (blocks_per_sm[dev] == 0) {
@@ -1256,16 +1372,8 @@ int launch_walk(Ctx *c, WalkArgs A) {
   int bps = blocks_per_sm[dev] - shape.blocks_less;
   if (bps < 1) bps = 1;
   int blocks = bps * c->num_sms;
-  // split tasks when the tree has no more of them than a full GPU of warps, in four when it
-  // has no more than half as many, in eight when no more than a quarter; the decision
-  // depends only on the whole tree's task count
-  // and the SM count (not on the kernel variant, the launch shape or a range), so every
-  // variant and a range walk compute what the full walk does; the VJP adds its parts' own-term
-  // gradients with FP64 atomics (its source scatter is order-dependent in the last bits anyway)
   const int base_tasks = A.ntasks;
-  const int basis = A.split_basis > 0 ? A.split_basis : base_tasks;
-  const int slots = kSplitWarpsPerSM * c->num_sms;
-  A.split = !A.mac_guard ? 1 : 4 * basis <= slots ? 8 : 2 * basis <= slots ? 4 : basis <= slots ? 2 : 1;
+  A.split = walk_split(c, A, MODE != kModeVjp);  // 64 exactly when S64 (launch_walk)
   A.ntasks = base_tasks * A.split;
   const int rows = A.acc_sorted ? A.nrange : A.n;
   A.rows = rows;
@@ -1317,10 +1425,12 @@ int launch_walk(Ctx *c, WalkArgs A) {
   A.nqueues = shape.one_queue ? 1 : c->num_sms;
   GRAV_CUDA_TRY(cudaMemsetAsync(A.task_counter, 0, sizeof(unsigned) * A.nqueues, c->stream));
   // a full force walk takes its tasks in the order the last one's costs give and records
-  // its own; the range, counted and VJP walks take them in index order
+  // its own; the range, counted and VJP walks take them in index order, and so does a walk
+  // with no more tasks than resident warps (all of them start at once: no order to keep)
   A.order = nullptr;
   A.cost = nullptr;
-  const bool ordered = MODE == kModeForce && A.task0 == 0 && !A.acc_sorted;
+  const bool ordered = MODE == kModeForce && A.task0 == 0 && !A.acc_sorted &&
+                       A.ntasks > bps * c->num_sms * kWalkWarps;
   if (ordered) {
     if (A.ntasks > c->walk_order_cap) {
       GRAV_CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -1355,14 +1465,26 @@ int launch_walk(Ctx *c, WalkArgs A) {
     GRAV_CUDA_TRY(cudaGetLastError());
   }
   if (A.split >= 4 && MODE != kModeVjp) {
-    k_walk_finish<<<(unsigned)((rows + 255) / 256), 256, 0, c->stream>>>(
-        A.part, rows, A.split, A.perm, A.acc_sorted ? nullptr : A.acc, A.acc_sorted, kick_vel,
-        A.kick);
+    if (A.split == 64)
+      k_walk_finish64<<<(unsigned)((8 * (int64_t)rows + 255) / 256), 256, 0, c->stream>>>(
+          A.part, rows, A.perm, A.acc_sorted ? nullptr : A.acc, A.acc_sorted, kick_vel, A.kick);
+    else
+      k_walk_finish<<<(unsigned)((rows + 255) / 256), 256, 0, c->stream>>>(
+          A.part, rows, A.split, A.perm, A.acc_sorted ? nullptr : A.acc, A.acc_sorted, kick_vel,
+          A.kick);
     ++c->launches;
     return cuda_status(cudaGetLastError());
   }
   if (A.split > 1 && kick_vel) return launch_kick(c, A.n, kick_vel, A.acc, A.kick);
   return GRAVITY_OK;
+}
+
+template <int ORDER, bool EPS0, int MODE>
+int launch_walk(Ctx *c, WalkArgs A) {
+  if constexpr (MODE != kModeVjp) {
+    if (walk_split(c, A, true) == 64) return launch_walk_s<ORDER, EPS0, MODE, true>(c, A);
+  }
+  return launch_walk_s<ORDER, EPS0, MODE, false>(c, A);
 }
 
 }  // namespace
