@@ -3,8 +3,8 @@
 The walk computes each body's force from the tree alone (Sec. 2.1, kernel 5), so walking
 the tree's tasks in G contiguous ranges and putting the rows back in the caller's order
 (gravity_scatter_sorted) must give exactly what one gravity_forces launch gives, bit for
-bit: at sizes where the walk splits its tasks between two warps and where it does not,
-with one cloud and with several.  The sharded leapfrog (shard.py, every rank's range
+bit: at sizes where the walk splits its tasks between two warps, between 64 and where it
+does not, with one cloud and with several.  The sharded leapfrog (shard.py, every rank's range
 computed in this process) must equal leapfrog_step bit for bit."""
 import numpy as np
 import pytest
@@ -22,6 +22,8 @@ def _setup(g, kind, order, leaf):
         g.gravity_set_clouds(ctx, off)
     elif kind == "small":
         pos, vel, m = inputs.rubble_pile(5000, seed=4)           # few tasks: split walk
+    elif kind == "tiny":
+        pos, vel, m = inputs.rubble_pile(2000, seed=6)           # 63 tasks: 64 parts each
     else:
         pos, vel, m = inputs.clumpy_plummer(200_000, seed=5, nclusters=8)
         vel = np.zeros_like(pos)
@@ -32,7 +34,8 @@ def _setup(g, kind, order, leaf):
 
 
 @pytest.mark.parametrize("kind,order,leaf", [("clumpy", 2, 16), ("clumpy", 0, 1),
-                                             ("small", 2, 16), ("clouds", 2, 16)])
+                                             ("small", 2, 16), ("clouds", 2, 16),
+                                             ("tiny", 2, 16), ("tiny", 0, 1)])
 @pytest.mark.parametrize("world", [2, 3, 7])
 def test_range_walks_equal_the_full_walk(gpu, kind, order, leaf, world):
     ctx, P, _, M, p = _setup(gpu, kind, order, leaf)
@@ -70,7 +73,7 @@ def test_range_arguments(gpu):
 
 
 @pytest.mark.parametrize("kind,scheme", [("clumpy", 0), ("small", 0), ("clouds", 0),
-                                         ("clumpy", 1)])
+                                         ("tiny", 0), ("clumpy", 1)])
 def test_sharded_leapfrog_equals_leapfrog_step(gpu, kind, scheme):
     out = []
     for sharded in (False, True):
