@@ -701,8 +701,9 @@ def run_ours(args, rank, world, local_rank):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True,
             "scaling": "strong" if shard_mode else "weak", "vs_baseline": None, "dtype": "f32",
-            "dtype_note": "FP32 pair terms and opening tests on hi/lo coordinates; FP64 moments, "
-                          "FP64 decisions in the guard band, FP64 outputs",
+            "dtype_note": "FP32 pair terms and opening tests on hi/lo coordinates; FP64 mass and "
+                          "COM, double-float FP32 second moments, FP64 decisions in the guard "
+                          "band, FP64 outputs",
             "precision": {"accum": "fp32-two-sum" if args.accum == 0 else "fp64"},
             "data": "synthetic", "config": workload(args), "phases_ms": {"build": t_build, "walk": t_walk},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

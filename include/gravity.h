@@ -113,7 +113,8 @@ int gravity_set_allocator(gravity_ctx *ctx, gravity_alloc_fn alloc, gravity_free
  * bounding cube of all bodies (the root), octree construction (63-bit Morton keys,
  * stable device radix sort = "sort bodies", binary radix tree collapsed to an
  * octree), and node mass / centre of mass by Eq. (COMinternal) in FP64 (plus the
- * traceless quadrupole when p->order == 2).  The tree stays in the context until
+ * traceless quadrupole when p->order == 2, its second moments carried up the tree in
+ * double-float FP32 arithmetic, ~47 significant bits).  The tree stays in the context until
  * the next build; pos and mass are read during this call only.
  * n = 0 is a no-op that leaves an empty tree.  p = NULL means defaults. */
 int gravity_tree_build(gravity_ctx *ctx, int64_t n, const double *pos, const double *mass,
